@@ -1,0 +1,365 @@
+/*
+ * rqrcp_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle for randomized
+ * QR with column pivoting (Xiao, Gu, Langou, "Fast parallel randomized QR with
+ * column pivoting algorithms for reliable low-rank matrix approximations", HiPC 2017).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code, header
+ * or constant table with the CUDA path of the package; it implements every step
+ * again from the paper.
+ *
+ * Conventions: all matrices are column-major, element (i,j) of X with leading
+ * dimension ldx lives at X[j*ldx + i].  Indices are 0-based; the paper is 1-based.
+ * Omega is row-major l x m (element (r,q) at Omega[r*m + q]).
+ * Arithmetic is IEEE double throughout; loops run in the order the paper states.
+ * OpenMP (when compiled with -fopenmp) only splits independent columns between
+ * threads; the arithmetic of each column is the same sequential loop either way.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *  - Householder reflectors follow the LAPACK xLARFG convention:
+ *    beta = -sign(alpha)*||x||, tau = (beta-alpha)/beta, v = x(2:)/(alpha-beta), v(1)=1,
+ *    tau = 0 when x(2:) = 0.  sign(alpha) is + for alpha >= 0 (also for -0.0).
+ *    The norm is sqrt(alpha^2 + sum x(2:)^2) without scaling: entries must stay
+ *    below ~1e150 in magnitude.
+ *  - argmax ties go to the smallest current column position.
+ *  - column norms on B are recomputed at every pivot step (Alg. 1 "Update r_s").
+ *  - rank guard: a pivot step whose largest remaining sketch norm^2 is at most
+ *    (10*max(m,n)*2^-53)^2 times the largest initial sketch column norm^2 stops
+ *    pivoting for good; the remaining columns keep their order, blocks keep their
+ *    static boundaries and B is no longer updated.
+ *  - if a diagonal entry of R11 is exactly zero the matching column of
+ *    Omega_hat_11 is set to zero instead of dividing.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_EXPORT __attribute__((visibility("default")))
+
+#define AT(X, ld, i, j) (X)[(size_t)(j) * (size_t)(ld) + (size_t)(i)]
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x64-10 counter-based generator, from its published definition:      */
+/* Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",  */
+/* SC'11.  Round: (x0,x1,x2,x3) -> (hi(M1*x2)^x1^k0, lo(M1*x2),                */
+/*                                  hi(M0*x0)^x3^k1, lo(M0*x0)); key += Weyl.  */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/*
+ * Omega in N(0,1)^{l x m} (Alg. 2, "Generate i.i.d Gaussian matrix").  Element with
+ * row-major flat index q = r*m + c takes lane q%4 of the Philox block with counter
+ * (q/4, 0, 0, 0) and key (seed, 0).  Lanes (0,1) and (2,3) form Box-Muller pairs
+ * (Box & Muller 1958): u1 = (w0>>11 + 1)*2^-53 in (0,1], u2 = (w1>>11)*2^-53 in [0,1),
+ * rho = sqrt(-2 ln u1), z_even = rho cos(2 pi u2), z_odd = rho sin(2 pi u2).
+ */
+ORC_EXPORT void orc_omega(int64_t l, int64_t m, uint64_t seed, double* Omega)
+{
+    const double two53 = 1.0 / 9007199254740992.0;
+    int64_t total = l * m;
+#pragma omp parallel for schedule(static)
+    for (int64_t blk = 0; blk < (total + 3) / 4; ++blk) {
+        uint64_t ctr[4] = {(uint64_t)blk, 0, 0, 0}, key[2] = {seed, 0}, w[4];
+        orc_philox4x64_10(ctr, key, w);
+        for (int pair = 0; pair < 2; ++pair) {
+            double u1 = ((double)(w[2 * pair] >> 11) + 1.0) * two53;
+            double u2 = (double)(w[2 * pair + 1] >> 11) * two53;
+            double rho = sqrt(-2.0 * log(u1));
+            double theta = 2.0 * M_PI * u2;
+            int64_t q0 = blk * 4 + 2 * pair;
+            if (q0 < total) Omega[q0] = rho * cos(theta);
+            if (q0 + 1 < total) Omega[q0 + 1] = rho * sin(theta);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Householder reflector (Alg. 1, "Form Householder reflection H_i"), xLARFG    */
+/* convention.  On entry x[0..len) is the column; on exit x[0] = beta and      */
+/* x[1..len) holds the tail of v (v[0] = 1 implicit).  Returns tau.            */
+/* ------------------------------------------------------------------------- */
+static double house_gen(int64_t len, double* x)
+{
+    if (len <= 1) return 0.0;
+    double ss = 0.0;
+    for (int64_t r = 1; r < len; ++r) ss += x[r] * x[r];
+    if (ss == 0.0) return 0.0;
+    double alpha = x[0];
+    double nrm = sqrt(alpha * alpha + ss);
+    double beta = (alpha >= 0.0) ? -nrm : nrm;
+    double tau = (beta - alpha) / beta;
+    double scal = 1.0 / (alpha - beta);
+    for (int64_t r = 1; r < len; ++r) x[r] *= scal;
+    x[0] = beta;
+    return tau;
+}
+
+/* y <- (I - tau v v^T) y for a column y of length len; v = [1; vt[1..len)]. */
+static void house_apply(int64_t len, const double* v, double tau, double* y)
+{
+    if (tau == 0.0) return;
+    double w = y[0];
+    for (int64_t r = 1; r < len; ++r) w += v[r] * y[r];
+    w *= tau;
+    y[0] -= w;
+    for (int64_t r = 1; r < len; ++r) y[r] -= w * v[r];
+}
+
+static void swap_cols(double* X, int64_t ldx, int64_t rows, int64_t a, int64_t b)
+{
+    if (a == b) return;
+    for (int64_t r = 0; r < rows; ++r) {
+        double t = AT(X, ldx, r, a);
+        AT(X, ldx, r, a) = AT(X, ldx, r, b);
+        AT(X, ldx, r, b) = t;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. 1: QR with column pivoting, k steps, column norms recomputed from the  */
+/* trailing rows at every step (Alg. 1 "Update r_s = ||A(i+1:m,s)||").         */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT int orc_qrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
+                        int32_t* jpvt, double* tau)
+{
+    if (m < 0 || n < 0 || k < 1 || k > (m < n ? m : n) || lda < (m > 1 ? m : 1)) return -1;
+    for (int64_t j = 0; j < n; ++j) jpvt[j] = (int32_t)j;
+    for (int64_t i = 0; i < k; ++i) {
+        int64_t best = i;
+        double bestv = -1.0;
+        for (int64_t s = i; s < n; ++s) {
+            double nu = 0.0;
+            for (int64_t r = i; r < m; ++r) nu += AT(A, lda, r, s) * AT(A, lda, r, s);
+            if (nu > bestv) { bestv = nu; best = s; }
+        }
+        swap_cols(A, lda, m, i, best);
+        int32_t tp = jpvt[i]; jpvt[i] = jpvt[best]; jpvt[best] = tp;
+        double* x = &AT(A, lda, i, i);
+        tau[i] = house_gen(m - i, x);
+#pragma omp parallel for schedule(static)
+        for (int64_t s = i + 1; s < n; ++s) house_apply(m - i, x, tau[i], &AT(A, lda, i, s));
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. 2: randomized QRCP.                                                    */
+/*   formula == 4 : B updated by Eq. (4) (Duersch-Gu), in place, after the      */
+/*                  partial QRCP on B has transformed it.                       */
+/*   formula == 5 : B updated by Eq. (5) (Martinsson et al.): the partial QRCP  */
+/*                  runs on a copy; B itself is only permuted, and               */
+/*                  B_trail <- B2 - Omega_bar_1 R12 with Omega_bar = Omega Q.    */
+/* Outputs: A overwritten with R (upper trapezoid, R22 = A(k:m,k:n)) and the    */
+/* reflector tails below the diagonal of columns 0..k-1; tau[0..k); jpvt (0-    */
+/* based, A_in(:,jpvt[c]) is column c of A*Pi); *rank_out = pivots taken before */
+/* the rank guard fired (k if never).  gaps (k entries, optional) receives for  */
+/* every pivot step (nu_max - nu_second)/nu_max over the candidate sketch norms */
+/* (1.0 with a single candidate, -1.0 where no pivot was chosen).  Bout (l x n,  */
+/* optional) receives B after the last block (formula 4: the transformed and    */
+/* updated sketch; formula 5: the permuted sketch Omega_bar_2 R22).             */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT int orc_rqrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
+                         int64_t p, const double* Omega, int formula, int32_t* jpvt, double* tau,
+                         int64_t* rank_out, double* gaps, double* Bout)
+{
+    if (m < 1 || n < 1) return -1;
+    if (lda < m) return -4;
+    if (k < 1 || k > (m < n ? m : n)) return -5;
+    if (b < 1) return -6;
+    if (p < 0) return -7;
+    if (formula != 4 && formula != 5) return -9;
+    const int64_t l = b + p;
+    double* B = (double*)malloc(sizeof(double) * (size_t)(l * n));
+    double* Bq = (double*)malloc(sizeof(double) * (size_t)(l * n));   /* QRCP copy (formula 5) */
+    double* Wh = (double*)malloc(sizeof(double) * (size_t)(b * b));   /* Omega_hat_11 */
+    double* Ob = NULL;                                                /* Omega_bar, row-major l x m */
+    if (!B || !Bq || !Wh) { free(B); free(Bq); free(Wh); return 1; }
+    if (formula == 5) {
+        Ob = (double*)malloc(sizeof(double) * (size_t)(l * m));
+        if (!Ob) { free(B); free(Bq); free(Wh); return 1; }
+        memcpy(Ob, Omega, sizeof(double) * (size_t)(l * m));
+    }
+
+    /* Alg. 2: B = Omega A, summed over q in increasing order. */
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t r = 0; r < l; ++r) {
+            double s = 0.0;
+            for (int64_t q = 0; q < m; ++q) s += Omega[r * m + q] * AT(A, lda, q, j);
+            AT(B, l, r, j) = s;
+        }
+    for (int64_t j = 0; j < n; ++j) jpvt[j] = (int32_t)j;
+    if (gaps) for (int64_t c = 0; c < k; ++c) gaps[c] = -1.0;
+
+    double nu0max = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double nu = 0.0;
+        for (int64_t r = 0; r < l; ++r) nu += AT(B, l, r, j) * AT(B, l, r, j);
+        if (nu > nu0max) nu0max = nu;
+    }
+    const double gtol = 10.0 * (double)(m > n ? m : n) * ldexp(1.0, -53);
+    const double guard = gtol * gtol * nu0max;
+    int pivoting = 1;
+    int64_t rank = k;
+
+    for (int64_t i = 0; i < k; i += b) {
+        const int64_t bb = (b < k - i) ? b : (k - i);
+        int pivoted_block = pivoting;
+
+        /* --- Alg. 2 "Partial QRCP on B(:,i:n) to get b pivots" (Alg. 1 on B) --- */
+        if (pivoting) {
+            double* Q = B;
+            if (formula == 5) { memcpy(Bq, B, sizeof(double) * (size_t)(l * n)); Q = Bq; }
+            for (int64_t t = 0; t < bb; ++t) {
+                const int64_t c = i + t;
+                int64_t best = c;
+                double v1 = -1.0, v2 = -1.0;
+                for (int64_t s = c; s < n; ++s) {
+                    double nu = 0.0;
+                    for (int64_t r = t; r < l; ++r) nu += AT(Q, l, r, s) * AT(Q, l, r, s);
+                    if (nu > v1) { v2 = v1; v1 = nu; best = s; }
+                    else if (nu > v2) v2 = nu;
+                }
+                if (v1 <= guard) { pivoting = 0; rank = c; break; }
+                if (gaps) gaps[c] = (v2 < 0.0) ? 1.0 : (v1 - v2) / v1;
+                /* Alg. 2 "Swap ... columns in A, Pi" (and in B). */
+                swap_cols(A, lda, m, c, best);
+                swap_cols(B, l, l, c, best);
+                if (formula == 5) swap_cols(Bq, l, l, c, best);
+                int32_t tp = jpvt[c]; jpvt[c] = jpvt[best]; jpvt[best] = tp;
+                /* Householder on Q(t:l, c), applied to Q(t:l, c+1:n). */
+                double* x = &AT(Q, l, t, c);
+                double tb = house_gen(l - t, x);
+#pragma omp parallel for schedule(static)
+                for (int64_t s = c + 1; s < n; ++s) house_apply(l - t, x, tb, &AT(Q, l, t, s));
+                for (int64_t r = t + 1; r < l; ++r) x[r - t] = 0.0; /* R_hat is upper */
+            }
+        }
+
+        /* --- Alg. 2 "unpivoted QR on A(i:m, i:i+b-1)" --- */
+        for (int64_t j = 0; j < bb; ++j) {
+            const int64_t col = i + j;
+            double* x = &AT(A, lda, col, col);
+            tau[col] = house_gen(m - col, x);
+            for (int64_t s = col + 1; s < i + bb; ++s) house_apply(m - col, x, tau[col], &AT(A, lda, col, s));
+        }
+
+        /* --- Alg. 2 "A(i:m,i+b:n) <- Q_tilde^T A(i:m,i+b:n)": reflectors one at a time --- */
+#pragma omp parallel for schedule(static)
+        for (int64_t s = i + bb; s < n; ++s)
+            for (int64_t j = 0; j < bb; ++j) {
+                const int64_t col = i + j;
+                house_apply(m - col, &AT(A, lda, col, col), tau[col], &AT(A, lda, col, s));
+            }
+
+        /* --- B update, only while pivoting is still on after this block --- */
+        if (!(pivoted_block && pivoting) || i + bb >= n) continue;
+        if (formula == 4) {
+            /* Eq. (4): B(0:bb, trail) <- R_hat12 - Omega_hat_11 R12, with
+               Omega_hat_11 = R_hat11 R11^{-1} from Omega_hat_11 R11 = R_hat11
+               (forward substitution over columns; both factors upper triangular). */
+            for (int64_t j = 0; j < bb; ++j) {
+                const double rjj = AT(A, lda, i + j, i + j);
+                for (int64_t r = 0; r < bb; ++r) {
+                    double s = AT(B, l, r, i + j);
+                    for (int64_t q = 0; q < j; ++q) s -= Wh[q * b + r] * AT(A, lda, i + q, i + j);
+                    Wh[j * b + r] = (rjj == 0.0) ? 0.0 : s / rjj;
+                }
+            }
+#pragma omp parallel for schedule(static)
+            for (int64_t s = i + bb; s < n; ++s)
+                for (int64_t r = 0; r < bb; ++r) {
+                    double acc = AT(B, l, r, s);
+                    for (int64_t q = 0; q < bb; ++q) acc -= Wh[q * b + r] * AT(A, lda, i + q, s);
+                    AT(B, l, r, s) = acc;
+                }
+        } else {
+            /* Eq. (5): Omega_bar <- Omega_bar Q_tilde (reflectors applied from the right
+               to the columns i..m-1 of Omega_bar, in order i, i+1, ...), then
+               B(:, trail) <- B(:, trail) - Omega_bar(:, i:i+bb) R12. */
+#pragma omp parallel for schedule(static)
+            for (int64_t r = 0; r < l; ++r) {
+                double* orow = &Ob[r * m];
+                for (int64_t j = 0; j < bb; ++j) {
+                    const int64_t col = i + j;
+                    const double* v = &AT(A, lda, col, col);
+                    if (tau[col] == 0.0) continue;
+                    double w = orow[col];
+                    for (int64_t q = col + 1; q < m; ++q) w += orow[q] * v[q - col];
+                    w *= tau[col];
+                    orow[col] -= w;
+                    for (int64_t q = col + 1; q < m; ++q) orow[q] -= w * v[q - col];
+                }
+            }
+#pragma omp parallel for schedule(static)
+            for (int64_t s = i + bb; s < n; ++s)
+                for (int64_t r = 0; r < l; ++r) {
+                    double acc = AT(B, l, r, s);
+                    for (int64_t q = 0; q < bb; ++q) acc -= Ob[r * m + i + q] * AT(A, lda, i + q, s);
+                    AT(B, l, r, s) = acc;
+                }
+        }
+    }
+    if (rank_out) *rank_out = rank;
+    if (Bout) memcpy(Bout, B, sizeof(double) * (size_t)(l * n));
+    free(B); free(Bq); free(Wh); free(Ob);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Q = H_0 H_1 ... H_{k-1} restricted to its first ncols columns (Alg. 2,      */
+/* "Q is the product of Q_tilde").  Backward accumulation on the identity.     */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT void orc_form_q(int64_t m, int64_t k, const double* A, int64_t lda, const double* tau,
+                           int64_t ncols, double* Q, int64_t ldq)
+{
+    for (int64_t j = 0; j < ncols; ++j)
+        for (int64_t r = 0; r < m; ++r) AT(Q, ldq, r, j) = (r == j) ? 1.0 : 0.0;
+    for (int64_t h = k - 1; h >= 0; --h) {
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < ncols; ++j) house_apply(m - h, &AT(A, lda, h, h), tau[h], &AT(Q, ldq, h, j));
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Low-rank product L = Q1 [R11 R12] Pi^T (Sec. I-A): column jpvt[c] of L is   */
+/* Q1 times column c of the k x n upper trapezoid of the factored A.  Q1       */
+/* (m x k, optional) receives the first k columns of Q.                        */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT int orc_lowrank(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                           const double* tau, const int32_t* jpvt, double* L, int64_t ldl, double* Q1)
+{
+    double* Q = (double*)malloc(sizeof(double) * (size_t)(m * k));
+    if (!Q) return 1;
+    orc_form_q(m, k, A, lda, tau, k, Q, m);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+        int64_t top = (c + 1 < k) ? c + 1 : k;
+        double* out = &AT(L, ldl, 0, jpvt[c]);
+        for (int64_t r = 0; r < m; ++r) out[r] = 0.0;
+        for (int64_t q = 0; q < top; ++q) {
+            double rq = AT(A, lda, q, c);
+            for (int64_t r = 0; r < m; ++r) out[r] += AT(Q, m, r, q) * rq;
+        }
+    }
+    if (Q1) memcpy(Q1, Q, sizeof(double) * (size_t)(m * k));
+    free(Q);
+    return 0;
+}
