@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of randomized QRCP (Alg. 2) on GB300.
+
+Default workload: plain FP64 full RQRCP (k = n) of an 8192 x 8192 matrix with i.i.d.
+N(0,1) entries, b = 64, p = 8.  A step is one whole factorization (sketch, every pivot
+search, swap, panel, compact-WY update and Eq. (4) sketch update) of a fresh copy of the
+input; the 512 MB input is larger than L2 and is rewritten before every step.
+
+metric value = counted flops / time, counted flops F = 2 l m n + 4 m n k - 2 (m+n) k^2 + 4 k^3/3
+(sketch + Householder QR to rank k).  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample of
+the same workload on the host cores.  With torchrun (N > 1) every rank factors its own
+matrix (independent replicas: the single-matrix path has no data-parallel split), value
+is the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RQRCP ms & GFLOP/s, mixed vs plain FP64 at rel. residual ≤1e-6; % roofline"
+
+WORKLOADS = {
+    "fp64_8192_iid": dict(m=8192, n=8192, k=8192, b=64, p=8, kind="iid", prec="fp64",
+                          desc="plain FP64 full RQRCP 8192x8192, i.i.d. N(0,1), b=64, p=8"),
+    "fp64_8192_rank500": dict(m=8192, n=8192, k=8192, b=64, p=8, kind="rank500", prec="fp64",
+                              desc="plain FP64 full RQRCP 8192x8192, exactly rank 500 (G1 G2), b=64, p=8"),
+    "fp64_1000_k64": dict(m=1000, n=1000, k=64, b=32, p=8, kind="logspec", prec="fp64",
+                          desc="plain FP64 partial RQRCP k=64 on 1000x1000 U diag(10^(-6i/1000)) V^T, b=32, p=8"),
+    "mixed_32768x16384_k512": dict(m=32768, n=16384, k=512, b=64, p=16, kind="expspec200", prec="mixed",
+                                   desc="mixed partial RQRCP k=512 on 32768x16384 FP32 U diag(exp(-i/200)) V^T, "
+                                        "b=64, p=16"),
+}
+
+# FP64 peak of a GB300 from the recipe's nominal table (DFMA pipe; no measured FP64 entry
+# exists in MEASURED_PEAKS.json).
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def counted_flops(m, n, k, l):
+    return 2.0 * l * m * n + 4.0 * m * n * k - 2.0 * (m + n) * k * k + 4.0 * k ** 3 / 3.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------------ inputs
+def make_input_torch(w, device, seed=1):
+    import torch
+    from paper_1804_05138_gb300 import inputs
+    m, n = w["m"], w["n"]
+    dt = torch.float64 if w["prec"] == "fp64" else torch.float32
+    if w["kind"] == "iid":
+        return inputs.gaussian_torch(m, n, seed, device=device, dtype=dt)
+    if w["kind"] == "rank500":
+        return inputs.rank_r_product_torch(m, n, 500, device=device, dtype=dt)
+    if w["kind"] == "logspec":
+        return inputs.spectrum_matrix_torch(m, n, inputs.sigma_log_decay(min(m, n)), device=device, dtype=dt)
+    if w["kind"] == "expspec200":
+        # sigma_i = exp(-i/200): beyond i = 4096 every sigma_i is below 1e-8 sigma_1, under one FP32
+        # rounding of the stored entries, so the draw keeps the leading 4096 triplets.
+        return inputs.spectrum_matrix_torch(m, n, inputs.sigma_exp_decay(min(m, n), 200.0), device=device,
+                                            dtype=dt, rank_cap=4096)
+    raise ValueError(w["kind"])
+
+
+def make_input_numpy(w, m, n):
+    from paper_1804_05138_gb300 import inputs
+    if w["kind"] == "iid":
+        return inputs.gaussian(m, n, seed=1)
+    if w["kind"] == "rank500":
+        return inputs.rank_r_product(m, n, 500)
+    if w["kind"] == "logspec":
+        return inputs.spectrum_matrix(m, n, inputs.sigma_log_decay(min(m, n)))
+    return inputs.spectrum_matrix(m, n, inputs.sigma_exp_decay(min(m, n), 200.0))
+
+
+# ------------------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(w, target_s=15.0):
+    """Time the FP64 oracle on a bounded sample of workload w: the same m x n matrix but
+    only the first blocks (k_sample columns).  Returns (GFLOP/s, cores, description)."""
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    m, n, b, p = w["m"], w["n"], w["b"], w["p"]
+    # keep the sample's memory modest on the host: cap rows/cols at 8192
+    ms, ns = min(m, 8192), min(n, 8192)
+    A = make_input_numpy(w, ms, ns)
+    Om = oracle.omega(b + p, ms, seed=0)
+    k_s = min(w["k"], b)
+    t0 = time.perf_counter()
+    oracle.rqrcp(A, k_s, b, p, Om)
+    dt = time.perf_counter() - t0
+    # grow the sample to roughly target_s of CPU work
+    blocks = max(1, min(int(target_s / max(dt, 1e-3)), max(1, min(w["k"], min(ms, ns)) // b)))
+    k_s = min(w["k"], blocks * b, min(ms, ns))
+    t0 = time.perf_counter()
+    oracle.rqrcp(A, k_s, b, p, Om)
+    dt = time.perf_counter() - t0
+    gf = counted_flops(ms, ns, k_s, b + p) / dt / 1e9
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    cores = int(omp) if omp else cores
+    desc = f"first {k_s} of {w['k']} pivots ({k_s // b} blocks) on a {ms}x{ns} matrix of the same recipe, {dt:.1f} s"
+    return gf, cores, desc, dt
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def gpu_smi_id(dev_index):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev_index] if vis else dev_index
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1804_05138_gb300 import binding, build as libbuild
+
+    libbuild.build()
+    binding.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    m, n, k, b, p = w["m"], w["n"], w["k"], w["b"], w["p"]
+    l = b + p
+    mixed = w["prec"] == "mixed"
+    F = counted_flops(m, n, k, l)
+    A0 = binding.colmajor(make_input_torch(w, dev, seed=1 + rank))
+    A = torch.empty_like(A0.t()).t()
+    jpvt = torch.empty(n, dtype=torch.int32, device=dev)
+    tau = torch.empty(k, dtype=torch.float64, device=dev)
+    need = binding.rqrcp_workspace_size(m, n, k, b, p, binding.RQRCP_PREC_MIXED if mixed else binding.RQRCP_PREC_FP64)
+    work = binding.workspace(need, dev)
+    stream = torch.cuda.current_stream(dev)
+    call = binding.rqrcp_factor_mixed if mixed else binding.rqrcp_factor
+
+    def one_step(timed_events=None):
+        A.copy_(A0)
+        if timed_events is not None:
+            timed_events[0].record(stream)
+        code = call(A, k, b, p, 0, jpvt, tau, work)
+        if timed_events is not None:
+            timed_events[1].record(stream)
+        if code != 0:
+            raise binding.RQRCPError(code, "factor")
+
+    for _ in range(args.warmup):
+        one_step()
+    code, rank_out = binding.rqrcp_read_status(work)
+    if code != 0:
+        raise binding.RQRCPError(code, "device status (warm-up)")
+
+    sampler = ClockSampler(gpu_smi_id(local_rank))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    binding.rqrcp_profile_begin()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        one_step(evs[i])
+    torch.cuda.synchronize()
+    prof = binding.rqrcp_profile_end()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(bv) for a, bv in evs]
+    code, rank_out = binding.rqrcp_read_status(work)
+    if code != 0:
+        raise binding.RQRCPError(code, "device status (timed)")
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * F / (ms_per_step * 1e-3) / 1e9
+
+    # dominant kernel and its roofline (alu: FP64 DFMA pipe; mixed: FP32 SIMT)
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    launches_total = sum(v["launches"] for v in prof.values())
+    kernels_per_launch_class = {"swap": 2, "bupdate": 2}
+    gpu_launches = sum(v["launches"] * kernels_per_launch_class.get(kname, 1) for kname, v in prof.items())
+    gpu_launches += args.steps  # status/jpvt init kernel, one per factorization
+    achieved_tflops = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    if mixed:
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max clock
+        roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp32_peak, 4), "traffic": None,
+                "kernel": dname, "peak_source": "FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    else:
+        roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                "kernel": dname, "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; DFMA pipe)"}
+    kernel_share = {kname: round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)
+                    for kname, v in prof.items() if v["launches"]}
+
+    # end to end through the public API with host buffers
+    # host buffers hold the column-major matrix as a contiguous (n, m) row-major array
+    host_A = A0.t().contiguous().cpu().pin_memory()
+    host_out = torch.empty_like(host_A).pin_memory()
+    host_jpvt = torch.empty(n, dtype=torch.int32).pin_memory()
+    host_tau = torch.empty(k, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_e2e = []
+    for _ in range(e2e_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A.t().copy_(host_A, non_blocking=True)
+        code = call(A, k, b, p, 0, jpvt, tau, work)
+        if code != 0:
+            raise binding.RQRCPError(code, "factor (e2e)")
+        host_out.copy_(A.t(), non_blocking=True)
+        host_jpvt.copy_(jpvt, non_blocking=True)
+        host_tau.copy_(tau, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e.append(e0.elapsed_time(e1))
+    e2e_ms = sum(t_e2e) / len(t_e2e)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    esz = A.element_size()
+    e2e = {"value": round(world * F / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+           "h2d_bytes_per_step": m * n * esz, "d2h_bytes_per_step": m * n * esz + n * 4 + k * 8,
+           "ms_per_step": round(e2e_ms, 3)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "b": b, "p": p,
+                   "counted_gflop_per_step": round(F / 1e9, 3),
+                   "l2": "inputs larger than L2: the 512 MB+ input is rewritten from a pristine copy before every step",
+                   "parallelism": "replicas" if world > 1 else "single", "rank_out": rank_out},
+        "roofline": roof,
+        "kernel_time_share": kernel_share,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="fp64_8192_iid", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        per_step = []
+        desc = cores = None
+        gf_last = None
+        for _ in range(args.warmup):
+            oracle_sample(w, target_s=2.0)
+        for _ in range(args.steps):
+            gf, cores, desc, dt = oracle_sample(w, target_s=8.0)
+            per_step.append(dt)
+            gf_last = gf
+        line = {"impl": "reference", "metric": METRIC, "value": round(gf_last, 4), "unit": "GFLOP/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1e3 * sum(per_step) / len(per_step), 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "b": w["b"], "p": w["p"]},
+                "cpu_baseline": {"value": round(gf_last, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": round(gf_last, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = run_ours(args, w, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gf, cores, desc, dt = oracle_sample(w, target_s=15.0)
+        out["cpu_baseline"] = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                               "sample": desc}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

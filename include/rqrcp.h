@@ -1,0 +1,147 @@
+/*
+ * rqrcp.h -- C ABI of librqrcp, a GB300 (sm_103a) implementation of randomized QR with
+ * column pivoting (RQRCP) from Xiao, Gu, Langou, "Fast parallel randomized QR with column
+ * pivoting algorithms for reliable low-rank matrix approximations" (HiPC 2017).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are column-major: element (i,j) of X with leading dimension ldx is X[j*ldx+i].
+ *    Indices are 0-based (the paper is 1-based).
+ *  - A sketching matrix Omega is row-major l x m: element (r,q) is Omega[r*ldo+q], ldo >= m.
+ *  - Every pointer named A, B, Omega, jpvt, tau, L, Q1, work is a DEVICE pointer on the
+ *    current CUDA device, owned by the caller; the library allocates no device memory.
+ *    Scratch space comes from `work` (size from rqrcp_workspace_size, 256-byte aligned).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only enqueue work;
+ *    they return before it runs.  rqrcp_read_status synchronises the stream and reports
+ *    device-side failures of the last call that used `work`.
+ *  - Return value: 0 on success; -i when the i-th argument (1-based) is invalid, as in
+ *    LAPACK's info; a positive RQRCP_ERR_* code otherwise.  Invalid arguments are
+ *    rejected before anything is enqueued.
+ *  - Calls that share `work` must not overlap on the GPU; distinct work buffers may run
+ *    concurrently on distinct streams.
+ */
+#ifndef RQRCP_H
+#define RQRCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RQRCP_OK 0
+#define RQRCP_ERR_CUDA 1        /* a CUDA runtime call failed (launch, memset, sync) */
+#define RQRCP_ERR_NONFINITE 2   /* the sketch of A holds NaN or Inf: A is not finite */
+#define RQRCP_ERR_TIMEOUT 3     /* a grid-wide barrier inside a kernel gave up waiting */
+#define RQRCP_ERR_WORKSPACE 4   /* work is NULL, misaligned or smaller than required */
+#define RQRCP_ERR_UNSUPPORTED 5 /* the shape exceeds what this build keeps on chip */
+
+#define RQRCP_PREC_FP64 0  /* plain form: every step in IEEE double */
+#define RQRCP_PREC_MIXED 1 /* mixed form: FP32 storage, FP64 reflector generation */
+
+/* Human-readable text for a return code (static string, never NULL). */
+const char* rqrcp_error_string(int code);
+
+/*
+ * Bytes of scratch that rqrcp_factor / rqrcp_factor_with_omega (precision FP64) or
+ * rqrcp_factor_mixed (precision MIXED) need for an m x n problem with target rank k,
+ * block size b and oversampling p.  Returns 0 if the arguments are invalid.
+ */
+size_t rqrcp_workspace_size(int64_t m, int64_t n, int64_t k, int64_t b, int64_t p, int precision);
+
+/*
+ * Gaussian sketching matrix of Alg. 2 ("Generate i.i.d Gaussian matrix Omega in
+ * N(0,1)^{(b+p) x m}").  Writes Omega (l x m, row-major, ldo >= m) on the device.
+ * Element with flat index q = r*m + c is lane q%4 of Philox4x64-10 (Salmon et al.,
+ * SC'11) evaluated at counter (q/4,0,0,0) with key (seed,0); lanes (0,1) and (2,3) are
+ * Box-Muller pairs: u1 = ((w0>>11)+1)*2^-53, u2 = (w1>>11)*2^-53,
+ * z_even = sqrt(-2 ln u1) cos(2 pi u2), z_odd = sqrt(-2 ln u1) sin(2 pi u2).
+ * The _f32 twin rounds the same doubles to float.
+ */
+int rqrcp_generate_omega(int64_t l, int64_t m, uint64_t seed, double* Omega, int64_t ldo, void* stream);
+int rqrcp_generate_omega_f32(int64_t l, int64_t m, uint64_t seed, float* Omega, int64_t ldo, void* stream);
+
+/*
+ * Sketch B = Omega A (Alg. 2, "Compute B = Omega A").  A is m x n (lda >= m), Omega is
+ * l x m row-major (ldo >= m), B is l x n (ldb >= l).  FP64 throughout.  `work` needs
+ * rqrcp_workspace_size(m, n, 1, l, 0, RQRCP_PREC_FP64) bytes.
+ */
+int rqrcp_sketch(int64_t m, int64_t n, const double* A, int64_t lda, const double* Omega, int64_t l,
+                 int64_t ldo, double* B, int64_t ldb, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Randomized QRCP, Alg. 2, plain FP64 form, with the sketch drawn from `seed` as in
+ * rqrcp_generate_omega.  Requires 1 <= k <= min(m,n), b >= 1, p >= 0, lda >= m.
+ * Block by block (block size bb = min(b, k-i)): partial QRCP on the sketch B picks bb
+ * pivots, the columns of A are swapped, the panel A(i:m, i:i+bb) gets an unpivoted
+ * Householder QR, the trailing columns get the compact-WY update Q^T, and B is updated
+ * by Eq. (4) (B(0:bb,trail) <- R_hat12 - R_hat11 R11^{-1} R12) without re-sketching.
+ * Output mirrors LAPACK xGEQP3: A holds R in its upper trapezoid (rows 0..k-1) and the
+ * updated trailing block R22 = A(k:m, k:n); the reflector tails sit below the diagonal of
+ * columns 0..k-1 (xLARFG convention, v(0) = 1 implied); tau[0..k) their scalars;
+ * jpvt[0..n) the permutation, 0-based: column c of A*Pi is column jpvt[c] of the input.
+ * Argmax ties go to the smallest current column position.  Rank guard: if the largest
+ * remaining sketch norm^2 falls to (10*max(m,n)*2^-53)^2 times the largest initial one,
+ * pivoting stops for good (the remaining columns keep their order, B is no longer
+ * updated); rqrcp_read_status reports the pivots taken before that as the rank.
+ * Limits of this build: l = b+p <= 1024 and the sketch and panel must fit in shared
+ * memory across the GPU (checked; RQRCP_ERR_UNSUPPORTED otherwise).
+ */
+int rqrcp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                 uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes, void* stream);
+
+/* As rqrcp_factor, with the l x m sketching matrix Omega (l = b+p, row-major, ldo >= m)
+ * supplied by the caller instead of drawn from a seed. */
+int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
+                            int64_t p, const double* Omega, int64_t ldo, int32_t* jpvt, double* tau,
+                            void* work, size_t work_bytes, void* stream);
+
+/*
+ * Mixed form of Alg. 2: A is FP32 (lda >= m); the sketch, pivot search, trailing
+ * updates and Eq. (4) run in FP32 arithmetic; every Householder reflector (column norm,
+ * beta, tau) of the panel is generated in FP64 and tau is returned in FP64.  Arguments
+ * and output layout as in rqrcp_factor.
+ */
+int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                       uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
+                       void* stream);
+
+/*
+ * Synchronises `stream`, then reads the device-side status left in `work` by the last
+ * factorization: returns RQRCP_OK, RQRCP_ERR_NONFINITE or RQRCP_ERR_TIMEOUT (or
+ * RQRCP_ERR_CUDA if the synchronisation itself fails) and stores the rank (number of
+ * pivots chosen before the rank guard fired, k if it never fired) in *rank if non-NULL.
+ */
+int rqrcp_read_status(const void* work, int64_t* rank, void* stream);
+
+/*
+ * Low-rank approximation L = Q1 [R11 R12] Pi^T (Sec. I-A) from the output of
+ * rqrcp_factor: Afact (m x n, ldaf), tau (k), jpvt (n).  L is m x n (ldl >= m); Q1
+ * (required, ldq >= m) receives the m x k matrix Q1 = H_0 ... H_{k-1} I(:,0:k).
+ * `work` needs rqrcp_lowrank_workspace_size(m, n, k) bytes.
+ */
+size_t rqrcp_lowrank_workspace_size(int64_t m, int64_t n, int64_t k);
+int rqrcp_lowrank(int64_t m, int64_t n, int64_t k, const double* Afact, int64_t ldaf, const double* tau,
+                  const int32_t* jpvt, double* L, int64_t ldl, double* Q1, int64_t ldq, void* work,
+                  size_t work_bytes, void* stream);
+
+/*
+ * Kernel-level timing for measurement (not part of the method).  Between
+ * rqrcp_profile_begin and rqrcp_profile_end, every kernel the library enqueues is
+ * bracketed by a pair of CUDA events on its stream, and the algorithmic work of the
+ * launch (flops and bytes that the step must do, not what the kernel happens to move)
+ * is accumulated per kernel class.  rqrcp_profile_end synchronises the device, turns
+ * the recording off and, for each class c < min(nmax, RQRCP_PROFILE_CLASSES), writes
+ * launches[c], the summed event time ms[c], flops[c] and bytes[c] (any pointer may be
+ * NULL).  Host-side state is global to the process; not thread-safe.
+ */
+#define RQRCP_PROFILE_CLASSES 12
+int rqrcp_profile_begin(void);
+int rqrcp_profile_end(int nmax, int64_t* launches, double* ms, double* flops, double* bytes);
+const char* rqrcp_profile_class_name(int cls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RQRCP_H */

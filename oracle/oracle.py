@@ -72,6 +72,8 @@ def _load():
         lib.orc_rqrcp.restype = ctypes.c_int
         lib.orc_form_q.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
         lib.orc_form_q.restype = None
+        lib.orc_apply_q.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp]
+        lib.orc_apply_q.restype = None
         lib.orc_lowrank.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i32p, _dp, _i64, _dp]
         lib.orc_lowrank.restype = ctypes.c_int
         _lib = lib
@@ -167,6 +169,22 @@ def form_q(Af: np.ndarray, tau: np.ndarray, k: int, ncols: int) -> np.ndarray:
     lib.orc_form_q(m, k, _ptr(A, ctypes.c_double), m, _ptr(t, ctypes.c_double), ncols,
                    _ptr(Q, ctypes.c_double), m)
     return Q
+
+
+def apply_q(Af: np.ndarray, tau: np.ndarray, k: int, x: np.ndarray) -> np.ndarray:
+    """Q x = H_0 ... H_{k-1} x for one vector (reflectors read from the factored array)."""
+    lib = _load()
+    A = np.asfortranarray(Af, dtype=np.float64)
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    y = np.array(x, dtype=np.float64, copy=True)
+    lib.orc_apply_q(A.shape[0], k, _ptr(A, ctypes.c_double), A.shape[0], _ptr(t, ctypes.c_double),
+                    _ptr(y, ctypes.c_double))
+    return y
+
+
+def sketch(A: np.ndarray, Omega: np.ndarray) -> np.ndarray:
+    """B = Omega A (Alg. 2), the plain definition."""
+    return np.asarray(Omega, dtype=np.float64) @ np.asarray(A, dtype=np.float64)
 
 
 def r_factor(Af: np.ndarray, k: int) -> np.ndarray:

@@ -338,6 +338,12 @@ ORC_EXPORT void orc_form_q(int64_t m, int64_t k, const double* A, int64_t lda, c
     }
 }
 
+/* x <- H_0 H_1 ... H_{k-1} x for one vector x of length m (Q times x, Alg. 2 output). */
+ORC_EXPORT void orc_apply_q(int64_t m, int64_t k, const double* A, int64_t lda, const double* tau, double* x)
+{
+    for (int64_t h = k - 1; h >= 0; --h) house_apply(m - h, &AT(A, lda, h, h), tau[h], x + h);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Low-rank product L = Q1 [R11 R12] Pi^T (Sec. I-A): column jpvt[c] of L is   */
 /* Q1 times column c of the k x n upper trapezoid of the factored A.  Q1       */

@@ -1,0 +1,272 @@
+"""ctypes binding of librqrcp (include/rqrcp.h): argument marshalling only.
+
+Functions named ``rqrcp_*`` mirror the C entry points one to one and take torch CUDA
+tensors for the device pointers (column-major matrices are tensors of shape (m, n) with
+stride (1, ld)).  ``factor``/``factor_mixed``/``lowrank`` add workspace allocation through
+torch and status checking.  There is no fallback: if the library is missing or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librqrcp.so")
+
+RQRCP_OK = 0
+RQRCP_ERR_CUDA = 1
+RQRCP_ERR_NONFINITE = 2
+RQRCP_ERR_TIMEOUT = 3
+RQRCP_ERR_WORKSPACE = 4
+RQRCP_ERR_UNSUPPORTED = 5
+RQRCP_PREC_FP64 = 0
+RQRCP_PREC_MIXED = 1
+
+# Every symbol include/rqrcp.h declares.
+ABI_SYMBOLS = (
+    "rqrcp_error_string", "rqrcp_workspace_size", "rqrcp_generate_omega", "rqrcp_generate_omega_f32",
+    "rqrcp_sketch", "rqrcp_factor", "rqrcp_factor_with_omega", "rqrcp_factor_mixed",
+    "rqrcp_read_status", "rqrcp_lowrank_workspace_size", "rqrcp_lowrank",
+    "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
+)
+RQRCP_PROFILE_CLASSES = 12
+
+_lock = threading.Lock()
+_lib = None
+
+_i64, _u64, _vp, _sz = ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t
+
+
+class RQRCPError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {code} ({error_string(code)})")
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librqrcp.so (built by paper_1804_05138_gb300.build) and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"librqrcp.so not built ({path}); run paper_1804_05138_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        sig = {
+            "rqrcp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "rqrcp_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i64, ctypes.c_int]),
+            "rqrcp_generate_omega": (ctypes.c_int, [_i64, _i64, _u64, _vp, _i64, _vp]),
+            "rqrcp_generate_omega_f32": (ctypes.c_int, [_i64, _i64, _u64, _vp, _i64, _vp]),
+            "rqrcp_sketch": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _sz, _vp]),
+            "rqrcp_factor": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp, _sz, _vp]),
+            "rqrcp_factor_with_omega": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _vp, _i64, _vp,
+                                                       _vp, _vp, _sz, _vp]),
+            "rqrcp_factor_mixed": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp,
+                                                  _sz, _vp]),
+            "rqrcp_read_status": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
+            "rqrcp_lowrank_workspace_size": (_sz, [_i64, _i64, _i64]),
+            "rqrcp_lowrank": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
+                                             _sz, _vp]),
+            "rqrcp_profile_begin": (ctypes.c_int, []),
+            "rqrcp_profile_end": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i64),
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double)]),
+            "rqrcp_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def error_string(code: int) -> str:
+    return load().rqrcp_error_string(int(code)).decode()
+
+
+# --------------------------------------------------------------------------- tensor helpers
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _ld(t) -> int:
+    """Leading dimension of a column-major (m, n) tensor."""
+    if t.dim() != 2 or t.stride(0) != 1:
+        raise ValueError("expected a column-major 2-D tensor (stride(0) == 1)")
+    return max(int(t.stride(1)), int(t.shape[0]), 1)
+
+
+def _ld_rowmajor(t) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a row-major 2-D tensor (stride(1) == 1)")
+    return max(int(t.stride(0)), int(t.shape[1]), 1)
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def colmajor(A):
+    """Column-major copy (or view) of a 2-D tensor: shape (m, n), stride (1, m)."""
+    if A.dim() == 2 and A.stride(0) == 1 and A.stride(1) >= A.shape[0]:
+        return A
+    return A.t().contiguous().t()
+
+
+def _check(code: int, where: str):
+    if code != RQRCP_OK:
+        raise RQRCPError(code, where)
+
+
+def workspace(nbytes: int, device):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------------------- 1:1 entry points
+def rqrcp_workspace_size(m, n, k, b, p, precision=RQRCP_PREC_FP64) -> int:
+    return int(load().rqrcp_workspace_size(m, n, k, b, p, precision))
+
+
+def rqrcp_lowrank_workspace_size(m, n, k) -> int:
+    return int(load().rqrcp_lowrank_workspace_size(m, n, k))
+
+
+def rqrcp_generate_omega(l, m, seed, Omega, stream=None) -> int:
+    fn = load().rqrcp_generate_omega if Omega.element_size() == 8 else load().rqrcp_generate_omega_f32
+    return fn(l, m, seed, _ptr(Omega), _ld_rowmajor(Omega), _stream(stream))
+
+
+def rqrcp_sketch(A, Omega, B, work, stream=None) -> int:
+    m, n = A.shape
+    l = Omega.shape[0]
+    return load().rqrcp_sketch(m, n, _ptr(A), _ld(A), _ptr(Omega), l, _ld_rowmajor(Omega), _ptr(B), _ld(B),
+                               _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
+    m, n = A.shape
+    return load().rqrcp_factor(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(work),
+                               work.numel(), _stream(stream))
+
+
+def rqrcp_factor_with_omega(A, k, b, p, Omega, jpvt, tau, work, stream=None) -> int:
+    m, n = A.shape
+    return load().rqrcp_factor_with_omega(m, n, _ptr(A), _ld(A), k, b, p, _ptr(Omega), _ld_rowmajor(Omega),
+                                          _ptr(jpvt), _ptr(tau), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
+    m, n = A.shape
+    return load().rqrcp_factor_mixed(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(work),
+                                     work.numel(), _stream(stream))
+
+
+def rqrcp_read_status(work, stream=None) -> tuple[int, int]:
+    rank = _i64(0)
+    code = load().rqrcp_read_status(_ptr(work), ctypes.byref(rank), _stream(stream))
+    return int(code), int(rank.value)
+
+
+def rqrcp_lowrank(Afact, k, tau, jpvt, L, Q1, work, stream=None) -> int:
+    m, n = Afact.shape
+    return load().rqrcp_lowrank(m, n, k, _ptr(Afact), _ld(Afact), _ptr(tau), _ptr(jpvt), _ptr(L), _ld(L),
+                                _ptr(Q1), _ld(Q1), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_profile_begin() -> int:
+    return int(load().rqrcp_profile_begin())
+
+
+def rqrcp_profile_end() -> dict:
+    """Per kernel class: {name: {"launches", "ms", "flops", "bytes"}} since rqrcp_profile_begin."""
+    n = RQRCP_PROFILE_CLASSES
+    launches = (_i64 * n)()
+    ms = (ctypes.c_double * n)()
+    fl = (ctypes.c_double * n)()
+    by = (ctypes.c_double * n)()
+    _check(load().rqrcp_profile_end(n, launches, ms, fl, by), "rqrcp_profile_end")
+    out = {}
+    for c in range(n):
+        name = load().rqrcp_profile_class_name(c).decode()
+        out[name] = {"launches": int(launches[c]), "ms": float(ms[c]), "flops": float(fl[c]), "bytes": float(by[c])}
+    return out
+
+
+# --------------------------------------------------------------------------- convenience layer
+@dataclass
+class Factorization:
+    A: object      # factored matrix (R above the diagonal, reflectors below), column-major
+    jpvt: object   # int32 permutation, column c of A*Pi is input column jpvt[c]
+    tau: object    # float64 Householder scalars, length k
+    rank: int      # pivots chosen before the rank guard fired
+    k: int
+
+
+def _run_factor(A, k, b, p, seed, omega, mixed, work, stream):
+    import torch
+    m, n = A.shape
+    dev = A.device
+    jpvt = torch.empty(n, dtype=torch.int32, device=dev)
+    tau = torch.empty(k, dtype=torch.float64, device=dev)
+    need = rqrcp_workspace_size(m, n, k, b, p, RQRCP_PREC_MIXED if mixed else RQRCP_PREC_FP64)
+    if need == 0:
+        raise ValueError("invalid factorization arguments")
+    if work is None or work.numel() < need:
+        work = workspace(need, dev)
+    if mixed:
+        code = rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream)
+    elif omega is None:
+        code = rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream)
+    else:
+        code = rqrcp_factor_with_omega(A, k, b, p, omega, jpvt, tau, work, stream)
+    _check(code, "rqrcp_factor_mixed" if mixed else "rqrcp_factor")
+    status, rank = rqrcp_read_status(work, stream)
+    _check(status, "device status")
+    return Factorization(A, jpvt, tau, rank, k)
+
+
+def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=None, stream=None,
+           overwrite: bool = False) -> Factorization:
+    """Randomized QRCP of a float64 CUDA matrix (plain FP64 form).  ``omega`` (row-major
+    (b+p) x m float64 CUDA tensor) replaces the seeded sketch when given."""
+    import torch
+    if A.dtype != torch.float64:
+        raise TypeError("factor expects float64; use factor_mixed for float32")
+    Acm = colmajor(A)
+    if not overwrite:
+        Acm = Acm.t().clone().t()
+    return _run_factor(Acm, k, b, p, seed, omega, False, work, stream)
+
+
+def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,
+                 overwrite: bool = False) -> Factorization:
+    """Randomized QRCP of a float32 CUDA matrix (mixed form, FP64 reflectors)."""
+    import torch
+    if A.dtype != torch.float32:
+        raise TypeError("factor_mixed expects float32")
+    Acm = colmajor(A)
+    if not overwrite:
+        Acm = Acm.t().clone().t()
+    return _run_factor(Acm, k, b, p, seed, None, True, work, stream)
+
+
+def lowrank(f: Factorization, stream=None):
+    """L = Q1 [R11 R12] Pi^T and Q1 from a plain FP64 factorization."""
+    import torch
+    m, n = f.A.shape
+    k = f.k
+    dev = f.A.device
+    L = torch.empty((n, m), dtype=torch.float64, device=dev).t()
+    Q1 = torch.empty((k, m), dtype=torch.float64, device=dev).t()
+    work = workspace(rqrcp_lowrank_workspace_size(m, n, k), dev)
+    _check(rqrcp_lowrank(f.A, k, f.tau, f.jpvt, L, Q1, work, stream), "rqrcp_lowrank")
+    status, _ = rqrcp_read_status(work, stream)
+    _check(status, "device status")
+    return L, Q1

@@ -1,0 +1,364 @@
+// gemm.cu -- SIMT contractions of the RQRCP hot loop (FP64 and FP32 storage).
+//
+//  gemm_tn   : split-K partials of X^T C for a short-and-wide result (M <= ~128 rows):
+//              the sketch B = Omega A (X = Omega^T) and W = V^T [V C] of the compact-WY
+//              update (X = V, first bb columns of C are V itself, giving the Gram V^T V).
+//  gemm_update: C -= V Y, the rank-bb trailing update of Alg. 2 ("A(i:m,i+b:n) <- Q^T A").
+//  sketch_reduce / tform / reduce_y: fixed-order reductions of the split-K partials, the
+//              initial sketch norms, and the compact-WY factor T (LAPACK xLARFT, forward,
+//              columnwise: T(j,j) = tau_j, T(0:j,j) = -tau_j T(0:j,0:j) V(:,0:j)^T v_j).
+//
+// Both contractions are K-major reads of column-major operands staged through shared
+// memory in 16-deep slices; each thread owns a 4x4 register tile strided by 16 so that
+// shared-memory reads are conflict-free and global reads are 128-byte coalesced.
+#include "internal.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+
+// Value of the reflector matrix V at (row q, column r) given the stored entry.
+template <typename T>
+__device__ __forceinline__ T vmask(T stored, int64_t q, int64_t r)
+{
+    return q > r ? stored : (q == r ? T(1) : T(0));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, int64_t ldx,
+                                                     const T* __restrict__ C, int64_t ldc, int64_t M,
+                                                     int64_t N, int64_t K, int64_t kchunk,
+                                                     double* __restrict__ P, int maskX, int64_t maskC,
+                                                     const Status* st)
+{
+    if (status_error(st)) return;
+    __shared__ T Xs[TK][TM + 1];
+    __shared__ T Cs[TK][TN + 1];
+    const int tid = threadIdx.x;
+    const int tm = tid & 15, tn = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * TM;
+    const int64_t n0 = (int64_t)blockIdx.y * TN;
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    const int64_t kend = min(K, kbeg + kchunk);
+
+    // Two-level accumulation: a 64-deep inner sum in T, folded into an outer T sum.
+    T acc[4][4], outer[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = outer[a][b] = T(0);
+
+    int inner = 0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
+#pragma unroll
+        for (int it = 0; it < (TK * TM) / NT; ++it) {
+            const int e = tid + it * NT;
+            const int kk = e & (TK - 1);
+            const int mm = e / TK;
+            const int64_t q = k0 + kk;
+            const int64_t r = m0 + mm;
+            T v = T(0);
+            if (q < kend && r < M) {
+                v = X[r * ldx + q];
+                if (maskX) v = vmask(v, q, r);
+            }
+            Xs[kk][mm] = v;
+        }
+#pragma unroll
+        for (int it = 0; it < (TK * TN) / NT; ++it) {
+            const int e = tid + it * NT;
+            const int kk = e & (TK - 1);
+            const int nn = e / TK;
+            const int64_t q = k0 + kk;
+            const int64_t c = n0 + nn;
+            T v = T(0);
+            if (q < kend && c < N) {
+                v = C[c * ldc + q];
+                if (c < maskC) v = vmask(v, q, c);
+            }
+            Cs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            T xa[4], cb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][tm + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cb[b] = Cs[kk][tn + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], cb[b], acc[a][b]);
+        }
+        __syncthreads();
+        if (++inner == 4) {
+            inner = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    outer[a][b] += acc[a][b];
+                    acc[a][b] = T(0);
+                }
+        }
+    }
+    double* Pz = P + (int64_t)blockIdx.z * N * M;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int64_t c = n0 + tn + 16 * b;
+        if (c >= N) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t r = m0 + tm + 16 * a;
+            if (r < M) Pz[c * M + r] = (double)outer[a][b] + (double)acc[a][b];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) gemm_update_kernel(T* __restrict__ C, int64_t ldc,
+                                                         const T* __restrict__ V, int64_t ldv,
+                                                         const double* __restrict__ Y, int64_t ldy,
+                                                         int64_t mr, int64_t nc, int64_t kb, int maskV,
+                                                         const int32_t* __restrict__ colmap,
+                                                         const Status* st)
+{
+    if (status_error(st)) return;
+    __shared__ T Vs[TK][TM + 1];
+    __shared__ T Ys[TK][TN + 1];
+    const int tid = threadIdx.x;
+    const int tm = tid & 15, tn = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * TM;
+    const int64_t c0 = (int64_t)blockIdx.y * TN;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+
+    for (int64_t q0 = 0; q0 < kb; q0 += TK) {
+#pragma unroll
+        for (int it = 0; it < (TK * TM) / NT; ++it) {
+            const int e = tid + it * NT;
+            const int rr = e & (TM - 1);
+            const int kk = e / TM;
+            const int64_t r = r0 + rr, q = q0 + kk;
+            T v = T(0);
+            if (r < mr && q < kb) {
+                v = V[q * ldv + r];
+                if (maskV) v = vmask(v, r, q);
+            }
+            Vs[kk][rr] = v;
+        }
+#pragma unroll
+        for (int it = 0; it < (TK * TN) / NT; ++it) {
+            const int e = tid + it * NT;
+            const int kk = e & (TK - 1);
+            const int cc = e / TK;
+            const int64_t q = q0 + kk, c = c0 + cc;
+            Ys[kk][cc] = (q < kb && c < nc) ? (T)Y[c * ldy + q] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            T va[4], yb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) va[a] = Vs[kk][tm + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) yb[b] = Ys[kk][tn + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(va[a], yb[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int64_t c = c0 + tn + 16 * b;
+        if (c >= nc) continue;
+        const int64_t cd = colmap ? (int64_t)colmap[c] : c;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t r = r0 + tm + 16 * a;
+            if (r < mr) C[cd * ldc + r] -= acc[a][b];
+        }
+    }
+}
+
+// One warp per column of B: sum the split-K partials in split order, store, and fold the
+// column norm^2 into the running maximum (non-negative doubles order like their bits).
+template <typename T>
+__global__ void sketch_reduce_kernel(const double* __restrict__ P, int nsplit, int64_t l, int64_t n,
+                                     T* __restrict__ B, int64_t ldb, Status* st)
+{
+    if (status_error(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    double nu = 0.0;
+    bool finite = true;
+    for (int64_t r = lane; r < l; r += 32) {
+        double s = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * n + j) * l + r];
+        const T v = (T)s;
+        B[j * ldb + r] = v;
+        finite = finite && isfinite((double)v);
+        nu += (double)v * (double)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nu += __shfl_xor_sync(0xffffffffu, nu, o);
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) {
+        if (!finite || !isfinite(nu)) set_error(st, RQRCP_ERR_NONFINITE);
+        else atomicMax(&st->nu0bits, (unsigned long long)__double_as_longlong(nu));
+    }
+}
+
+// Single block: Gram = V^T V from the partials of the first bb columns (kept in the output
+// buffer Tm as scratch), then T column by column in shared memory, then T overwrites Tm.
+__global__ void tform_kernel(const double* __restrict__ P, int nsplit, int64_t ncols, int bb,
+                             const double* __restrict__ tau, double* __restrict__ Tm, const Status* st)
+{
+    if (status_error(st)) return;
+    extern __shared__ double Ts[];  // bb x bb, column-major
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
+        const int q = e % bb, j = e / bb;
+        double s = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * ncols + j) * bb + q];
+        Tm[e] = s;
+        Ts[e] = 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < bb; ++j) {
+        const double tj = tau[j];
+        for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+            if (r < j) {
+                double s = 0.0;
+                for (int q = r; q < j; ++q) s += Ts[q * bb + r] * Tm[j * bb + q];
+                Ts[j * bb + r] = -tj * s;
+            } else {
+                Ts[j * bb + j] = tj;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Tm[e] = Ts[e];
+}
+
+// One warp per column c: W = sum of partials (column c0 + c), Y(:,c) = T^T W (transT) or T W.
+__global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_t ncols, int64_t c0, int bb,
+                                const double* __restrict__ Tm, int transT, double* __restrict__ Y, int64_t nc,
+                                const Status* st)
+{
+    if (status_error(st)) return;
+    extern __shared__ double sm[];
+    double* Ts = sm;                      // bb x bb
+    const int nw = blockDim.x / 32;
+    double* Wsh = sm + bb * bb;           // nw x bb
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Ts[e] = Tm[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double* Wc = Wsh + w * bb;
+    for (int64_t c = (int64_t)blockIdx.x * nw + w; c < nc; c += (int64_t)gridDim.x * nw) {
+        const int64_t col = c0 + c;
+        for (int q = lane; q < bb; q += 32) {
+            double s = 0.0;
+            for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * ncols + col) * bb + q];
+            Wc[q] = s;
+        }
+        __syncwarp();
+        for (int r = lane; r < bb; r += 32) {
+            double s = 0.0;
+            if (transT)
+                for (int q = 0; q <= r; ++q) s += Ts[r * bb + q] * Wc[q];
+            else
+                for (int q = r; q < bb; ++q) s += Ts[q * bb + r] * Wc[q];
+            Y[c * bb + r] = s;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int64_t M, int64_t N,
+                           int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,
+                           const Status* st, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((N + TN - 1) / TN), (unsigned)((K + kchunk - 1) / kchunk));
+    gemm_tn_kernel<T><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gemm_update(T* C, int64_t ldc, const T* V, int64_t ldv, const double* Y, int64_t ldy,
+                               int64_t mr, int64_t nc, int64_t kb, int maskV, const int32_t* colmap,
+                               const Status* st, cudaStream_t s)
+{
+    if (mr <= 0 || nc <= 0 || kb <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((mr + TM - 1) / TM), (unsigned)((nc + TN - 1) / TN));
+    gemm_update_kernel<T><<<grid, NT, 0, s>>>(C, ldc, V, ldv, Y, ldy, mr, nc, kb, maskV, colmap, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sketch_reduce(const double* P, int nsplit, int64_t l, int64_t n, T* B, int64_t ldb,
+                                 Status* st, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256, cols_per_block = threads / 32;
+    sketch_reduce_kernel<T><<<(unsigned)((n + cols_per_block - 1) / cols_per_block), threads, 0, s>>>(
+        P, nsplit, l, n, B, ldb, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, const double* tau,
+                         double* Tm, const Status* st, cudaStream_t s)
+{
+    const size_t smem = sizeof(double) * (size_t)bb * bb;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaError_t e = allow_max_dynamic_smem(tform_kernel)) return e;
+        attr_set = true;
+    }
+    tform_kernel<<<1, 128, smem, s>>>(P, nsplit, ncols, bb, tau, Tm, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t c0, int bb, const double* Tm,
+                            int transT, double* Y, int64_t nc, const Status* st, cudaStream_t s)
+{
+    if (nc <= 0) return cudaSuccess;
+    const int threads = 256, nw = threads / 32;
+    const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)nw * bb);
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaError_t e = allow_max_dynamic_smem(reduce_y_kernel)) return e;
+        attr_set = true;
+    }
+    int64_t grid = (nc + nw - 1) / nw;
+    const int64_t cap = (int64_t)dev_info().sms * 4;
+    if (grid > cap) grid = cap;
+    reduce_y_kernel<<<(unsigned)grid, threads, smem, s>>>(P, nsplit, ncols, c0, bb, Tm, transT, Y, nc, st);
+    return cudaGetLastError();
+}
+
+#define RQ_INST(T)                                                                                   \
+    template cudaError_t launch_gemm_tn<T>(const T*, int64_t, const T*, int64_t, int64_t, int64_t,  \
+                                           int64_t, int64_t, double*, int, int64_t, const Status*,  \
+                                           cudaStream_t);                                           \
+    template cudaError_t launch_gemm_update<T>(T*, int64_t, const T*, int64_t, const double*,       \
+                                               int64_t, int64_t, int64_t, int64_t, int,             \
+                                               const int32_t*, const Status*, cudaStream_t);        \
+    template cudaError_t launch_sketch_reduce<T>(const double*, int, int64_t, int64_t, T*, int64_t, \
+                                                 Status*, cudaStream_t);
+RQ_INST(double)
+RQ_INST(float)
+#undef RQ_INST
+
+}  // namespace rq

@@ -1,0 +1,172 @@
+// internal.cuh -- shared device helpers and kernel launchers of librqrcp (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rqrcp.h"
+
+namespace rq {
+
+// Device-side status block at the head of every workspace (zeroed by the host before a call).
+struct Status {
+    int error;                     // RQRCP_OK or an RQRCP_ERR_* code set by a kernel
+    int guard;                     // 1 once the rank guard fired
+    long long rank;                // pivots chosen before the guard fired
+    unsigned int bar_count;        // grid barrier arrival counter
+    unsigned int bar_gen;          // grid barrier generation
+    unsigned long long nu0bits;    // bits of the largest initial sketch column norm^2 (>= 0)
+    long long pad[12];
+};
+static_assert(sizeof(Status) <= 256, "status block must fit in 256 bytes");
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per barrier wait
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int status_error(const Status* st)
+{
+    return *(volatile const int*)&st->error;
+}
+
+__device__ __forceinline__ void set_error(Status* st, int code)
+{
+    atomicCAS(&st->error, 0, code);
+}
+
+// Grid-wide barrier for cooperatively launched kernels.  Every wait is bounded: after
+// kWaitLimitNs the block records RQRCP_ERR_TIMEOUT and the barrier returns false, as it
+// does when any block has recorded an error; callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(Status* st)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &st->bar_gen;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            while (*vgen == gen) {
+                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                    set_error(st, RQRCP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (status_error(st)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------------------------------
+// Launchers (each returns cudaSuccess or the launch error).
+// ---------------------------------------------------------------------------------------
+struct DevInfo {
+    int sms;
+    int max_smem_optin;
+};
+const DevInfo& dev_info();
+
+// Allow a kernel the largest dynamic shared memory the device grants next to the kernel's
+// own static shared memory.  Returns the runtime error, if any.
+template <typename K>
+cudaError_t allow_max_dynamic_smem(K kernel)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kernel);
+    if (e != cudaSuccess) return e;
+    const int maxdyn = dev_info().max_smem_optin - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
+}
+
+// Omega (l x m row-major) from Philox4x64-10 + Box-Muller.
+template <typename T>
+cudaError_t launch_omega(int64_t l, int64_t m, uint64_t seed, T* Om, int64_t ldo, cudaStream_t s);
+
+// Split-K partial products P[sp][c][r] = sum_{q in chunk sp} X(q, r) * C(q, c), r < M, c < N.
+// X is K x M column-major (ldx), C is K x N column-major (ldc).  maskX: X has the unit-lower
+// reflector structure (X(q,r) = 0 for q < r, 1 for q == r).  maskC: the first maskC columns
+// of C have the same structure.  kchunk must be a multiple of 16.
+template <typename T>
+cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int64_t M, int64_t N,
+                           int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,
+                           const Status* st, cudaStream_t s);
+
+// C(mr x nc) -= V(mr x kb) * Y(kb x nc).  maskV: V has the unit-lower reflector structure.
+// colmap (optional): column c of the product goes to column colmap[c] of C.
+template <typename T>
+cudaError_t launch_gemm_update(T* C, int64_t ldc, const T* V, int64_t ldv, const double* Y, int64_t ldy,
+                               int64_t mr, int64_t nc, int64_t kb, int maskV, const int32_t* colmap,
+                               const Status* st, cudaStream_t s);
+
+// B(0:l, j) = sum_sp P[sp][j][0:l]; records max column norm^2 and non-finite entries.
+template <typename T>
+cudaError_t launch_sketch_reduce(const double* P, int nsplit, int64_t l, int64_t n, T* B, int64_t ldb,
+                                 Status* st, cudaStream_t s);
+
+// Gram = sum_sp P[sp][0:bb][0:bb]; T (bb x bb, forward columnwise compact WY) from Gram and tau.
+cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, const double* tau,
+                         double* Tm, const Status* st, cudaStream_t s);
+
+// Y(:, c) = op(T) * sum_sp P[sp][c0 + c][0:bb], c < nc, op(T) = T^T if transT else T.
+cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t c0, int bb, const double* Tm,
+                            int transT, double* Y, int64_t nc, const Status* st, cudaStream_t s);
+
+// Cooperative pivot search on B(:, i:n) (bb steps of QRCP on the sketch).  `cand` is
+// pivot_cand_bytes(l) of candidate buffers followed by the swap map (1 + 4*bb int64).
+template <typename T>
+cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int32_t* jpvt,
+                         int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s);
+size_t pivot_cand_bytes(int l);
+
+// Column swaps of A following the net column map written by the pivot kernel
+// (swapmap[0] = count, then (destination, source) position pairs); tmp holds 2*bb columns.
+template <typename T>
+cudaError_t launch_swaps(T* A, int64_t lda, int64_t m, int bb, const long long* swapmap, T* tmp,
+                         const Status* st, cudaStream_t s);
+
+// Status block reset (rank = k) and jpvt = 0..n-1.
+cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s);
+
+// Cooperative Householder panel QR of A(i:m, i:i+bb) (FP64 reflector generation).
+template <typename T>
+cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, double* part, Status* st,
+                         cudaStream_t s);
+size_t panel_part_bytes(int bb);
+bool panel_fits(int64_t m1, int bb, int elem_bytes);
+bool pivot_fits(int64_t ncols, int l, int elem_bytes);
+
+// Eq. (4): Omega_hat_11 = R_hat11 R11^{-1}, then B(0:bb, i+bb:n) -= Omega_hat_11 R12.
+template <typename T>
+cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i, int bb, int64_t n,
+                           double* What, const Status* st, cudaStream_t s);
+
+// Opt-in kernel timing (prof.cu): classes in the order of rqrcp_profile_class_name.
+enum ProfClass {
+    K_OMEGA = 0, K_SKETCH_GEMM, K_SKETCH_REDUCE, K_PIVOT, K_SWAP, K_PANEL,
+    K_WY_GEMM, K_TFORM, K_REDUCE_Y, K_WY_UPDATE, K_BUPDATE, K_LOWRANK_MISC
+};
+bool prof_on();
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, double flops, double bytes, cudaStream_t s);
+
+}  // namespace rq

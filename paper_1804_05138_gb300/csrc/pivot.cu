@@ -1,0 +1,300 @@
+// pivot.cu -- "Partial QRCP on B(:,i:n) to get b pivots" (Alg. 2), i.e. Alg. 1 run on the
+// l x (n-i) sketch for bb steps, as one cooperative kernel.
+//
+// Each block keeps a contiguous slice of B's trailing columns in shared memory for the whole
+// block of pivot steps.  Per step t (pivot position c = i + t):
+//   1. every block finds its best column by squared norm of rows t..l-1 (recomputed, Alg. 1
+//      "Update r_s"), ties to the smallest current position, and publishes the value, the
+//      position and the whole column into a double-buffered candidate slot;
+//   2. one bounded grid barrier;
+//   3. every block reads all candidates, picks the same winner, regenerates the same
+//      Householder reflector (xLARFG convention, FP64) from the winner's column and applies
+//      it to its own columns.  The swap "c <-> winner" is pure bookkeeping: the slot that
+//      held position c takes the winner's old position.
+// After the last step the slices are written back to B in the new column order, block 0
+// applies the transpositions to jpvt and records the net column map used to swap A.
+// Rank guard: if the best remaining norm^2 is not above guard_rel2 * (largest initial
+// sketch norm^2), pivoting stops for good at this step.
+#include <climits>
+
+#include "internal.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int kMaxCand = 1024;  // maximum blocks of the cooperative launch
+
+__device__ __forceinline__ bool better(double v1, long long p1, double v2, long long p2)
+{
+    return v1 > v2 || (v1 == v2 && p1 < p2);
+}
+
+// Block-wide argmax over (value, position) pairs; result broadcast through shared memory.
+__device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long long* sp, int* si)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long op = __shfl_xor_sync(0xffffffffu, p, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (better(ov, op, v, p)) { v = ov; p = op; idx = oi; }
+    }
+    __syncthreads();
+    if (lane == 0) { sv[w] = v; sp[w] = p; si[w] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k)
+            if (better(sv[k], sp[k], sv[0], sp[0])) { sv[0] = sv[k]; sp[0] = sp[k]; si[0] = si[k]; }
+    }
+    __syncthreads();
+    v = sv[0]; p = sp[0]; idx = si[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t ldb, int l, int64_t n,
+                                                     int64_t i, int bb, int64_t cpb,
+                                                     int32_t* __restrict__ jpvt, int32_t* __restrict__ piv,
+                                                     long long* __restrict__ swapmap,
+                                                     double* __restrict__ cval, long long* __restrict__ cpos,
+                                                     T* __restrict__ ccol, double guard_rel2, Status* st)
+{
+    if (status_error(st)) return;
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, NTH = blockDim.x;
+    if (*(volatile int*)&st->guard) {  // pivoting switched off by an earlier block
+        if (g == 0) {
+            for (int t = tid; t < bb; t += NTH) piv[t] = (int32_t)(i + t);
+            if (tid == 0) swapmap[0] = 0;
+        }
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ldS = l | 1;  // odd stride: conflict-free column-per-thread access
+    T* cols = reinterpret_cast<T*>(smem_raw);
+    size_t off = ((size_t)cpb * ldS * sizeof(T) + 15) & ~(size_t)15;
+    long long* pos = reinterpret_cast<long long*>(smem_raw + off);
+    off += (size_t)cpb * sizeof(long long);
+    double* xs = reinterpret_cast<double*>(smem_raw + off);
+    off += (size_t)l * sizeof(double);
+    T* vT = reinterpret_cast<T*>(smem_raw + off);
+    off += ((size_t)l * sizeof(T) + 15) & ~(size_t)15;
+    long long* pivs = reinterpret_cast<long long*>(smem_raw + off);
+    off += (size_t)bb * sizeof(long long);
+    int* active = reinterpret_cast<int*>(smem_raw + off);
+
+    __shared__ double red_v[32];
+    __shared__ long long red_p[32];
+    __shared__ int red_i[32];
+    __shared__ double sh_tau, sh_beta, sh_scal;
+
+    const int64_t nprime = n - i;
+    const int64_t s0 = (int64_t)g * cpb;
+    const int nloc = (int)max((int64_t)0, min(cpb, nprime - s0));
+    for (int64_t e = tid; e < (int64_t)nloc * l; e += NTH) {
+        const int s = (int)(e / l), r = (int)(e % l);
+        cols[(size_t)s * ldS + r] = B[(i + s0 + s) * ldb + r];
+    }
+    for (int s = tid; s < nloc; s += NTH) {
+        pos[s] = i + s0 + s;
+        active[s] = 1;
+    }
+    __syncthreads();
+    const double guard = guard_rel2 * __longlong_as_double((long long)st->nu0bits);
+
+    int steps = bb;
+    for (int t = 0; t < bb; ++t) {
+        const long long c = i + t;
+        const int buf = t & 1;
+        // 1. local candidate
+        double myv = -1.0;
+        long long myp = LLONG_MAX;
+        int mys = -1;
+        for (int s = tid; s < nloc; s += NTH) {
+            if (!active[s]) continue;
+            const T* col = cols + (size_t)s * ldS;
+            double nu = 0.0;
+            for (int r = t; r < l; ++r) nu += (double)col[r] * (double)col[r];
+            if (better(nu, pos[s], myv, myp)) { myv = nu; myp = pos[s]; mys = s; }
+        }
+        block_argmax(myv, myp, mys, red_v, red_p, red_i);
+        if (tid == 0) {
+            cval[buf * kMaxCand + g] = myv;
+            cpos[buf * kMaxCand + g] = myp;
+        }
+        if (mys >= 0)
+            for (int r = tid; r < l; r += NTH)
+                ccol[((size_t)buf * kMaxCand + g) * l + r] = cols[(size_t)mys * ldS + r];
+        // 2. barrier
+        if (!grid_barrier(st)) return;
+        // 3. global winner (identical in every block)
+        double wv = -1.0;
+        long long wp = LLONG_MAX;
+        int wg = -1;
+        for (int h = tid; h < G; h += NTH) {
+            const double v = ld_cg(&cval[buf * kMaxCand + h]);
+            const long long p = ld_cg(&cpos[buf * kMaxCand + h]);
+            if (better(v, p, wv, wp)) { wv = v; wp = p; wg = h; }
+        }
+        block_argmax(wv, wp, wg, red_v, red_p, red_i);
+        if (!(wv > guard)) {  // also catches "no candidate" (-1) and NaN
+            if (g == 0 && tid == 0) {
+                st->guard = 1;
+                st->rank = c;
+            }
+            steps = t;
+            break;
+        }
+        for (int r = tid; r < l; r += NTH) xs[r] = (double)ld_cg(&ccol[((size_t)buf * kMaxCand + wg) * l + r]);
+        __syncthreads();
+        if (tid == 0) {
+            double ss = 0.0;
+            for (int r = t + 1; r < l; ++r) ss += xs[r] * xs[r];
+            const double alpha = xs[t];
+            double tau = 0.0, beta = alpha, scal = 0.0;
+            if (ss != 0.0) {
+                const double nrm = sqrt(alpha * alpha + ss);
+                beta = (alpha >= 0.0) ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            sh_tau = tau;
+            sh_beta = beta;
+            sh_scal = scal;
+            if (g == 0) pivs[t] = wp;
+        }
+        __syncthreads();
+        for (int r = t + 1 + tid; r < l; r += NTH) vT[r] = (T)(xs[r] * sh_scal);
+        __syncthreads();
+        const T tauT = (T)sh_tau;
+        for (int s = tid; s < nloc; s += NTH) {
+            T* col = cols + (size_t)s * ldS;
+            if (pos[s] == wp) {  // the winner: becomes column c of R_hat
+                col[t] = (T)sh_beta;
+                for (int r = t + 1; r < l; ++r) col[r] = T(0);
+                active[s] = 0;
+                pos[s] = c;
+                continue;
+            }
+            if (pos[s] == c) pos[s] = wp;  // the column displaced by the swap
+            if (!active[s] || sh_tau == 0.0) continue;
+            T w = col[t];
+            for (int r = t + 1; r < l; ++r) w += vT[r] * col[r];
+            w *= tauT;
+            col[t] -= w;
+            for (int r = t + 1; r < l; ++r) col[r] -= w * vT[r];
+        }
+        __syncthreads();
+    }
+    // write the slices back in the new column order
+    for (int64_t e = tid; e < (int64_t)nloc * l; e += NTH) {
+        const int s = (int)(e / l), r = (int)(e % l);
+        B[pos[s] * ldb + r] = cols[(size_t)s * ldS + r];
+    }
+    if (g == 0) {
+        for (int t = steps + tid; t < bb; t += NTH) pivs[t] = i + t;
+        __syncthreads();
+        for (int t = tid; t < bb; t += NTH) piv[t] = (int32_t)pivs[t];
+        if (tid == 0) {
+            // jpvt: apply the transpositions in order.  swapmap: net map of the moved positions
+            // (count, then pairs (destination position, source position)).
+            long long cnt = 0;
+            long long* mp = swapmap + 1;
+            for (int t = 0; t < bb; ++t) {
+                const long long a = i + t, b2 = pivs[t];
+                if (a == b2) continue;
+                const int32_t tj = jpvt[a];
+                jpvt[a] = jpvt[b2];
+                jpvt[b2] = tj;
+                long long ia = -1, ib = -1;
+                for (long long e = 0; e < cnt; ++e) {
+                    if (mp[2 * e] == a) ia = e;
+                    if (mp[2 * e] == b2) ib = e;
+                }
+                if (ia < 0) { mp[2 * cnt] = a; mp[2 * cnt + 1] = a; ia = cnt++; }
+                if (ib < 0) { mp[2 * cnt] = b2; mp[2 * cnt + 1] = b2; ib = cnt++; }
+                const long long tmp = mp[2 * ia + 1];
+                mp[2 * ia + 1] = mp[2 * ib + 1];
+                mp[2 * ib + 1] = tmp;
+            }
+            swapmap[0] = cnt;
+        }
+    }
+}
+
+struct PivotCfg {
+    int grid, threads;
+    int64_t cpb;
+    size_t smem;
+};
+
+template <typename T>
+size_t pivot_smem(int64_t cpb, int l, int bb)
+{
+    const int ldS = l | 1;
+    size_t off = ((size_t)cpb * ldS * sizeof(T) + 15) & ~(size_t)15;
+    off += (size_t)cpb * sizeof(long long) + (size_t)l * sizeof(double);
+    off += ((size_t)l * sizeof(T) + 15) & ~(size_t)15;
+    off += (size_t)bb * sizeof(long long) + (size_t)cpb * sizeof(int);
+    return off;
+}
+
+}  // namespace
+
+size_t pivot_cand_bytes(int l)
+{
+    return 2 * (size_t)kMaxCand * (sizeof(double) + sizeof(long long)) + 2 * (size_t)kMaxCand * l * sizeof(double);
+}
+
+bool pivot_fits(int64_t ncols, int l, int elem_bytes)
+{
+    if (l > 1024) return false;
+    const int64_t G = dev_info().sms;
+    const int64_t cpb = (ncols + G - 1) / G;
+    if (cpb > 1024) return false;
+    const size_t need = elem_bytes == 8 ? pivot_smem<double>(cpb, l, 1024) : pivot_smem<float>(cpb, l, 1024);
+    return need <= (size_t)dev_info().max_smem_optin - 2048;
+}
+
+template <typename T>
+cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int32_t* jpvt,
+                         int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaError_t e = allow_max_dynamic_smem(pivot_kernel<T>)) return e;
+        attr_set = true;
+    }
+    const int64_t nprime = n - i;
+    int64_t G = (nprime + 63) / 64;
+    if (G > dev_info().sms) G = dev_info().sms;
+    if (G < 1) G = 1;
+    const int64_t cpb = (nprime + G - 1) / G;
+    int threads = (int)(((cpb + 31) / 32) * 32);
+    if (threads < 128) threads = 128;
+    if (threads > 1024) threads = 1024;
+    const size_t smem = pivot_smem<T>(cpb, l, bb);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pivot_kernel<T>, threads, smem);
+    if (e != cudaSuccess) return e;
+    if ((int64_t)per_sm * dev_info().sms < G) return cudaErrorCooperativeLaunchTooLarge;
+
+    char* cb = static_cast<char*>(cand);
+    double* cval = reinterpret_cast<double*>(cb);
+    long long* cpos = reinterpret_cast<long long*>(cb + 2 * (size_t)kMaxCand * sizeof(double));
+    T* ccol = reinterpret_cast<T*>(cb + 2 * (size_t)kMaxCand * (sizeof(double) + sizeof(long long)));
+    // the swap map lives right after the candidate columns
+    long long* swapmap = reinterpret_cast<long long*>(cb + pivot_cand_bytes(l));
+    int bbv = bb;
+    int lv = l;
+    int64_t ldbv = ldb, nv = n, iv = i, cpbv = cpb;
+    double gr = guard_rel2;
+    void* args[] = {&B, &ldbv, &lv, &nv, &iv, &bbv, &cpbv, &jpvt, &piv, &swapmap, &cval, &cpos, &ccol, &gr, &st};
+    return cudaLaunchCooperativeKernel((const void*)pivot_kernel<T>, dim3((unsigned)G), dim3(threads), args, smem, s);
+}
+
+template cudaError_t launch_pivot<double>(double*, int64_t, int, int64_t, int64_t, int, int32_t*, int32_t*,
+                                          void*, double, Status*, cudaStream_t);
+template cudaError_t launch_pivot<float>(float*, int64_t, int, int64_t, int64_t, int, int32_t*, int32_t*,
+                                         void*, double, Status*, cudaStream_t);
+
+}  // namespace rq

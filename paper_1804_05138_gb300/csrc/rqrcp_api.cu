@@ -1,0 +1,408 @@
+// rqrcp_api.cu -- C ABI of librqrcp: argument checks, workspace carving and the block loop of
+// Alg. 2 (randomized QRCP) enqueued on the caller's stream.
+//
+// Per block i (bb = min(b, k-i)), all on one stream with no host synchronisation:
+//   pivot   : partial QRCP on B(:, i:n)                     (cooperative kernel)
+//   swaps   : move the chosen columns of A into place       (gather + scatter)
+//   panel   : Householder QR of A(i:m, i:i+bb), FP64 reflector generation (cooperative kernel)
+//   gemm_tn : [V^T V | V^T A(i:m, i+bb:n)] as split-K partials
+//   tform   : T of the compact WY form I - V T V^T
+//   reduce_y: Y = T^T V^T A(i:m, i+bb:n)
+//   update  : A(i:m, i+bb:n) -= V Y                         (rows i..i+bb-1 become R12)
+//   bupdate : Eq. (4) on the top bb rows of the trailing sketch
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace rq {
+
+const DevInfo& dev_info()
+{
+    static DevInfo cache[64];
+    static bool have[64] = {};
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d < 0 || d >= 64) d = 0;
+    if (!have[d]) {
+        cudaDeviceGetAttribute(&cache[d].sms, cudaDevAttrMultiProcessorCount, d);
+        cudaDeviceGetAttribute(&cache[d].max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+        have[d] = true;
+    }
+    return cache[d];
+}
+
+cudaError_t launch_lowrank_rk(const double* Af, int64_t ldaf, int64_t k, int64_t n, double* Rk, cudaStream_t s);
+cudaError_t launch_eye(double* Q, int64_t ldq, int64_t m, int64_t k, cudaStream_t s);
+
+namespace {
+
+constexpr int kMaxSplit = 16;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+    size_t status, omega, B, P, Y, Tm, What, piv, cand, part, tmp, total;
+};
+
+Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
+{
+    const int64_t l = b + p;
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.status = take(sizeof(Status));
+    L.omega = take((size_t)l * m * esz);
+    L.B = take((size_t)l * n * esz);
+    L.P = take((size_t)kMaxSplit * n * (size_t)(l > b ? l : b) * sizeof(double));
+    L.Y = take((size_t)b * n * sizeof(double));
+    L.Tm = take((size_t)b * b * sizeof(double));
+    L.What = take((size_t)b * b * sizeof(double));
+    L.piv = take((size_t)b * sizeof(int32_t));
+    L.cand = take(pivot_cand_bytes((int)l) + sizeof(long long) * (1 + 4 * (size_t)b));
+    L.part = take(panel_part_bytes((int)b));
+    L.tmp = take((size_t)2 * b * m * esz);
+    L.total = off;
+    return L;
+}
+
+// Split-K factor for an M x N result contracted over K: about four blocks per SM.
+void choose_split(int64_t M, int64_t N, int64_t K, int& nsplit, int64_t& kchunk)
+{
+    const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    const int64_t target = 4 * (int64_t)dev_info().sms;
+    int64_t S = (target + tiles - 1) / tiles;
+    if (S < 1) S = 1;
+    if (S > kMaxSplit) S = kMaxSplit;
+    const int64_t maxS = (K + 63) / 64;
+    if (S > maxS) S = maxS < 1 ? 1 : maxS;
+    kchunk = (K + S - 1) / S;
+    kchunk = ((kchunk + 15) / 16) * 16;
+    nsplit = (int)((K + kchunk - 1) / kchunk);
+}
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+    static constexpr double unit_roundoff = 1.1102230246251565e-16;  // 2^-53
+};
+template <>
+struct Prec<float> {
+    static constexpr double unit_roundoff = 5.9604644775390625e-08;  // 2^-24
+};
+
+#define RQ_CHECK(expr)                          \
+    do {                                        \
+        if ((expr) != cudaSuccess) {            \
+            cudaGetLastError();                 \
+            return RQRCP_ERR_CUDA;              \
+        }                                       \
+    } while (0)
+
+// Launch with optional event bracketing and the algorithmic work of the launch.
+#define RQ_LAUNCH(cls, flops, bytes, expr)                      \
+    do {                                                        \
+        const bool prof_ = prof_on();                           \
+        if (prof_) prof_begin((cls), s);                        \
+        RQ_CHECK(expr);                                         \
+        if (prof_) prof_end((cls), (double)(flops), (double)(bytes), s); \
+    } while (0)
+
+int check_work(void* work, size_t work_bytes, size_t need)
+{
+    if (work == nullptr || (reinterpret_cast<uintptr_t>(work) & (kAlign - 1)) != 0 || work_bytes < need)
+        return RQRCP_ERR_WORKSPACE;
+    return RQRCP_OK;
+}
+
+template <typename T>
+int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, int64_t p, uint64_t seed,
+                const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
+                cudaStream_t s)
+{
+    const int64_t l = b + p;
+    const Layout L = make_layout(m, n, b, p, sizeof(T));
+    if (int e = check_work(work, work_bytes, L.total)) return e;
+    if (l > 1024 || b > 128 || !pivot_fits(n, (int)l, (int)sizeof(T)) || !panel_fits(m, (int)b, (int)sizeof(T)))
+        return RQRCP_ERR_UNSUPPORTED;
+    char* w = static_cast<char*>(work);
+    Status* st = reinterpret_cast<Status*>(w + L.status);
+    T* Om = reinterpret_cast<T*>(w + L.omega);
+    T* B = reinterpret_cast<T*>(w + L.B);
+    double* P = reinterpret_cast<double*>(w + L.P);
+    double* Y = reinterpret_cast<double*>(w + L.Y);
+    double* Tm = reinterpret_cast<double*>(w + L.Tm);
+    double* What = reinterpret_cast<double*>(w + L.What);
+    int32_t* piv = reinterpret_cast<int32_t*>(w + L.piv);
+    void* cand = w + L.cand;
+    const long long* swapmap = reinterpret_cast<const long long*>(w + L.cand + pivot_cand_bytes((int)l));
+    double* part = reinterpret_cast<double*>(w + L.part);
+    T* tmp = reinterpret_cast<T*>(w + L.tmp);
+
+    RQ_CHECK(launch_init(st, k, jpvt, n, s));
+    const double es = (double)sizeof(T);
+    const T* Omega = Omega_user;
+    if (Omega == nullptr) {
+        RQ_LAUNCH(K_OMEGA, 0, l * m * es, launch_omega<T>(l, m, seed, Om, m, s));
+        Omega = Om;
+        ldo = m;
+    }
+    // Alg. 2: B = Omega A
+    {
+        int ns;
+        int64_t kc;
+        choose_split(l, n, m, ns, kc);
+        RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
+                  launch_gemm_tn<T>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s));
+        RQ_LAUNCH(K_SKETCH_REDUCE, 0, (double)ns * l * n * 8 + (double)l * n * es,
+                  launch_sketch_reduce<T>(P, ns, l, n, B, l, st, s));
+    }
+    const double gtol = 10.0 * (double)(m > n ? m : n) * Prec<T>::unit_roundoff;
+    const double guard_rel2 = gtol * gtol;
+    for (int64_t i = 0; i < k; i += b) {
+        const int bb = (int)(b < k - i ? b : k - i);
+        const double np = (double)(n - i);
+        RQ_LAUNCH(K_PIVOT, 4.0 * l * np * bb, 2.0 * l * np * es,
+                  launch_pivot<T>(B, l, (int)l, n, i, bb, jpvt, piv, cand, guard_rel2, st, s));
+        RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * m * es, launch_swaps<T>(A, lda, m, bb, swapmap, tmp, st, s));
+        T* Vp = A + i * lda + i;
+        const int64_t mr = m - i;
+        RQ_LAUNCH(K_PANEL, 2.0 * mr * bb * bb - 2.0 * bb * bb * bb / 3.0, 2.0 * mr * bb * es,
+                  launch_panel<T>(Vp, lda, mr, bb, tau + i, part, st, s));
+        const int64_t nt = n - i - bb;
+        if (nt <= 0) continue;
+        int ns;
+        int64_t kc;
+        choose_split(bb, n - i, mr, ns, kc);
+        RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
+                  launch_gemm_tn<T>(Vp, lda, Vp, lda, bb, n - i, mr, kc, P, 1, bb, st, s));
+        RQ_LAUNCH(K_TFORM, (double)bb * bb * bb / 3.0, (double)ns * bb * bb * 8,
+                  launch_tform(P, ns, n - i, bb, tau + i, Tm, st, s));
+        RQ_LAUNCH(K_REDUCE_Y, (double)bb * bb * nt, ((double)ns + 1.0) * bb * nt * 8,
+                  launch_reduce_y(P, ns, n - i, bb, bb, Tm, 1, Y, nt, st, s));
+        RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
+                  launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st, s));
+        if (i + bb < k)
+            RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
+                      launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));
+    }
+    return RQRCP_OK;
+}
+
+int validate_factor(int64_t m, int64_t n, const void* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                    const void* jpvt, const void* tau)
+{
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (A == nullptr) return -3;
+    if (lda < m) return -4;
+    if (k < 1 || k > (m < n ? m : n)) return -5;
+    if (b < 1) return -6;
+    if (p < 0) return -7;
+    if (jpvt == nullptr) return -9;
+    if (tau == nullptr) return -10;
+    return 0;
+}
+
+}  // namespace
+}  // namespace rq
+
+using namespace rq;
+
+extern "C" {
+
+__attribute__((visibility("default"))) const char* rqrcp_error_string(int code)
+{
+    if (code < 0) return "invalid argument (the negated return value is its 1-based position)";
+    switch (code) {
+    case RQRCP_OK: return "success";
+    case RQRCP_ERR_CUDA: return "a CUDA runtime call failed";
+    case RQRCP_ERR_NONFINITE: return "the sketch of A is not finite (A holds NaN or Inf)";
+    case RQRCP_ERR_TIMEOUT: return "a grid-wide barrier timed out inside a kernel";
+    case RQRCP_ERR_WORKSPACE: return "workspace missing, misaligned (256 B) or too small";
+    case RQRCP_ERR_UNSUPPORTED: return "shape beyond what this build keeps in shared memory";
+    default: return "unknown error code";
+    }
+}
+
+__attribute__((visibility("default"))) size_t rqrcp_workspace_size(int64_t m, int64_t n, int64_t k, int64_t b,
+                                                                   int64_t p, int precision)
+{
+    if (m < 1 || n < 1 || k < 1 || b < 1 || p < 0) return 0;
+    if (precision != RQRCP_PREC_FP64 && precision != RQRCP_PREC_MIXED) return 0;
+    return make_layout(m, n, b, p, precision == RQRCP_PREC_FP64 ? sizeof(double) : sizeof(float)).total;
+}
+
+__attribute__((visibility("default"))) int rqrcp_generate_omega(int64_t l, int64_t m, uint64_t seed, double* Omega,
+                                                                int64_t ldo, void* stream)
+{
+    if (l < 1) return -1;
+    if (m < 1) return -2;
+    if (Omega == nullptr) return -4;
+    if (ldo < m) return -5;
+    return launch_omega<double>(l, m, seed, Omega, ldo, (cudaStream_t)stream) == cudaSuccess ? RQRCP_OK
+                                                                                             : RQRCP_ERR_CUDA;
+}
+
+__attribute__((visibility("default"))) int rqrcp_generate_omega_f32(int64_t l, int64_t m, uint64_t seed, float* Omega,
+                                                                    int64_t ldo, void* stream)
+{
+    if (l < 1) return -1;
+    if (m < 1) return -2;
+    if (Omega == nullptr) return -4;
+    if (ldo < m) return -5;
+    return launch_omega<float>(l, m, seed, Omega, ldo, (cudaStream_t)stream) == cudaSuccess ? RQRCP_OK
+                                                                                            : RQRCP_ERR_CUDA;
+}
+
+__attribute__((visibility("default"))) int rqrcp_sketch(int64_t m, int64_t n, const double* A, int64_t lda,
+                                                        const double* Omega, int64_t l, int64_t ldo, double* B,
+                                                        int64_t ldb, void* work, size_t work_bytes, void* stream)
+{
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (A == nullptr) return -3;
+    if (lda < m) return -4;
+    if (Omega == nullptr) return -5;
+    if (l < 1) return -6;
+    if (ldo < m) return -7;
+    if (B == nullptr) return -8;
+    if (ldb < l) return -9;
+    const Layout L = make_layout(m, n, l, 0, sizeof(double));
+    if (int e = check_work(work, work_bytes, L.total)) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(work);
+    Status* st = reinterpret_cast<Status*>(w + L.status);
+    double* P = reinterpret_cast<double*>(w + L.P);
+    RQ_CHECK(launch_init(st, 0, nullptr, 0, s));
+    int ns;
+    int64_t kc;
+    choose_split(l, n, m, ns, kc);
+    RQ_CHECK(launch_gemm_tn<double>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s));
+    RQ_CHECK(launch_sketch_reduce<double>(P, ns, l, n, B, ldb, st, s));
+    return RQRCP_OK;
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
+                                                        int64_t b, int64_t p, uint64_t seed, int32_t* jpvt,
+                                                        double* tau, void* work, size_t work_bytes, void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e;
+    return factor_impl<double>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
+                               (cudaStream_t)stream);
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda,
+                                                                   int64_t k, int64_t b, int64_t p,
+                                                                   const double* Omega, int64_t ldo, int32_t* jpvt,
+                                                                   double* tau, void* work, size_t work_bytes,
+                                                                   void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 1 : e;
+    if (Omega == nullptr) return -8;
+    if (ldo < m) return -9;
+    return factor_impl<double>(m, n, A, lda, k, b, p, 0, Omega, ldo, jpvt, tau, work, work_bytes,
+                               (cudaStream_t)stream);
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k,
+                                                              int64_t b, int64_t p, uint64_t seed, int32_t* jpvt,
+                                                              double* tau, void* work, size_t work_bytes,
+                                                              void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e;
+    return factor_impl<float>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
+                              (cudaStream_t)stream);
+}
+
+__attribute__((visibility("default"))) int rqrcp_read_status(const void* work, int64_t* rank, void* stream)
+{
+    if (work == nullptr) return -1;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return RQRCP_ERR_CUDA;
+    }
+    Status h;
+    if (cudaMemcpy(&h, work, sizeof(Status), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return RQRCP_ERR_CUDA;
+    }
+    if (rank) *rank = h.rank;
+    return h.error;
+}
+
+__attribute__((visibility("default"))) size_t rqrcp_lowrank_workspace_size(int64_t m, int64_t n, int64_t k)
+{
+    if (m < 1 || n < 1 || k < 1) return 0;
+    const int64_t bb = 64;
+    size_t off = 0;
+    off = align_up(off + sizeof(Status));
+    off = align_up(off + (size_t)kMaxSplit * (size_t)(k > bb ? k : bb) * bb * sizeof(double));  // P
+    off = align_up(off + (size_t)bb * bb * sizeof(double));                                        // Tm
+    off = align_up(off + (size_t)k * (size_t)(n > bb ? n : bb) * sizeof(double));                 // Y / Rk
+    return off;
+}
+
+__attribute__((visibility("default"))) int rqrcp_lowrank(int64_t m, int64_t n, int64_t k, const double* Afact,
+                                                         int64_t ldaf, const double* tau, const int32_t* jpvt,
+                                                         double* L, int64_t ldl, double* Q1, int64_t ldq,
+                                                         void* work, size_t work_bytes, void* stream)
+{
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (k < 1 || k > (m < n ? m : n)) return -3;
+    if (Afact == nullptr) return -4;
+    if (ldaf < m) return -5;
+    if (tau == nullptr) return -6;
+    if (jpvt == nullptr) return -7;
+    if (L == nullptr) return -8;
+    if (ldl < m) return -9;
+    if (Q1 == nullptr) return -10;
+    if (ldq < m) return -11;
+    const size_t need = rqrcp_lowrank_workspace_size(m, n, k);
+    if (int e = check_work(work, work_bytes, need)) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t bb = 64;
+    char* w = static_cast<char*>(work);
+    size_t off = 0;
+    Status* st = reinterpret_cast<Status*>(w);
+    off = align_up(off + sizeof(Status));
+    double* P = reinterpret_cast<double*>(w + off);
+    off = align_up(off + (size_t)kMaxSplit * (size_t)(k > bb ? k : bb) * bb * sizeof(double));
+    double* Tm = reinterpret_cast<double*>(w + off);
+    off = align_up(off + (size_t)bb * bb * sizeof(double));
+    double* Y = reinterpret_cast<double*>(w + off);
+    RQ_CHECK(launch_init(st, k, nullptr, 0, s));
+    // Q1 = H_0 ... H_{k-1} I(:, 0:k), accumulated backwards block by block:
+    // Q1(i:m, :) <- (I - V T V^T) Q1(i:m, :).
+    RQ_CHECK(launch_eye(Q1, ldq, m, k, s));
+    const int64_t last = ((k - 1) / bb) * bb;
+    for (int64_t i = last; i >= 0; i -= bb) {
+        const int kb = (int)(bb < k - i ? bb : k - i);
+        const double* Vp = Afact + i * ldaf + i;
+        const int64_t mr = m - i;
+        int ns;
+        int64_t kc;
+        choose_split(kb, kb, mr, ns, kc);
+        RQ_CHECK(launch_gemm_tn<double>(Vp, ldaf, Vp, ldaf, kb, kb, mr, kc, P, 1, kb, st, s));
+        RQ_CHECK(launch_tform(P, ns, kb, kb, tau + i, Tm, st, s));
+        const int64_t nq = k - i;  // columns of Q1 touched by this block: i..k-1
+        choose_split(kb, nq, mr, ns, kc);
+        RQ_CHECK(launch_gemm_tn<double>(Vp, ldaf, Q1 + i * ldq + i, ldq, kb, nq, mr, kc, P, 1, 0, st, s));
+        RQ_CHECK(launch_reduce_y(P, ns, nq, 0, kb, Tm, 0, Y, nq, st, s));
+        RQ_CHECK(launch_gemm_update<double>(Q1 + i * ldq + i, ldq, Vp, ldaf, Y, kb, mr, nq, kb, 1, nullptr, st, s));
+    }
+    // L(:, jpvt[c]) = Q1 [R11 R12](:, c)  as  L -= Q1 (-Rk) with a column scatter.
+    RQ_CHECK(launch_lowrank_rk(Afact, ldaf, k, n, Y, s));
+    RQ_CHECK(cudaMemset2DAsync(L, ldl * sizeof(double), 0, m * sizeof(double), n, s));
+    RQ_CHECK(launch_gemm_update<double>(L, ldl, Q1, ldq, Y, k, m, n, k, 0, jpvt, st, s));
+    return RQRCP_OK;
+}
+
+}  // extern "C"

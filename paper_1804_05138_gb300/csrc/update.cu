@@ -1,0 +1,148 @@
+// update.cu -- small kernels around the hot loop of Alg. 2:
+//  * status / jpvt initialisation;
+//  * "Swap (j_1..j_b) and (i:i+b-1) columns in A": gather the moved columns into scratch,
+//    then scatter them to their new positions (whole columns, all m rows, coalesced);
+//  * Eq. (4): B(0:bb, i+bb:n) <- R_hat12 - Omega_hat_11 R12 with Omega_hat_11 = R_hat11 R11^{-1}
+//    from the forward substitution Omega_hat_11 R11 = R_hat11 (both upper triangular).
+#include "internal.cuh"
+
+namespace rq {
+namespace {
+
+__global__ void init_kernel(Status* st, int64_t k, int32_t* jpvt, int64_t n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        st->error = 0;
+        st->guard = 0;
+        st->rank = k;
+        st->bar_count = 0;
+        st->bar_gen = 0;
+        st->nu0bits = 0;
+    }
+    for (int64_t j = t; j < n; j += (int64_t)gridDim.x * blockDim.x) jpvt[j] = (int32_t)j;
+}
+
+template <typename T>
+__global__ void swap_gather_kernel(const T* __restrict__ A, int64_t lda, int64_t m,
+                                   const long long* __restrict__ swapmap, T* __restrict__ tmp, const Status* st)
+{
+    if (status_error(st)) return;
+    const long long cnt = swapmap[0];
+    const long long e = blockIdx.y;
+    if (e >= cnt) return;
+    const long long src = swapmap[1 + 2 * e + 1];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+        tmp[e * m + r] = A[src * lda + r];
+}
+
+template <typename T>
+__global__ void swap_scatter_kernel(T* __restrict__ A, int64_t lda, int64_t m,
+                                    const long long* __restrict__ swapmap, const T* __restrict__ tmp,
+                                    const Status* st)
+{
+    if (status_error(st)) return;
+    const long long cnt = swapmap[0];
+    const long long e = blockIdx.y;
+    if (e >= cnt) return;
+    const long long dst = swapmap[1 + 2 * e];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+        A[dst * lda + r] = tmp[e * m + r];
+}
+
+// One block: row r of Omega_hat_11 by thread r (forward substitution over columns j).
+template <typename T>
+__global__ void bsolve_kernel(const T* __restrict__ B, int64_t ldb, const T* __restrict__ A, int64_t lda,
+                              int64_t i, int bb, double* __restrict__ What, const Status* st)
+{
+    if (status_error(st) || *(volatile const int*)&st->guard) return;
+    extern __shared__ double R11[];  // bb x bb column-major
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
+        const int q = e % bb, j = e / bb;
+        R11[e] = (double)A[(i + j) * lda + i + q];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < bb; r += blockDim.x) {
+        for (int q = 0; q < r; ++q) What[q * bb + r] = 0.0;
+        for (int j = r; j < bb; ++j) {
+            double s = (double)B[(i + j) * ldb + r];
+            for (int q = r; q < j; ++q) s -= What[q * bb + r] * R11[j * bb + q];
+            const double rjj = R11[j * bb + j];
+            What[j * bb + r] = (rjj == 0.0) ? 0.0 : s / rjj;
+        }
+    }
+}
+
+// B(r, c) -= sum_{q >= r} What(r, q) * A(i+q, c) for the trailing columns c.
+template <typename T>
+__global__ void bapply_kernel(T* __restrict__ B, int64_t ldb, const T* __restrict__ A, int64_t lda,
+                              int64_t i, int bb, int64_t n, const double* __restrict__ What, const Status* st)
+{
+    if (status_error(st) || *(volatile const int*)&st->guard) return;
+    extern __shared__ double Ws[];  // bb x bb column-major
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Ws[e] = What[e];
+    __syncthreads();
+    const int64_t c0 = i + bb + (int64_t)blockIdx.x * 64;
+    const int64_t c1 = min(n, c0 + 64);
+    const int64_t total = (c1 - c0) * bb;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = (int)(e % bb);
+        const int64_t c = c0 + e / bb;
+        const T* a = A + c * lda + i;
+        double acc = (double)B[c * ldb + r];
+        for (int q = r; q < bb; ++q) acc -= Ws[q * bb + r] * (double)a[q];
+        B[c * ldb + r] = (T)acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s)
+{
+    int64_t grid = (n + 255) / 256;
+    if (grid < 1) grid = 1;
+    if (grid > 1024) grid = 1024;
+    init_kernel<<<(unsigned)grid, 256, 0, s>>>(st, k, jpvt, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_swaps(T* A, int64_t lda, int64_t m, int bb, const long long* swapmap, T* tmp,
+                         const Status* st, cudaStream_t s)
+{
+    int64_t gx = (m + 255) / 256;
+    if (gx > 16) gx = 16;
+    dim3 grid((unsigned)gx, (unsigned)(2 * bb));
+    swap_gather_kernel<T><<<grid, 256, 0, s>>>(A, lda, m, swapmap, tmp, st);
+    swap_scatter_kernel<T><<<grid, 256, 0, s>>>(A, lda, m, swapmap, tmp, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i, int bb, int64_t n,
+                           double* What, const Status* st, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaError_t e = allow_max_dynamic_smem(bsolve_kernel<T>)) return e;
+        if (cudaError_t e = allow_max_dynamic_smem(bapply_kernel<T>)) return e;
+        attr_set = true;
+    }
+    const size_t smem = sizeof(double) * (size_t)bb * bb;
+    const int threads = ((bb + 31) / 32) * 32;
+    bsolve_kernel<T><<<1, threads, smem, s>>>(B, ldb, A, lda, i, bb, What, st);
+    const int64_t nt = n - i - bb;
+    if (nt > 0) bapply_kernel<T><<<(unsigned)((nt + 63) / 64), 256, smem, s>>>(B, ldb, A, lda, i, bb, n, What, st);
+    return cudaGetLastError();
+}
+
+#define RQ_INST(T)                                                                                    \
+    template cudaError_t launch_swaps<T>(T*, int64_t, int64_t, int, const long long*, T*, const Status*, \
+                                         cudaStream_t);                                               \
+    template cudaError_t launch_bupdate<T>(T*, int64_t, const T*, int64_t, int64_t, int, int64_t,     \
+                                           double*, const Status*, cudaStream_t);
+RQ_INST(double)
+RQ_INST(float)
+#undef RQ_INST
+
+}  // namespace rq

@@ -1,0 +1,84 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every symbol that
+include/rqrcp.h declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_05138_gb300 import binding, build
+    build.build()
+    return binding.load()
+
+
+def _declared_symbols():
+    with open(os.path.join(ROOT, "include", "rqrcp.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(rqrcp_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1804_05138_gb300 import binding
+    declared = _declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(binding.ABI_SYMBOLS) == set(declared)
+
+
+def test_error_strings(lib):
+    from paper_1804_05138_gb300 import binding
+    for code in range(0, 6):
+        assert binding.error_string(code)
+    assert "invalid argument" in binding.error_string(-3)
+
+
+def test_workspace_size_rejects_bad_arguments(lib):
+    from paper_1804_05138_gb300 import binding as b
+    assert b.rqrcp_workspace_size(0, 10, 1, 4, 2) == 0
+    assert b.rqrcp_workspace_size(10, 10, 1, 0, 2) == 0
+    assert b.rqrcp_workspace_size(10, 10, 1, 4, -1) == 0
+    assert b.rqrcp_workspace_size(10, 10, 1, 4, 2, 7) == 0
+    assert b.rqrcp_workspace_size(1000, 1000, 64, 32, 8) > 0
+    assert b.rqrcp_workspace_size(1000, 1000, 64, 32, 8, b.RQRCP_PREC_MIXED) > 0
+    assert b.rqrcp_lowrank_workspace_size(100, 80, 10) > 0
+
+
+def test_factor_argument_codes(lib):
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation happens first
+    f = lib.rqrcp_factor
+    #            m    n    A     lda  k   b   p  seed jpvt  tau   work  bytes stream
+    assert f(0, 5, fake, 1, 1, 1, 0, 0, fake, fake, None, 0, None) == -1
+    assert f(5, 0, fake, 5, 1, 1, 0, 0, fake, fake, None, 0, None) == -2
+    assert f(5, 5, None, 5, 1, 1, 0, 0, fake, fake, None, 0, None) == -3
+    assert f(5, 5, fake, 4, 1, 1, 0, 0, fake, fake, None, 0, None) == -4
+    assert f(5, 5, fake, 5, 6, 1, 0, 0, fake, fake, None, 0, None) == -5
+    assert f(5, 5, fake, 5, 0, 1, 0, 0, fake, fake, None, 0, None) == -5
+    assert f(5, 5, fake, 5, 2, 0, 0, 0, fake, fake, None, 0, None) == -6
+    assert f(5, 5, fake, 5, 2, 1, -1, 0, fake, fake, None, 0, None) == -7
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, None, fake, None, 0, None) == -9
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, None, None, 0, None) == -10
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, None, 0, None) == 4      # no workspace
+    g = lib.rqrcp_factor_with_omega
+    assert g(5, 5, fake, 5, 2, 1, 0, None, 5, fake, fake, None, 0, None) == -8
+    assert g(5, 5, fake, 5, 2, 1, 0, fake, 4, fake, fake, None, 0, None) == -9
+    assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, None, fake, None, 0, None) == -10
+    assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, fake, None, None, 0, None) == -11
+    h = lib.rqrcp_factor_mixed
+    assert h(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, fake, 16, None) == 4     # too small
+
+
+def test_other_entry_point_argument_codes(lib):
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.rqrcp_generate_omega(0, 5, 0, fake, 5, None) == -1
+    assert lib.rqrcp_generate_omega(2, 5, 0, fake, 4, None) == -5
+    assert lib.rqrcp_sketch(5, 5, fake, 5, fake, 3, 4, fake, 3, None, 0, None) == -7
+    assert lib.rqrcp_sketch(5, 5, fake, 5, fake, 3, 5, fake, 2, None, 0, None) == -9
+    assert lib.rqrcp_lowrank(5, 5, 6, fake, 5, fake, fake, fake, 5, fake, 5, None, 0, None) == -3
+    assert lib.rqrcp_lowrank(5, 5, 2, fake, 5, fake, fake, fake, 5, None, 5, None, 0, None) == -10
+    assert lib.rqrcp_read_status(None, None, None) == -1
