@@ -126,6 +126,27 @@ int rqrcp_lowrank(int64_t m, int64_t n, int64_t k, const double* Afact, int64_t 
                   size_t work_bytes, void* stream);
 
 /*
+ * Sketch B = Omega A for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment convenience around the same sketch as rqrcp_sketch.
+ * Who needs it: code that is handed only the input and output pointers (a plugin or
+ * callback behind a narrow C interface with no allocator and no workspace to pass), and
+ * code that must not call cudaMalloc/cudaFree because of the device-wide synchronisation
+ * those calls imply.  Arguments and layouts are those of rqrcp_sketch, minus the workspace.
+ * Scratch: a fixed array of 8 MiB of device memory that every GPU which loads the library
+ * holds until the process exits; a problem needs n * l * 8 bytes of it for one split
+ * (n * l <= 1,048,544), larger ones are rejected with RQRCP_ERR_UNSUPPORTED before anything
+ * is enqueued.  The first call on each device looks the array's address up (with that
+ * device current); make that first call before any stream capture.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  Every call on a device shares that
+ * device's one array, which keeps the last call's contents; the status block is cleared at
+ * the start of each call.  Calls on the same device that overlap on the GPU (different
+ * streams or different host threads) race on the array, so serialise them.  Device-side
+ * status (non-finite sketch) is not reported: a non-finite A shows as NaN/Inf in B.
+ */
+int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, const double* Omega, int64_t l,
+                         int64_t ldo, double* B, int64_t ldb, void* stream);
+
+/*
  * Kernel-level timing for measurement (not part of the method).  Between
  * rqrcp_profile_begin and rqrcp_profile_end, every kernel the library enqueues is
  * bracketed by a pair of CUDA events on its stream, and the algorithmic work of the

@@ -31,6 +31,7 @@ ABI_SYMBOLS = (
     "rqrcp_sketch", "rqrcp_factor", "rqrcp_factor_with_omega", "rqrcp_factor_mixed",
     "rqrcp_read_status", "rqrcp_lowrank_workspace_size", "rqrcp_lowrank",
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
+    "rqrcp_sketch_noalloc",
 )
 RQRCP_PROFILE_CLASSES = 12
 
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_double)]),
             "rqrcp_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+            "rqrcp_sketch_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -148,6 +150,14 @@ def rqrcp_sketch(A, Omega, B, work, stream=None) -> int:
     l = Omega.shape[0]
     return load().rqrcp_sketch(m, n, _ptr(A), _ld(A), _ptr(Omega), l, _ld_rowmajor(Omega), _ptr(B), _ld(B),
                                _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_sketch_noalloc(A, Omega, B, stream=None) -> int:
+    """B = Omega A with the library's fixed device scratch (no workspace argument)."""
+    m, n = A.shape
+    l = Omega.shape[0]
+    return load().rqrcp_sketch_noalloc(m, n, _ptr(A), _ld(A), _ptr(Omega), l, _ld_rowmajor(Omega), _ptr(B),
+                                       _ld(B), _stream(stream))
 
 
 def rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
