@@ -38,6 +38,8 @@ WORKLOADS = {
                           desc="plain FP64 full RQRCP 8192x8192, i.i.d. N(0,1), b=64, p=8"),
     "fp64_8192_rank500": dict(m=8192, n=8192, k=8192, b=64, p=8, kind="rank500", prec="fp64",
                               desc="plain FP64 full RQRCP 8192x8192, exactly rank 500 (G1 G2), b=64, p=8"),
+    "fp64_4096_iid": dict(m=4096, n=4096, k=4096, b=64, p=8, kind="iid", prec="fp64",
+                          desc="plain FP64 full RQRCP 4096x4096, i.i.d. N(0,1), b=64, p=8 (profiling size)"),
     "fp64_1000_k64": dict(m=1000, n=1000, k=64, b=32, p=8, kind="logspec", prec="fp64",
                           desc="plain FP64 partial RQRCP k=64 on 1000x1000 U diag(10^(-6i/1000)) V^T, b=32, p=8"),
     "mixed_32768x16384_k512": dict(m=32768, n=16384, k=512, b=64, p=16, kind="expspec200", prec="mixed",
@@ -48,6 +50,11 @@ WORKLOADS = {
 # FP64 peak of a GB300 from the recipe's nominal table (DFMA pipe; no measured FP64 entry
 # exists in MEASURED_PEAKS.json).
 FP64_NOMINAL_TFLOPS = 1.25
+
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) divided
+# by the launch's algorithmic bytes, on the 4096^2 FP64 capture summarised in
+# profiles/gemm_fp64_4096_wy_kernels.md; scaled to a full launch by the algorithmic bytes.
+MEASURED_TRAFFIC_RATIO = {"fp64": {"wy_gemm_tn": 1.028, "wy_update": 0.604}}
 
 
 def counted_flops(m, n, k, l):
@@ -269,9 +276,15 @@ def run_ours(args, w, rank, world, local_rank):
                 "unit": "TFLOP/s", "frac": round(achieved_tflops / fp32_peak, 4), "traffic": None,
                 "kernel": dname, "peak_source": "FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     else:
+        ratio = MEASURED_TRAFFIC_RATIO["fp64"].get(dname)
+        traffic = None
+        if ratio is not None and d["launches"]:
+            traffic = round(ratio * d["bytes"] / d["launches"])
         roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
-                "kernel": dname, "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; DFMA pipe)"}
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": traffic,
+                "kernel": dname, "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; DFMA pipe)",
+                "algorithmic_bytes_per_launch": round(d["bytes"] / max(1, d["launches"])),
+                "traffic_source": "ncu 4096^2 capture scaled by algorithmic bytes (profiles/gemm_fp64_4096_wy_kernels.md)"}
     kernel_share = {kname: round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)
                     for kname, v in prof.items() if v["launches"]}
 
