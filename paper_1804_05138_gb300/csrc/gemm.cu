@@ -217,35 +217,41 @@ __global__ void sketch_reduce_kernel(const double* __restrict__ P, int nsplit, i
     }
 }
 
-// Single block: Gram = V^T V from the partials of the first bb columns (kept in the output
-// buffer Tm as scratch), then T column by column in shared memory, then T overwrites Tm.
+// One block per row r of T.  The rows of the forward columnwise recurrence are independent:
+// T(r,r) = tau_r and T(r,j) = -tau_j sum_{q=r}^{j-1} T(r,q) G(q,j), G = V^T V.  The block sums
+// G(r:bb, r:bb) from the split-K partials into shared memory; warp 0 runs the recurrence.
 __global__ void tform_kernel(const double* __restrict__ P, int nsplit, int64_t ncols, int bb,
                              const double* __restrict__ tau, double* __restrict__ Tm, const Status* st)
 {
     if (status_error(st)) return;
-    extern __shared__ double Ts[];  // bb x bb, column-major
-    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
-        const int q = e % bb, j = e / bb;
+    extern __shared__ double sm[];
+    const int r = blockIdx.x;
+    const int w = bb - r;
+    double* Gs = sm;          // Gs[jj * w + qq] = G(r + qq, r + jj), qq < jj
+    double* Tr = sm + w * w;  // T(r, r..bb-1)
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int qq = e % w, jj = e / w;
         double s = 0.0;
-        for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * ncols + j) * bb + q];
-        Tm[e] = s;
-        Ts[e] = 0.0;
+        if (qq < jj)
+            for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * ncols + r + jj) * bb + r + qq];
+        Gs[e] = s;
     }
     __syncthreads();
-    for (int j = 0; j < bb; ++j) {
-        const double tj = tau[j];
-        for (int r = threadIdx.x; r <= j; r += blockDim.x) {
-            if (r < j) {
-                double s = 0.0;
-                for (int q = r; q < j; ++q) s += Ts[q * bb + r] * Tm[j * bb + q];
-                Ts[j * bb + r] = -tj * s;
-            } else {
-                Ts[j * bb + j] = tj;
-            }
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) Tr[0] = tau[r];
+        __syncwarp();
+        for (int jj = 1; jj < w; ++jj) {
+            double s = 0.0;
+            for (int qq = lane; qq < jj; qq += 32) s += Tr[qq] * Gs[jj * w + qq];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) Tr[jj] = -tau[r + jj] * s;
+            __syncwarp();
         }
-        __syncthreads();
     }
-    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Tm[e] = Ts[e];
+    __syncthreads();
+    for (int j = threadIdx.x; j < bb; j += blockDim.x) Tm[(int64_t)j * bb + r] = (j < r) ? 0.0 : Tr[j - r];
 }
 
 // One warp per column c: W = sum of partials (column c0 + c), Y(:,c) = T^T W (transT) or T W.
@@ -320,13 +326,13 @@ cudaError_t launch_sketch_reduce(const double* P, int nsplit, int64_t l, int64_t
 cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, const double* tau,
                          double* Tm, const Status* st, cudaStream_t s)
 {
-    const size_t smem = sizeof(double) * (size_t)bb * bb;
+    const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)bb);
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(tform_kernel)) return e;
         attr_set = true;
     }
-    tform_kernel<<<1, 128, smem, s>>>(P, nsplit, ncols, bb, tau, Tm, st);
+    tform_kernel<<<bb, 128, smem, s>>>(P, nsplit, ncols, bb, tau, Tm, st);
     return cudaGetLastError();
 }
 

@@ -38,16 +38,23 @@ __device__ __forceinline__ void set_error(Status* st, int code)
     atomicCAS(&st->error, 0, code);
 }
 
-// Grid-wide barrier for cooperatively launched kernels.  Every wait is bounded: after
-// kWaitLimitNs the block records RQRCP_ERR_TIMEOUT and the barrier returns false, as it
-// does when any block has recorded an error; callers then leave the kernel.
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for cooperatively launched kernels: one arrival counter and a generation
+// word polled with acquire loads.  Every wait is bounded: after kWaitLimitNs the block records
+// RQRCP_ERR_TIMEOUT and the barrier returns false, as it does when any block has recorded an
+// error; callers then leave the kernel.
 __device__ __forceinline__ bool grid_barrier(Status* st)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &st->bar_gen;
-        const unsigned int gen = *vgen;
+        const unsigned int gen = ld_acquire_gpu(&st->bar_gen);
         __threadfence();
         const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
         int ok = 1;
@@ -57,13 +64,12 @@ __device__ __forceinline__ bool grid_barrier(Status* st)
             atomicAdd(&st->bar_gen, 1u);
         } else {
             const unsigned long long t0 = globaltimer_ns();
-            while (*vgen == gen) {
+            while (ld_acquire_gpu(&st->bar_gen) == gen) {
                 if (globaltimer_ns() - t0 > kWaitLimitNs) {
                     set_error(st, RQRCP_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();

@@ -37,15 +37,14 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
     const int nchunk = NTH / bbp;        // >= 1 because bb <= 256 and NTH == 256
     double* red = S + (size_t)ldS * bb;  // nchunk x bbp
     double* wk = red + (size_t)nchunk * bbp;
+    double* sums = wk + bbp;
     double* diag = part + 2 * (size_t)G * bb;  // 2 x bb, after the partials
     __shared__ double sh_tau, sh_beta, sh_scal;
 
     const int64_t r0 = (int64_t)g * rpb;
     const int nrow = (int)max((int64_t)0, min(rpb, m1 - r0));
-    for (int64_t e = tid; e < (int64_t)nrow * bb; e += NTH) {
-        const int r = (int)(e % nrow), k = (int)(e / nrow);
-        S[(size_t)k * ldS + r] = (double)A[(int64_t)k * lda + r0 + r];
-    }
+    for (int k = 0; k < bb; ++k)
+        for (int r = tid; r < nrow; r += NTH) S[(size_t)k * ldS + r] = (double)A[(int64_t)k * lda + r0 + r];
     __syncthreads();
     const int kidx = tid % bbp, chunk = tid / bbp;
 
@@ -73,16 +72,26 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
         }
         // B. barrier
         if (!grid_barrier(st)) return;
-        // C. reduce in block order, reflector, update
+        // C. reduce the blocks' partials (every thread takes blocks h = chunk (mod nchunk) of one
+        //    column, then the nchunk group sums are added in group order: identical in every block)
+        {
+            double s = 0.0;
+            if (kidx < nk) {
+#pragma unroll 8
+                for (int h = chunk; h < G; h += nchunk) s += ld_cg(&part[((size_t)buf * G + h) * bb + kidx]);
+            }
+            red[chunk * bbp + kidx] = s;
+        }
+        __syncthreads();
         if (tid < nk) {
             double s = 0.0;
-            for (int h = 0; h < G; ++h) s += ld_cg(&part[((size_t)buf * G + h) * bb + tid]);
-            red[tid] = s;
+            for (int c = 0; c < nchunk; ++c) s += red[c * bbp + tid];
+            sums[tid] = s;
         }
         __syncthreads();
         if (tid == 0) {
             const double alpha = ld_cg(&diag[(size_t)buf * bb]);
-            const double ss = red[0];
+            const double ss = sums[0];
             double tj = 0.0, beta = alpha, scal = 0.0;
             if (ss != 0.0) {
                 const double nrm = sqrt(alpha * alpha + ss);
@@ -96,17 +105,15 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
             if (g == 0) tau[j] = tj;
         }
         __syncthreads();
-        if (tid > 0 && tid < nk) wk[tid] = sh_tau * (ld_cg(&diag[(size_t)buf * bb + tid]) + sh_scal * red[tid]);
+        if (tid > 0 && tid < nk) wk[tid] = sh_tau * (ld_cg(&diag[(size_t)buf * bb + tid]) + sh_scal * sums[tid]);
         double* xj = S + (size_t)j * ldS;
         if (sh_tau != 0.0)
             for (int r = rstart + tid; r < nrow; r += NTH) xj[r] *= sh_scal;
         __syncthreads();
         if (sh_tau != 0.0) {
-            const int ncol = nk - 1;
-            const int rows = nrow - rstart;
-            for (int64_t e = tid; e < (int64_t)rows * ncol; e += NTH) {
-                const int r = rstart + (int)(e % rows), kk = 1 + (int)(e / rows);
-                S[(size_t)(j + kk) * ldS + r] -= wk[kk] * xj[r];
+            for (int r = rstart + tid; r < nrow; r += NTH) {
+                const double v = xj[r];
+                for (int kk = 1; kk < nk; ++kk) S[(size_t)(j + kk) * ldS + r] -= wk[kk] * v;
             }
             if (r0 <= j && j < r0 + nrow) {
                 const int rj = (int)(j - r0);
@@ -116,17 +123,139 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
         if (r0 <= j && j < r0 + nrow && tid == 0) S[(size_t)j * ldS + (j - r0)] = sh_beta;
         __syncthreads();
     }
-    for (int64_t e = tid; e < (int64_t)nrow * bb; e += NTH) {
-        const int r = (int)(e % nrow), k = (int)(e / nrow);
-        A[(int64_t)k * lda + r0 + r] = (T)S[(size_t)k * ldS + r];
+    for (int k = 0; k < bb; ++k)
+        for (int r = tid; r < nrow; r += NTH) A[(int64_t)k * lda + r0 + r] = (T)S[(size_t)k * ldS + r];
+}
+
+// FP32 panel of the mixed form.  Storage and the reflector application stay in FP32; the
+// dot products use the compensated Dot2 scheme (Ogita, Rump, Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005: TwoProduct by FMA, TwoSum, compensation carried
+// separately), each thread's (sum, compensation) pair is widened to FP64 for the cross-thread
+// and cross-block sums, and every reflector (norm, beta, tau, 1/(alpha-beta)) is formed in
+// FP64.  Same block layout and barrier pattern as the FP64 panel.
+__device__ __forceinline__ void dot2_acc(float x, float y, float& s, float& c)
+{
+    const float p = x * y;
+    const float e = fmaf(x, y, -p);      // exact product error
+    const float t = s + p;
+    const float z = t - s;
+    const float q = (s - (t - z)) + (p - z);  // exact sum error
+    s = t;
+    c += q + e;
+}
+
+__global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, int64_t lda, int64_t m1, int bb,
+                                                        int64_t rpb, double* __restrict__ tau,
+                                                        double* __restrict__ part, Status* st)
+{
+    if (status_error(st)) return;
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, NTH = blockDim.x;
+    extern __shared__ __align__(16) double smd[];
+    const int bbp = pow2_at_least(bb);
+    const int nchunk = NTH / bbp;
+    double* red = smd;                    // nchunk x bbp
+    double* sums = red + (size_t)nchunk * bbp;
+    float* wk = reinterpret_cast<float*>(sums + bbp);  // bbp floats
+    float* S = wk + bbp;                  // ldS x bb
+    const int ldS = (int)(rpb | 1);
+    double* diag = part + 2 * (size_t)G * bb;
+    __shared__ double sh_tau, sh_beta, sh_scal;
+
+    const int64_t r0 = (int64_t)g * rpb;
+    const int nrow = (int)max((int64_t)0, min(rpb, m1 - r0));
+    for (int k = 0; k < bb; ++k)
+        for (int r = tid; r < nrow; r += NTH) S[(size_t)k * ldS + r] = A[(int64_t)k * lda + r0 + r];
+    __syncthreads();
+    const int kidx = tid % bbp, chunk = tid / bbp;
+
+    for (int j = 0; j < bb; ++j) {
+        const int buf = j & 1;
+        const int nk = bb - j;
+        const int rstart = (int)max((int64_t)0, (int64_t)j + 1 - r0);
+        if (kidx < nk) {
+            const float* xj = S + (size_t)j * ldS;
+            const float* xk = S + (size_t)(j + kidx) * ldS;
+            float sacc = 0.f, cacc = 0.f;
+            for (int r = rstart + chunk; r < nrow; r += nchunk) dot2_acc(xj[r], xk[r], sacc, cacc);
+            red[chunk * bbp + kidx] = (double)sacc + (double)cacc;
+        }
+        __syncthreads();
+        if (tid < nk) {
+            double sv = 0.0;
+            for (int c = 0; c < nchunk; ++c) sv += red[c * bbp + tid];
+            part[((size_t)buf * G + g) * bb + tid] = sv;
+        }
+        if (r0 <= j && j < r0 + nrow) {
+            const int rj = (int)(j - r0);
+            for (int kk = tid; kk < nk; kk += NTH) diag[(size_t)buf * bb + kk] = (double)S[(size_t)(j + kk) * ldS + rj];
+        }
+        if (!grid_barrier(st)) return;
+        {
+            double sv = 0.0;
+            if (kidx < nk) {
+#pragma unroll 8
+                for (int h = chunk; h < G; h += nchunk) sv += ld_cg(&part[((size_t)buf * G + h) * bb + kidx]);
+            }
+            red[chunk * bbp + kidx] = sv;
+        }
+        __syncthreads();
+        if (tid < nk) {
+            double sv = 0.0;
+            for (int c = 0; c < nchunk; ++c) sv += red[c * bbp + tid];
+            sums[tid] = sv;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double alpha = ld_cg(&diag[(size_t)buf * bb]);
+            const double ss = sums[0];
+            double tj = 0.0, beta = alpha, scal = 0.0;
+            if (ss != 0.0) {
+                const double nrm = sqrt(alpha * alpha + ss);
+                beta = (alpha >= 0.0) ? -nrm : nrm;
+                tj = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            sh_tau = tj;
+            sh_beta = beta;
+            sh_scal = scal;
+            if (g == 0) tau[j] = tj;
+        }
+        __syncthreads();
+        if (tid > 0 && tid < nk)
+            wk[tid] = (float)(sh_tau * (ld_cg(&diag[(size_t)buf * bb + tid]) + sh_scal * sums[tid]));
+        float* xj = S + (size_t)j * ldS;
+        if (sh_tau != 0.0)
+            for (int r = rstart + tid; r < nrow; r += NTH) xj[r] = (float)((double)xj[r] * sh_scal);
+        __syncthreads();
+        if (sh_tau != 0.0) {
+            for (int r = rstart + tid; r < nrow; r += NTH) {
+                const float v = xj[r];
+                for (int kk = 1; kk < nk; ++kk) S[(size_t)(j + kk) * ldS + r] = fmaf(-wk[kk], v, S[(size_t)(j + kk) * ldS + r]);
+            }
+            if (r0 <= j && j < r0 + nrow) {
+                const int rj = (int)(j - r0);
+                for (int kk = 1 + tid; kk < nk; kk += NTH) S[(size_t)(j + kk) * ldS + rj] -= wk[kk];
+            }
+        }
+        if (r0 <= j && j < r0 + nrow && tid == 0) S[(size_t)j * ldS + (j - r0)] = (float)sh_beta;
+        __syncthreads();
     }
+    for (int k = 0; k < bb; ++k)
+        for (int r = tid; r < nrow; r += NTH) A[(int64_t)k * lda + r0 + r] = S[(size_t)k * ldS + r];
+}
+
+size_t panel_f32_smem(int64_t rpb, int bb)
+{
+    const int bbp = pow2_at_least(bb);
+    const int nchunk = 256 / bbp;
+    return sizeof(double) * ((size_t)nchunk * bbp + (size_t)bbp) + sizeof(float) * ((size_t)bbp + (size_t)(rpb | 1) * bb);
 }
 
 size_t panel_smem(int64_t rpb, int bb)
 {
     const int bbp = pow2_at_least(bb);
     const int nchunk = 256 / bbp;
-    return sizeof(double) * ((size_t)(rpb | 1) * bb + (size_t)nchunk * bbp + (size_t)bbp);
+    return sizeof(double) * ((size_t)(rpb | 1) * bb + (size_t)nchunk * bbp + 2 * (size_t)bbp);
 }
 
 int64_t panel_blocks(int64_t m1)
@@ -156,23 +285,26 @@ template <typename T>
 cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, double* part, Status* st,
                          cudaStream_t s)
 {
+    constexpr bool f32 = sizeof(T) == 4;
+    const void* kern = f32 ? (const void*)panel_f32_kernel : (const void*)panel_kernel<double>;
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaError_t e = allow_max_dynamic_smem(panel_kernel<T>)) return e;
+        if (cudaError_t e = f32 ? allow_max_dynamic_smem(panel_f32_kernel) : allow_max_dynamic_smem(panel_kernel<double>))
+            return e;
         attr_set = true;
     }
     const int64_t G = panel_blocks(m1);
     const int64_t rpb = (m1 + G - 1) / G;
-    const size_t smem = panel_smem(rpb, bb);
+    const size_t smem = f32 ? panel_f32_smem(rpb, bb) : panel_smem(rpb, bb);
     const int threads = 256;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<T>, threads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if ((int64_t)per_sm * dev_info().sms < G) return cudaErrorCooperativeLaunchTooLarge;
     int64_t ldav = lda, m1v = m1, rpbv = rpb;
     int bbv = bb;
     void* args[] = {&A, &ldav, &m1v, &bbv, &rpbv, &tau, &part, &st};
-    return cudaLaunchCooperativeKernel((const void*)panel_kernel<T>, dim3((unsigned)G), dim3(threads), args, smem, s);
+    return cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(threads), args, smem, s);
 }
 
 template cudaError_t launch_panel<double>(double*, int64_t, int64_t, int, double*, double*, Status*, cudaStream_t);

@@ -51,9 +51,17 @@ __device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long
     v = sv[0]; p = sp[0]; idx = si[0];
 }
 
+// Per-column reduction over the TPC threads that share a column (adjacent lanes).
+template <typename T>
+__device__ __forceinline__ T column_sum(T v, int tpc)
+{
+    for (int o = 1; o < tpc; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t ldb, int l, int64_t n,
-                                                     int64_t i, int bb, int64_t cpb,
+                                                     int64_t i, int bb, int64_t cpb, int tpc,
                                                      int32_t* __restrict__ jpvt, int32_t* __restrict__ piv,
                                                      long long* __restrict__ swapmap,
                                                      double* __restrict__ cval, long long* __restrict__ cpos,
@@ -81,6 +89,8 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     long long* pivs = reinterpret_cast<long long*>(smem_raw + off);
     off += (size_t)bb * sizeof(long long);
     int* active = reinterpret_cast<int*>(smem_raw + off);
+    off += (size_t)cpb * sizeof(int);
+    double* nus = reinterpret_cast<double*>(smem_raw + ((off + 7) & ~(size_t)7));
 
     __shared__ double red_v[32];
     __shared__ long long red_p[32];
@@ -99,22 +109,36 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         active[s] = 1;
     }
     __syncthreads();
+    // Thread layout: tpc adjacent threads share column slot `sl`, thread `sub` takes rows
+    // r = sub, sub + tpc, ...  Column sums combine the tpc partials by shuffles.
+    const int sub = tid % tpc;
+    const int slots_per_pass = NTH / tpc;
+    const int my_slot0 = tid / tpc;
+    // initial squared norms of rows 0..l-1 (recomputed from the rows, Alg. 1 "Update r_s")
+    for (int sl = my_slot0; sl - my_slot0 < ((nloc + slots_per_pass - 1) / slots_per_pass) * slots_per_pass;
+         sl += slots_per_pass) {
+        T part = T(0);
+        if (sl < nloc) {
+            const T* col = cols + (size_t)sl * ldS;
+            for (int r = sub; r < l; r += tpc) part = fma(col[r], col[r], part);
+        }
+        part = column_sum(part, tpc);
+        if (sl < nloc && sub == 0) nus[sl] = (double)part;
+    }
+    __syncthreads();
     const double guard = guard_rel2 * __longlong_as_double((long long)st->nu0bits);
 
     int steps = bb;
     for (int t = 0; t < bb; ++t) {
         const long long c = i + t;
         const int buf = t & 1;
-        // 1. local candidate
+        // 1. local candidate from the norms of rows t..l-1
         double myv = -1.0;
         long long myp = LLONG_MAX;
         int mys = -1;
         for (int s = tid; s < nloc; s += NTH) {
             if (!active[s]) continue;
-            const T* col = cols + (size_t)s * ldS;
-            double nu = 0.0;
-            for (int r = t; r < l; ++r) nu += (double)col[r] * (double)col[r];
-            if (better(nu, pos[s], myv, myp)) { myv = nu; myp = pos[s]; mys = s; }
+            if (better(nus[s], pos[s], myv, myp)) { myv = nus[s]; myp = pos[s]; mys = s; }
         }
         block_argmax(myv, myp, mys, red_v, red_p, red_i);
         if (tid == 0) {
@@ -146,42 +170,68 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         }
         for (int r = tid; r < l; r += NTH) xs[r] = (double)ld_cg(&ccol[((size_t)buf * kMaxCand + wg) * l + r]);
         __syncthreads();
-        if (tid == 0) {
+        // Householder reflector from rows t..l-1 of the winner (xLARFG), warp 0, fixed order
+        if (tid < 32) {
             double ss = 0.0;
-            for (int r = t + 1; r < l; ++r) ss += xs[r] * xs[r];
-            const double alpha = xs[t];
-            double tau = 0.0, beta = alpha, scal = 0.0;
-            if (ss != 0.0) {
-                const double nrm = sqrt(alpha * alpha + ss);
-                beta = (alpha >= 0.0) ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
+            for (int r = t + 1 + tid; r < l; r += 32) ss += xs[r] * xs[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            if (tid == 0) {
+                const double alpha = xs[t];
+                double tau = 0.0, beta = alpha, scal = 0.0;
+                if (ss != 0.0) {
+                    const double nrm = sqrt(alpha * alpha + ss);
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scal = 1.0 / (alpha - beta);
+                }
+                sh_tau = tau;
+                sh_beta = beta;
+                sh_scal = scal;
+                if (g == 0) pivs[t] = wp;
             }
-            sh_tau = tau;
-            sh_beta = beta;
-            sh_scal = scal;
-            if (g == 0) pivs[t] = wp;
         }
         __syncthreads();
         for (int r = t + 1 + tid; r < l; r += NTH) vT[r] = (T)(xs[r] * sh_scal);
+        if (tid == 0) vT[t] = T(1);
         __syncthreads();
+        // 4. apply H to every remaining column, then the norms of rows t+1..l-1 for step t+1
         const T tauT = (T)sh_tau;
-        for (int s = tid; s < nloc; s += NTH) {
-            T* col = cols + (size_t)s * ldS;
-            if (pos[s] == wp) {  // the winner: becomes column c of R_hat
-                col[t] = (T)sh_beta;
-                for (int r = t + 1; r < l; ++r) col[r] = T(0);
-                active[s] = 0;
-                pos[s] = c;
-                continue;
+        const bool apply = sh_tau != 0.0;
+        for (int sl = my_slot0; sl - my_slot0 < ((nloc + slots_per_pass - 1) / slots_per_pass) * slots_per_pass;
+             sl += slots_per_pass) {
+            const bool mine = sl < nloc;
+            T* col = cols + (size_t)(mine ? sl : 0) * ldS;
+            const bool winner = mine && pos[sl] == wp;
+            const bool live = mine && active[sl] && !winner;
+            // rows owned by this thread at and below t: r = t + ((sub - t) mod tpc) + j*tpc
+            const int r0 = t + ((sub - (t % tpc)) + tpc) % tpc;
+            T w = T(0);
+            if (live && apply)
+                for (int r = r0; r < l; r += tpc) w = fma(vT[r], col[r], w);
+            w = column_sum(w, tpc);
+            T nu = T(0);
+            if (live) {
+                const T wt = w * tauT;
+                for (int r = r0; r < l; r += tpc) {
+                    T x = col[r];
+                    if (apply) x = fma(-wt, vT[r], x);
+                    col[r] = x;
+                    if (r > t) nu = fma(x, x, nu);
+                }
             }
-            if (pos[s] == c) pos[s] = wp;  // the column displaced by the swap
-            if (!active[s] || sh_tau == 0.0) continue;
-            T w = col[t];
-            for (int r = t + 1; r < l; ++r) w += vT[r] * col[r];
-            w *= tauT;
-            col[t] -= w;
-            for (int r = t + 1; r < l; ++r) col[r] -= w * vT[r];
+            nu = column_sum(nu, tpc);
+            if (mine && sub == 0) {
+                if (winner) {
+                    active[sl] = 0;
+                    pos[sl] = c;
+                } else {
+                    if (pos[sl] == c) pos[sl] = wp;  // the column displaced by the swap
+                    nus[sl] = (double)nu;
+                }
+            }
+            if (winner)  // becomes column c of R_hat
+                for (int r = r0; r < l; r += tpc) col[r] = (r == t) ? (T)sh_beta : T(0);
         }
         __syncthreads();
     }
@@ -235,6 +285,8 @@ size_t pivot_smem(int64_t cpb, int l, int bb)
     off += (size_t)cpb * sizeof(long long) + (size_t)l * sizeof(double);
     off += ((size_t)l * sizeof(T) + 15) & ~(size_t)15;
     off += (size_t)bb * sizeof(long long) + (size_t)cpb * sizeof(int);
+    off = (off + 7) & ~(size_t)7;
+    off += (size_t)cpb * sizeof(double);
     return off;
 }
 
@@ -265,12 +317,15 @@ cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb,
         attr_set = true;
     }
     const int64_t nprime = n - i;
-    int64_t G = (nprime + 63) / 64;
+    // every SM takes a slice of at least 8 columns; tpc threads share a column
+    int64_t G = (nprime + 7) / 8;
     if (G > dev_info().sms) G = dev_info().sms;
     if (G < 1) G = 1;
     const int64_t cpb = (nprime + G - 1) / G;
-    int threads = (int)(((cpb + 31) / 32) * 32);
-    if (threads < 128) threads = 128;
+    int tpc = 4;
+    while (tpc > 1 && cpb * tpc > 1024) tpc >>= 1;
+    int threads = (int)(((cpb * tpc + 31) / 32) * 32);
+    if (threads < 64) threads = 64;
     if (threads > 1024) threads = 1024;
     const size_t smem = pivot_smem<T>(cpb, l, bb);
     int per_sm = 0;
@@ -287,8 +342,9 @@ cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb,
     int bbv = bb;
     int lv = l;
     int64_t ldbv = ldb, nv = n, iv = i, cpbv = cpb;
+    int tpcv = tpc;
     double gr = guard_rel2;
-    void* args[] = {&B, &ldbv, &lv, &nv, &iv, &bbv, &cpbv, &jpvt, &piv, &swapmap, &cval, &cpos, &ccol, &gr, &st};
+    void* args[] = {&B, &ldbv, &lv, &nv, &iv, &bbv, &cpbv, &tpcv, &jpvt, &piv, &swapmap, &cval, &cpos, &ccol, &gr, &st};
     return cudaLaunchCooperativeKernel((const void*)pivot_kernel<T>, dim3((unsigned)G), dim3(threads), args, smem, s);
 }
 

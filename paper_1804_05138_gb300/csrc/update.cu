@@ -50,27 +50,40 @@ __global__ void swap_scatter_kernel(T* __restrict__ A, int64_t lda, int64_t m,
         A[dst * lda + r] = tmp[e * m + r];
 }
 
-// One block: row r of Omega_hat_11 by thread r (forward substitution over columns j).
+// One block per row r of Omega_hat_11 = R_hat11 R11^{-1}: the rows of the forward substitution
+// Omega_hat_11(r,j) = (R_hat11(r,j) - sum_{q=r}^{j-1} Omega_hat_11(r,q) R11(q,j)) / R11(j,j)
+// are independent.  R11(r:bb, r:bb) goes to shared memory; warp 0 runs the recurrence.
 template <typename T>
 __global__ void bsolve_kernel(const T* __restrict__ B, int64_t ldb, const T* __restrict__ A, int64_t lda,
                               int64_t i, int bb, double* __restrict__ What, const Status* st)
 {
     if (status_error(st) || *(volatile const int*)&st->guard) return;
-    extern __shared__ double R11[];  // bb x bb column-major
-    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
-        const int q = e % bb, j = e / bb;
-        R11[e] = (double)A[(i + j) * lda + i + q];
+    extern __shared__ double sm[];
+    const int r = blockIdx.x;
+    const int w = bb - r;
+    double* Rs = sm;          // Rs[jj * w + qq] = R11(r + qq, r + jj), qq <= jj
+    double* Wr = sm + w * w;  // Omega_hat_11(r, r..bb-1)
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int qq = e % w, jj = e / w;
+        Rs[e] = (qq <= jj) ? (double)A[(i + r + jj) * lda + i + r + qq] : 0.0;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < bb; r += blockDim.x) {
-        for (int q = 0; q < r; ++q) What[q * bb + r] = 0.0;
-        for (int j = r; j < bb; ++j) {
-            double s = (double)B[(i + j) * ldb + r];
-            for (int q = r; q < j; ++q) s -= What[q * bb + r] * R11[j * bb + q];
-            const double rjj = R11[j * bb + j];
-            What[j * bb + r] = (rjj == 0.0) ? 0.0 : s / rjj;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int jj = 0; jj < w; ++jj) {
+            double s = 0.0;
+            for (int qq = lane; qq < jj; qq += 32) s += Wr[qq] * Rs[jj * w + qq];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                const double rjj = Rs[jj * w + jj];
+                Wr[jj] = (rjj == 0.0) ? 0.0 : ((double)B[(i + r + jj) * ldb + r] - s) / rjj;
+            }
+            __syncwarp();
         }
     }
+    __syncthreads();
+    for (int j = threadIdx.x; j < bb; j += blockDim.x) What[(int64_t)j * bb + r] = (j < r) ? 0.0 : Wr[j - r];
 }
 
 // B(r, c) -= sum_{q >= r} What(r, q) * A(i+q, c) for the trailing columns c.
@@ -128,9 +141,8 @@ cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i
         if (cudaError_t e = allow_max_dynamic_smem(bapply_kernel<T>)) return e;
         attr_set = true;
     }
-    const size_t smem = sizeof(double) * (size_t)bb * bb;
-    const int threads = ((bb + 31) / 32) * 32;
-    bsolve_kernel<T><<<1, threads, smem, s>>>(B, ldb, A, lda, i, bb, What, st);
+    const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)bb);
+    bsolve_kernel<T><<<bb, 128, smem, s>>>(B, ldb, A, lda, i, bb, What, st);
     const int64_t nt = n - i - bb;
     if (nt > 0) bapply_kernel<T><<<(unsigned)((nt + 63) / 64), 256, smem, s>>>(B, ldb, A, lda, i, bb, n, What, st);
     return cudaGetLastError();
