@@ -42,6 +42,10 @@ WORKLOADS = {
                           desc="plain FP64 full RQRCP 4096x4096, i.i.d. N(0,1), b=64, p=8 (profiling size)"),
     "fp64_1000_k64": dict(m=1000, n=1000, k=64, b=32, p=8, kind="logspec", prec="fp64",
                           desc="plain FP64 partial RQRCP k=64 on 1000x1000 U diag(10^(-6i/1000)) V^T, b=32, p=8"),
+    "diff_4096_k256": dict(m=4096, n=4096, k=256, b=64, p=8, kind="invsq", prec="diff",
+                           desc="differentiable truncated RQRCP: FP32 forward + backward of "
+                                "||A - Q1 [R11 R12] Pi^T||_F^2 + random upstream on (Q1, R), 4096x4096, "
+                                "sigma_i = 1/(1+i)^2, k=256, b=64, p=8"),
     "mixed_32768x16384_k512": dict(m=32768, n=16384, k=512, b=64, p=16, kind="expspec200", prec="mixed",
                                    desc="mixed partial RQRCP k=512 on 32768x16384 FP32 U diag(exp(-i/200)) V^T, "
                                         "b=64, p=16"),
@@ -75,6 +79,8 @@ def make_input_torch(w, device, seed=1):
     from paper_1804_05138_gb300 import inputs
     m, n = w["m"], w["n"]
     dt = torch.float64 if w["prec"] == "fp64" else torch.float32
+    if w["kind"] == "invsq":
+        return inputs.spectrum_matrix_torch(m, n, inputs.sigma_inverse_square(min(m, n)), device=device, dtype=dt)
     if w["kind"] == "iid":
         return inputs.gaussian_torch(m, n, seed, device=device, dtype=dt)
     if w["kind"] == "rank500":
@@ -97,6 +103,8 @@ def make_input_numpy(w, m, n):
         return inputs.rank_r_product(m, n, 500)
     if w["kind"] == "logspec":
         return inputs.spectrum_matrix(m, n, inputs.sigma_log_decay(min(m, n)))
+    if w["kind"] == "invsq":
+        return inputs.spectrum_matrix(m, n, inputs.sigma_inverse_square(min(m, n)))
     return inputs.spectrum_matrix(m, n, inputs.sigma_exp_decay(min(m, n), 200.0))
 
 
@@ -209,8 +217,11 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.set_device(dev)
     m, n, k, b, p = w["m"], w["n"], w["k"], w["b"], w["p"]
     l = b + p
-    mixed = w["prec"] == "mixed"
+    mixed = w["prec"] in ("mixed", "diff")
+    diff = w["prec"] == "diff"
     F = counted_flops(m, n, k, l)
+    if diff:  # forward (factor + Q1) and backward (thin-QR adjoint with the wide block)
+        F += 4.0 * m * k * k + 4.0 * m * (n - k) * k + 5.0 * m * k * k
     A0 = binding.colmajor(make_input_torch(w, dev, seed=1 + rank))
     A = torch.empty_like(A0.t()).t()
     jpvt = torch.empty(n, dtype=torch.int32, device=dev)
@@ -220,11 +231,24 @@ def run_ours(args, w, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     call = binding.rqrcp_factor_mixed if mixed else binding.rqrcp_factor
 
+    if diff:
+        from paper_1804_05138_gb300 import autograd as rq_autograd
+        gq = torch.randn((m, k), device=dev, generator=torch.Generator(device=dev).manual_seed(5)) * 1e-3
+        gr = torch.randn((k, n), device=dev, generator=torch.Generator(device=dev).manual_seed(6)) * 1e-3
+
     def one_step(timed_events=None):
         A.copy_(A0)
         if timed_events is not None:
             timed_events[0].record(stream)
-        code = call(A, k, b, p, 0, jpvt, tau, work)
+        if diff:
+            Ag = A.detach().requires_grad_(True)
+            Q1, R, jp = rq_autograd.rqrcp_truncated(Ag, k, b, p, 0)
+            E = Ag[:, jp.long()] - Q1 @ R
+            loss = (E * E).sum() + (gq * Q1).sum() + (gr * R).sum()
+            loss.backward()
+            code = 0
+        else:
+            code = call(A, k, b, p, 0, jpvt, tau, work)
         if timed_events is not None:
             timed_events[1].record(stream)
         if code != 0:
@@ -232,9 +256,11 @@ def run_ours(args, w, rank, world, local_rank):
 
     for _ in range(args.warmup):
         one_step()
-    code, rank_out = binding.rqrcp_read_status(work)
-    if code != 0:
-        raise binding.RQRCPError(code, "device status (warm-up)")
+    rank_out = k
+    if not diff:  # the differentiable step checks the status of its own workspaces
+        code, rank_out = binding.rqrcp_read_status(work)
+        if code != 0:
+            raise binding.RQRCPError(code, "device status (warm-up)")
 
     sampler = ClockSampler(gpu_smi_id(local_rank))
     if world > 1:
@@ -251,9 +277,10 @@ def run_ours(args, w, rank, world, local_rank):
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(bv) for a, bv in evs]
-    code, rank_out = binding.rqrcp_read_status(work)
-    if code != 0:
-        raise binding.RQRCPError(code, "device status (timed)")
+    if not diff:
+        code, rank_out = binding.rqrcp_read_status(work)
+        if code != 0:
+            raise binding.RQRCPError(code, "device status (timed)")
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -303,12 +330,20 @@ def run_ours(args, w, rank, world, local_rank):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         A.t().copy_(host_A, non_blocking=True)
-        code = call(A, k, b, p, 0, jpvt, tau, work)
-        if code != 0:
-            raise binding.RQRCPError(code, "factor (e2e)")
-        host_out.copy_(A.t(), non_blocking=True)
-        host_jpvt.copy_(jpvt, non_blocking=True)
-        host_tau.copy_(tau, non_blocking=True)
+        if diff:
+            Ag = A.detach().requires_grad_(True)
+            Q1, R, jp = rq_autograd.rqrcp_truncated(Ag, k, b, p, 0)
+            E = Ag[:, jp.long()] - Q1 @ R
+            ((E * E).sum() + (gq * Q1).sum() + (gr * R).sum()).backward()
+            host_out.copy_(Ag.grad.t(), non_blocking=True)
+            host_jpvt.copy_(jp, non_blocking=True)
+        else:
+            code = call(A, k, b, p, 0, jpvt, tau, work)
+            if code != 0:
+                raise binding.RQRCPError(code, "factor (e2e)")
+            host_out.copy_(A.t(), non_blocking=True)
+            host_jpvt.copy_(jpvt, non_blocking=True)
+            host_tau.copy_(tau, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         t_e2e.append(e0.elapsed_time(e1))

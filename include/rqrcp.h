@@ -116,14 +116,40 @@ int rqrcp_read_status(const void* work, int64_t* rank, void* stream);
 
 /*
  * Low-rank approximation L = Q1 [R11 R12] Pi^T (Sec. I-A) from the output of
- * rqrcp_factor: Afact (m x n, ldaf), tau (k), jpvt (n).  L is m x n (ldl >= m); Q1
- * (required, ldq >= m) receives the m x k matrix Q1 = H_0 ... H_{k-1} I(:,0:k).
- * `work` needs rqrcp_lowrank_workspace_size(m, n, k) bytes.
+ * rqrcp_factor: Afact (m x n, ldaf), tau (k), jpvt (n).  Q1 (required, ldq >= m) receives
+ * the m x k matrix Q1 = H_0 ... H_{k-1} I(:,0:k); L (m x n, ldl >= m) receives the product,
+ * or is skipped when L is NULL.  `work` needs rqrcp_lowrank_workspace_size(m, n, k) bytes.
+ * The _f32 twin takes the FP32 output of rqrcp_factor_mixed (tau stays FP64).
  */
 size_t rqrcp_lowrank_workspace_size(int64_t m, int64_t n, int64_t k);
 int rqrcp_lowrank(int64_t m, int64_t n, int64_t k, const double* Afact, int64_t ldaf, const double* tau,
                   const int32_t* jpvt, double* L, int64_t ldl, double* Q1, int64_t ldq, void* work,
                   size_t work_bytes, void* stream);
+int rqrcp_lowrank_f32(int64_t m, int64_t n, int64_t k, const float* Afact, int64_t ldaf, const double* tau,
+                      const int32_t* jpvt, float* L, int64_t ldl, float* Q1, int64_t ldq, void* work,
+                      size_t work_bytes, void* stream);
+
+/*
+ * Gradient of the truncated factorization with the permutation held fixed (the paper has
+ * the forward only; this is the adjoint of what Alg. 2 computes for the first k columns).
+ * With X = A Pi = [X1 X2], X1 = Q1 R11 and R12 = Q1^T X2, given upstream gradients dQ1
+ * (m x k, lddq) and dR = [dR11 dR12] (k x n, lddr; only the upper triangle of dR11 is read),
+ * writes dA (m x n, ldda):  dX2 = Q1 dR12;  dQ' = dQ1 + X2 dR12^T;
+ * M = R11 dR11^T - dQ'^T Q1;  dX1 = (dQ' + Q1 copyltu(M)) R11^{-T}, copyltu(M) =
+ * tril(M) + tril(M,-1)^T;  dA(:, jpvt[c]) = dX(:, c).  Inputs: the original A (lda), jpvt
+ * (n, from the forward), Q1 (ldq) and R = [R11 R12] (k x n, ldr, R11 read as upper
+ * triangular), all device memory.  A zero diagonal entry of R11 gives a zero gradient
+ * column.  `work` needs rqrcp_backward_workspace_size(m, n, k, precision) bytes.
+ */
+size_t rqrcp_backward_workspace_size(int64_t m, int64_t n, int64_t k, int precision);
+int rqrcp_backward(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const int32_t* jpvt,
+                   const double* Q1, int64_t ldq, const double* R, int64_t ldr, const double* dQ1,
+                   int64_t lddq, const double* dR, int64_t lddr, double* dA, int64_t ldda, void* work,
+                   size_t work_bytes, void* stream);
+int rqrcp_backward_f32(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const int32_t* jpvt,
+                       const float* Q1, int64_t ldq, const float* R, int64_t ldr, const float* dQ1,
+                       int64_t lddq, const float* dR, int64_t lddr, float* dA, int64_t ldda, void* work,
+                       size_t work_bytes, void* stream);
 
 /*
  * Sketch B = Omega A for callers that cannot allocate device memory.  The paper has no
@@ -156,7 +182,7 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  * launches[c], the summed event time ms[c], flops[c] and bytes[c] (any pointer may be
  * NULL).  Host-side state is global to the process; not thread-safe.
  */
-#define RQRCP_PROFILE_CLASSES 12
+#define RQRCP_PROFILE_CLASSES 13
 int rqrcp_profile_begin(void);
 int rqrcp_profile_end(int nmax, int64_t* launches, double* ms, double* flops, double* bytes);
 const char* rqrcp_profile_class_name(int cls);

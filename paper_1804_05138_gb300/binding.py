@@ -31,9 +31,10 @@ ABI_SYMBOLS = (
     "rqrcp_sketch", "rqrcp_factor", "rqrcp_factor_with_omega", "rqrcp_factor_mixed",
     "rqrcp_read_status", "rqrcp_lowrank_workspace_size", "rqrcp_lowrank",
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
-    "rqrcp_sketch_noalloc",
+    "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
+    "rqrcp_backward_f32",
 )
-RQRCP_PROFILE_CLASSES = 12
+RQRCP_PROFILE_CLASSES = 13
 
 _lock = threading.Lock()
 _lib = None
@@ -77,6 +78,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  ctypes.POINTER(ctypes.c_double)]),
             "rqrcp_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
             "rqrcp_sketch_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp]),
+            "rqrcp_lowrank_f32": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
+                                                 _sz, _vp]),
+            "rqrcp_backward_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
+            "rqrcp_backward": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64,
+                                              _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
+            "rqrcp_backward_f32": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64,
+                                                  _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -185,9 +193,24 @@ def rqrcp_read_status(work, stream=None) -> tuple[int, int]:
 
 
 def rqrcp_lowrank(Afact, k, tau, jpvt, L, Q1, work, stream=None) -> int:
+    """L may be None (only Q1 is formed).  Dispatches on Afact's dtype (FP64 or FP32 twin)."""
     m, n = Afact.shape
-    return load().rqrcp_lowrank(m, n, k, _ptr(Afact), _ld(Afact), _ptr(tau), _ptr(jpvt), _ptr(L), _ld(L),
-                                _ptr(Q1), _ld(Q1), _ptr(work), work.numel(), _stream(stream))
+    fn = load().rqrcp_lowrank if Afact.element_size() == 8 else load().rqrcp_lowrank_f32
+    return fn(m, n, k, _ptr(Afact), _ld(Afact), _ptr(tau), _ptr(jpvt), _ptr(L), _ld(L) if L is not None else m,
+              _ptr(Q1), _ld(Q1), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_backward_workspace_size(m, n, k, precision=RQRCP_PREC_FP64) -> int:
+    return int(load().rqrcp_backward_workspace_size(m, n, k, precision))
+
+
+def rqrcp_backward(A, jpvt, Q1, R, dQ1, dR, dA, work, stream=None) -> int:
+    """dA from the upstream gradients of (Q1, R); dispatches on dtype (FP64 or FP32 twin)."""
+    m, n = A.shape
+    k = Q1.shape[1]
+    fn = load().rqrcp_backward if A.element_size() == 8 else load().rqrcp_backward_f32
+    return fn(m, n, k, _ptr(A), _ld(A), _ptr(jpvt), _ptr(Q1), _ld(Q1), _ptr(R), _ld(R), _ptr(dQ1), _ld(dQ1),
+              _ptr(dR), _ld(dR), _ptr(dA), _ld(dA), _ptr(work), work.numel(), _stream(stream))
 
 
 def rqrcp_profile_begin() -> int:
@@ -268,13 +291,13 @@ def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, 
 
 
 def lowrank(f: Factorization, stream=None):
-    """L = Q1 [R11 R12] Pi^T and Q1 from a plain FP64 factorization."""
+    """L = Q1 [R11 R12] Pi^T and Q1 from a factorization (FP64, or FP32 from the mixed form)."""
     import torch
     m, n = f.A.shape
     k = f.k
     dev = f.A.device
-    L = torch.empty((n, m), dtype=torch.float64, device=dev).t()
-    Q1 = torch.empty((k, m), dtype=torch.float64, device=dev).t()
+    L = torch.empty((n, m), dtype=f.A.dtype, device=dev).t()
+    Q1 = torch.empty((k, m), dtype=f.A.dtype, device=dev).t()
     work = workspace(rqrcp_lowrank_workspace_size(m, n, k), dev)
     _check(rqrcp_lowrank(f.A, k, f.tau, f.jpvt, L, Q1, work, stream), "rqrcp_lowrank")
     status, _ = rqrcp_read_status(work, stream)

@@ -32,8 +32,10 @@ const DevInfo& dev_info()
     return cache[d];
 }
 
-cudaError_t launch_lowrank_rk(const double* Af, int64_t ldaf, int64_t k, int64_t n, double* Rk, cudaStream_t s);
-cudaError_t launch_eye(double* Q, int64_t ldq, int64_t m, int64_t k, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lowrank_rk(const T* Af, int64_t ldaf, int64_t k, int64_t n, double* Rk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_eye(T* Q, int64_t ldq, int64_t m, int64_t k, cudaStream_t s);
 
 namespace {
 
@@ -215,6 +217,69 @@ int validate_factor(int64_t m, int64_t n, const void* A, int64_t lda, int64_t k,
 
 using namespace rq;
 
+extern "C" size_t rqrcp_lowrank_workspace_size(int64_t m, int64_t n, int64_t k);
+
+namespace rq {
+namespace {
+template <typename T>
+int lowrank_impl(int64_t m, int64_t n, int64_t k, const T* Afact, int64_t ldaf, const double* tau,
+                 const int32_t* jpvt, T* L, int64_t ldl, T* Q1, int64_t ldq, void* work, size_t work_bytes,
+                 void* stream)
+{
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (k < 1 || k > (m < n ? m : n)) return -3;
+    if (Afact == nullptr) return -4;
+    if (ldaf < m) return -5;
+    if (tau == nullptr) return -6;
+    if (jpvt == nullptr) return -7;
+    if (L != nullptr && ldl < m) return -9;
+    if (Q1 == nullptr) return -10;
+    if (ldq < m) return -11;
+    const size_t need = rqrcp_lowrank_workspace_size(m, n, k);
+    if (int e = check_work(work, work_bytes, need)) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t bb = 64;
+    char* w = static_cast<char*>(work);
+    size_t off = 0;
+    Status* st = reinterpret_cast<Status*>(w);
+    off = align_up(off + sizeof(Status));
+    double* P = reinterpret_cast<double*>(w + off);
+    off = align_up(off + (size_t)kMaxSplit * (size_t)(k > bb ? k : bb) * bb * sizeof(double));
+    double* Tm = reinterpret_cast<double*>(w + off);
+    off = align_up(off + (size_t)bb * bb * sizeof(double));
+    double* Y = reinterpret_cast<double*>(w + off);
+    RQ_CHECK(launch_init(st, k, nullptr, 0, s));
+    // Q1 = H_0 ... H_{k-1} I(:, 0:k), accumulated backwards block by block:
+    // Q1(i:m, :) <- (I - V T V^T) Q1(i:m, :).
+    RQ_CHECK(launch_eye<T>(Q1, ldq, m, k, s));
+    const int64_t last = ((k - 1) / bb) * bb;
+    for (int64_t i = last; i >= 0; i -= bb) {
+        const int kb = (int)(bb < k - i ? bb : k - i);
+        const T* Vp = Afact + i * ldaf + i;
+        const int64_t mr = m - i;
+        int ns;
+        int64_t kc;
+        choose_split(kb, kb, mr, ns, kc);
+        RQ_CHECK(launch_gemm_tn<T>(Vp, ldaf, Vp, ldaf, kb, kb, mr, kc, P, 1, kb, st, s));
+        RQ_CHECK(launch_tform(P, ns, kb, kb, tau + i, Tm, st, s));
+        const int64_t nq = k - i;  // columns of Q1 touched by this block: i..k-1
+        choose_split(kb, nq, mr, ns, kc);
+        RQ_CHECK(launch_gemm_tn<T>(Vp, ldaf, Q1 + i * ldq + i, ldq, kb, nq, mr, kc, P, 1, 0, st, s));
+        RQ_CHECK(launch_reduce_y(P, ns, nq, 0, kb, Tm, 0, Y, nq, st, s));
+        RQ_CHECK(launch_gemm_update<T>(Q1 + i * ldq + i, ldq, Vp, ldaf, Y, kb, mr, nq, kb, 1, nullptr, st, s));
+    }
+    // L(:, jpvt[c]) = Q1 [R11 R12](:, c)  as  L -= Q1 (-Rk) with a column scatter.
+    if (L == nullptr) return RQRCP_OK;
+    RQ_CHECK(launch_lowrank_rk<T>(Afact, ldaf, k, n, Y, s));
+    RQ_CHECK(cudaMemset2DAsync(L, ldl * sizeof(T), 0, m * sizeof(T), n, s));
+    RQ_CHECK(launch_gemm_update<T>(L, ldl, Q1, ldq, Y, k, m, n, k, 0, jpvt, st, s));
+    return RQRCP_OK;
+}
+
+}  // namespace
+}  // namespace rq
+
 extern "C" {
 
 __attribute__((visibility("default"))) const char* rqrcp_error_string(int code)
@@ -354,55 +419,15 @@ __attribute__((visibility("default"))) int rqrcp_lowrank(int64_t m, int64_t n, i
                                                          double* L, int64_t ldl, double* Q1, int64_t ldq,
                                                          void* work, size_t work_bytes, void* stream)
 {
-    if (m < 1) return -1;
-    if (n < 1) return -2;
-    if (k < 1 || k > (m < n ? m : n)) return -3;
-    if (Afact == nullptr) return -4;
-    if (ldaf < m) return -5;
-    if (tau == nullptr) return -6;
-    if (jpvt == nullptr) return -7;
-    if (L == nullptr) return -8;
-    if (ldl < m) return -9;
-    if (Q1 == nullptr) return -10;
-    if (ldq < m) return -11;
-    const size_t need = rqrcp_lowrank_workspace_size(m, n, k);
-    if (int e = check_work(work, work_bytes, need)) return e;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t bb = 64;
-    char* w = static_cast<char*>(work);
-    size_t off = 0;
-    Status* st = reinterpret_cast<Status*>(w);
-    off = align_up(off + sizeof(Status));
-    double* P = reinterpret_cast<double*>(w + off);
-    off = align_up(off + (size_t)kMaxSplit * (size_t)(k > bb ? k : bb) * bb * sizeof(double));
-    double* Tm = reinterpret_cast<double*>(w + off);
-    off = align_up(off + (size_t)bb * bb * sizeof(double));
-    double* Y = reinterpret_cast<double*>(w + off);
-    RQ_CHECK(launch_init(st, k, nullptr, 0, s));
-    // Q1 = H_0 ... H_{k-1} I(:, 0:k), accumulated backwards block by block:
-    // Q1(i:m, :) <- (I - V T V^T) Q1(i:m, :).
-    RQ_CHECK(launch_eye(Q1, ldq, m, k, s));
-    const int64_t last = ((k - 1) / bb) * bb;
-    for (int64_t i = last; i >= 0; i -= bb) {
-        const int kb = (int)(bb < k - i ? bb : k - i);
-        const double* Vp = Afact + i * ldaf + i;
-        const int64_t mr = m - i;
-        int ns;
-        int64_t kc;
-        choose_split(kb, kb, mr, ns, kc);
-        RQ_CHECK(launch_gemm_tn<double>(Vp, ldaf, Vp, ldaf, kb, kb, mr, kc, P, 1, kb, st, s));
-        RQ_CHECK(launch_tform(P, ns, kb, kb, tau + i, Tm, st, s));
-        const int64_t nq = k - i;  // columns of Q1 touched by this block: i..k-1
-        choose_split(kb, nq, mr, ns, kc);
-        RQ_CHECK(launch_gemm_tn<double>(Vp, ldaf, Q1 + i * ldq + i, ldq, kb, nq, mr, kc, P, 1, 0, st, s));
-        RQ_CHECK(launch_reduce_y(P, ns, nq, 0, kb, Tm, 0, Y, nq, st, s));
-        RQ_CHECK(launch_gemm_update<double>(Q1 + i * ldq + i, ldq, Vp, ldaf, Y, kb, mr, nq, kb, 1, nullptr, st, s));
-    }
-    // L(:, jpvt[c]) = Q1 [R11 R12](:, c)  as  L -= Q1 (-Rk) with a column scatter.
-    RQ_CHECK(launch_lowrank_rk(Afact, ldaf, k, n, Y, s));
-    RQ_CHECK(cudaMemset2DAsync(L, ldl * sizeof(double), 0, m * sizeof(double), n, s));
-    RQ_CHECK(launch_gemm_update<double>(L, ldl, Q1, ldq, Y, k, m, n, k, 0, jpvt, st, s));
-    return RQRCP_OK;
+    return lowrank_impl<double>(m, n, k, Afact, ldaf, tau, jpvt, L, ldl, Q1, ldq, work, work_bytes, stream);
+}
+
+__attribute__((visibility("default"))) int rqrcp_lowrank_f32(int64_t m, int64_t n, int64_t k, const float* Afact,
+                                                             int64_t ldaf, const double* tau, const int32_t* jpvt,
+                                                             float* L, int64_t ldl, float* Q1, int64_t ldq,
+                                                             void* work, size_t work_bytes, void* stream)
+{
+    return lowrank_impl<float>(m, n, k, Afact, ldaf, tau, jpvt, L, ldl, Q1, ldq, work, work_bytes, stream);
 }
 
 }  // extern "C"
