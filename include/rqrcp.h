@@ -130,6 +130,22 @@ int rqrcp_lowrank_f32(int64_t m, int64_t n, int64_t k, const float* Afact, int64
                       size_t work_bytes, void* stream);
 
 /*
+ * FP64 outputs of the mixed form with one FP64 reorthogonalisation pass (the paper's low-rank
+ * factors Q1 and [R11 R12], Sec. I-A; the pass itself is not in the paper).  From the output of
+ * rqrcp_factor_mixed (Afact FP32, tau FP64) forms Q1 (m x k, FP64, ldq >= m) and
+ * R = [R11 R12] (k x n, FP64, ldr >= k, zero below the diagonal), measures
+ * e = ||Q1^T Q1 - I||_F and, when e > tol, applies one CholQR pass on the device:
+ * G = Q1^T Q1 = S^T S (S upper), Q1 <- Q1 S^{-1}, R <- S R, which keeps Q1 R unchanged.  The
+ * decision is taken on the device (no host synchronisation); *orth (device, may be NULL)
+ * receives e.  `work` needs rqrcp_reorth_workspace_size(m, n, k) bytes.  A Gram matrix that
+ * is not positive definite is reported as RQRCP_ERR_NONFINITE by rqrcp_read_status(work).
+ */
+size_t rqrcp_reorth_workspace_size(int64_t m, int64_t n, int64_t k);
+int rqrcp_lowrank_reorth(int64_t m, int64_t n, int64_t k, const float* Afact, int64_t ldaf, const double* tau,
+                         double* Q1, int64_t ldq, double* R, int64_t ldr, double tol, double* orth, void* work,
+                         size_t work_bytes, void* stream);
+
+/*
  * Gradient of the truncated factorization with the permutation held fixed (the paper has
  * the forward only; this is the adjoint of what Alg. 2 computes for the first k columns).
  * With X = A Pi = [X1 X2], X1 = Q1 R11 and R12 = Q1^T X2, given upstream gradients dQ1

@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "rqrcp_read_status", "rqrcp_lowrank_workspace_size", "rqrcp_lowrank",
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
-    "rqrcp_backward_f32",
+    "rqrcp_backward_f32", "rqrcp_reorth_workspace_size", "rqrcp_lowrank_reorth",
 )
 RQRCP_PROFILE_CLASSES = 13
 
@@ -81,6 +81,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "rqrcp_lowrank_f32": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
                                                  _sz, _vp]),
             "rqrcp_backward_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
+            "rqrcp_reorth_workspace_size": (_sz, [_i64, _i64, _i64]),
+            "rqrcp_lowrank_reorth": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64,
+                                                    ctypes.c_double, _vp, _vp, _sz, _vp]),
             "rqrcp_backward": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64,
                                               _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
             "rqrcp_backward_f32": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64,
@@ -198,6 +201,17 @@ def rqrcp_lowrank(Afact, k, tau, jpvt, L, Q1, work, stream=None) -> int:
     fn = load().rqrcp_lowrank if Afact.element_size() == 8 else load().rqrcp_lowrank_f32
     return fn(m, n, k, _ptr(Afact), _ld(Afact), _ptr(tau), _ptr(jpvt), _ptr(L), _ld(L) if L is not None else m,
               _ptr(Q1), _ld(Q1), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_reorth_workspace_size(m, n, k) -> int:
+    return int(load().rqrcp_reorth_workspace_size(m, n, k))
+
+
+def rqrcp_lowrank_reorth(Afact, k, tau, Q1, R, tol, orth, work, stream=None) -> int:
+    """FP64 Q1 (m x k) and R (k x n) from a mixed factorization; CholQR pass when ||Q1^T Q1 - I||_F > tol."""
+    m, n = Afact.shape
+    return load().rqrcp_lowrank_reorth(m, n, k, _ptr(Afact), _ld(Afact), _ptr(tau), _ptr(Q1), _ld(Q1), _ptr(R),
+                                       _ld(R), float(tol), _ptr(orth), _ptr(work), work.numel(), _stream(stream))
 
 
 def rqrcp_backward_workspace_size(m, n, k, precision=RQRCP_PREC_FP64) -> int:

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
     double* red = S + (size_t)ldS * bb;  // nchunk x bbp
     double* wk = red + (size_t)nchunk * bbp;
     double* sums = wk + bbp;
+    double* dg = sums + bbp;  // the published diagonal row
     double* diag = part + 2 * (size_t)G * bb;  // 2 x bb, after the partials
     __shared__ double sh_tau, sh_beta, sh_scal;
 
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
                 for (int h = chunk; h < G; h += nchunk) s += ld_cg(&part[((size_t)buf * G + h) * bb + kidx]);
             }
             red[chunk * bbp + kidx] = s;
+            if (tid < nk) dg[tid] = ld_cg(&diag[(size_t)buf * bb + tid]);
         }
         __syncthreads();
         if (tid < nk) {
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
         }
         __syncthreads();
         if (tid == 0) {
-            const double alpha = ld_cg(&diag[(size_t)buf * bb]);
+            const double alpha = dg[0];
             const double ss = sums[0];
             double tj = 0.0, beta = alpha, scal = 0.0;
             if (ss != 0.0) {
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
             if (g == 0) tau[j] = tj;
         }
         __syncthreads();
-        if (tid > 0 && tid < nk) wk[tid] = sh_tau * (ld_cg(&diag[(size_t)buf * bb + tid]) + sh_scal * sums[tid]);
+        if (tid > 0 && tid < nk) wk[tid] = sh_tau * (dg[tid] + sh_scal * sums[tid]);
         double* xj = S + (size_t)j * ldS;
         if (sh_tau != 0.0)
             for (int r = rstart + tid; r < nrow; r += NTH) xj[r] *= sh_scal;
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
     const int nchunk = NTH / bbp;
     double* red = smd;                    // nchunk x bbp
     double* sums = red + (size_t)nchunk * bbp;
-    float* wk = reinterpret_cast<float*>(sums + bbp);  // bbp floats
+    double* dg = sums + bbp;  // the published diagonal row
+    float* wk = reinterpret_cast<float*>(dg + bbp);  // bbp floats
     float* S = wk + bbp;                  // ldS x bb
     const int ldS = (int)(rpb | 1);
     double* diag = part + 2 * (size_t)G * bb;
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
                 for (int h = chunk; h < G; h += nchunk) sv += ld_cg(&part[((size_t)buf * G + h) * bb + kidx]);
             }
             red[chunk * bbp + kidx] = sv;
+            if (tid < nk) dg[tid] = ld_cg(&diag[(size_t)buf * bb + tid]);
         }
         __syncthreads();
         if (tid < nk) {
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
         }
         __syncthreads();
         if (tid == 0) {
-            const double alpha = ld_cg(&diag[(size_t)buf * bb]);
+            const double alpha = dg[0];
             const double ss = sums[0];
             double tj = 0.0, beta = alpha, scal = 0.0;
             if (ss != 0.0) {
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
         }
         __syncthreads();
         if (tid > 0 && tid < nk)
-            wk[tid] = (float)(sh_tau * (ld_cg(&diag[(size_t)buf * bb + tid]) + sh_scal * sums[tid]));
+            wk[tid] = (float)(sh_tau * (dg[tid] + sh_scal * sums[tid]));
         float* xj = S + (size_t)j * ldS;
         if (sh_tau != 0.0)
             for (int r = rstart + tid; r < nrow; r += NTH) xj[r] = (float)((double)xj[r] * sh_scal);
@@ -248,14 +252,14 @@ size_t panel_f32_smem(int64_t rpb, int bb)
 {
     const int bbp = pow2_at_least(bb);
     const int nchunk = 256 / bbp;
-    return sizeof(double) * ((size_t)nchunk * bbp + (size_t)bbp) + sizeof(float) * ((size_t)bbp + (size_t)(rpb | 1) * bb);
+    return sizeof(double) * ((size_t)nchunk * bbp + 2 * (size_t)bbp) + sizeof(float) * ((size_t)bbp + (size_t)(rpb | 1) * bb);
 }
 
 size_t panel_smem(int64_t rpb, int bb)
 {
     const int bbp = pow2_at_least(bb);
     const int nchunk = 256 / bbp;
-    return sizeof(double) * ((size_t)(rpb | 1) * bb + (size_t)nchunk * bbp + 2 * (size_t)bbp);
+    return sizeof(double) * ((size_t)(rpb | 1) * bb + (size_t)nchunk * bbp + 3 * (size_t)bbp);
 }
 
 int64_t panel_blocks(int64_t m1)

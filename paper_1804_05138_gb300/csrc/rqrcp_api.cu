@@ -232,7 +232,7 @@ int lowrank_impl(int64_t m, int64_t n, int64_t k, const T* Afact, int64_t ldaf, 
     if (Afact == nullptr) return -4;
     if (ldaf < m) return -5;
     if (tau == nullptr) return -6;
-    if (jpvt == nullptr) return -7;
+    if (L != nullptr && jpvt == nullptr) return -7;
     if (L != nullptr && ldl < m) return -9;
     if (Q1 == nullptr) return -10;
     if (ldq < m) return -11;
@@ -278,6 +278,17 @@ int lowrank_impl(int64_t m, int64_t n, int64_t k, const T* Afact, int64_t ldaf, 
 }
 
 }  // namespace
+
+// Q1 only (no low-rank product, no permutation), for the FP64 reorthogonalisation path.
+template <typename T>
+int lowrank_q1_only(int64_t m, int64_t k, const T* Afact, int64_t ldaf, const double* tau, T* Q1, int64_t ldq,
+                    void* work, size_t work_bytes, cudaStream_t s)
+{
+    return lowrank_impl<T>(m, k, k, Afact, ldaf, tau, nullptr, nullptr, m, Q1, ldq, work, work_bytes, s);
+}
+template int lowrank_q1_only<double>(int64_t, int64_t, const double*, int64_t, const double*, double*, int64_t,
+                                     void*, size_t, cudaStream_t);
+
 }  // namespace rq
 
 extern "C" {
