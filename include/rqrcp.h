@@ -100,7 +100,8 @@ int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_
  * Mixed form of Alg. 2: A is FP32 (lda >= m); the sketch, pivot search, trailing
  * updates and Eq. (4) run in FP32 arithmetic; every Householder reflector (column norm,
  * beta, tau) of the panel is generated in FP64 and tau is returned in FP64.  Arguments
- * and output layout as in rqrcp_factor.
+ * and output layout as in rqrcp_factor; the rank guard uses 10*sqrt(max(m,n))*2^-24 in place
+ * of 10*max(m,n)*2^-53 (about ten times the rounding noise of an FP32 sketch column).
  */
 int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
                        uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
@@ -189,6 +190,28 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
                          int64_t ldo, double* B, int64_t ldb, void* stream);
 
 /*
+ * Batched randomized QRCP of many independent FP32 matrices of uneven shapes in ONE persistent
+ * launch (the paper factors one matrix at a time; batching is the GPU form of running Alg. 2 on
+ * many small problems).  `descs` is a device array of `count` descriptors, 72 bytes each, with
+ * this layout (8-byte aligned, in order): float* A, int32_t* jpvt (n), double* tau (k),
+ * int64_t* rank (1), int64_t m, int64_t n, int64_t k, int64_t lda, int32_t b, int32_t pad.
+ * Every matrix needs 1 <= k <= min(m,n) <= max(m_max, n_max), m <= m_max, n <= n_max,
+ * 1 <= b <= b_max <= 64 (b is per matrix, e.g. from the autotuner).  `order` (device, count
+ * ints) is the processing order (largest first balances best); one block per SM takes the next
+ * matrix from an atomic counter and factors it alone.  All matrices share one FP32 sketching
+ * matrix Omega (l_max x m_max, l_max = b_max + p, drawn from `seed` as rqrcp_generate_omega_f32);
+ * matrix i uses its leading (b_i + p) x m_i block.  Per-matrix results as rqrcp_factor_mixed;
+ * rank is -1 when the sketch of that matrix is not finite.  The call is two kernels and a
+ * memset on `stream` and allocates nothing (graph-capturable).  `work` needs
+ * rqrcp_batched_workspace_size(m_max, n_max, b_max, p) bytes.  Limits: SW * m_max floats
+ * (SW = 8) and n_max doubles must fit in one block's shared memory (m_max <= ~5000 for
+ * n_max = 2048), else RQRCP_ERR_UNSUPPORTED.
+ */
+size_t rqrcp_batched_workspace_size(int64_t m_max, int64_t n_max, int64_t b_max, int64_t p);
+int rqrcp_factor_batched(int64_t count, const void* descs, const int* order, int64_t m_max, int64_t n_max,
+                         int64_t b_max, int64_t p, uint64_t seed, void* work, size_t work_bytes, void* stream);
+
+/*
  * Kernel-level timing for measurement (not part of the method).  Between
  * rqrcp_profile_begin and rqrcp_profile_end, every kernel the library enqueues is
  * bracketed by a pair of CUDA events on its stream, and the algorithmic work of the
@@ -198,7 +221,7 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  * launches[c], the summed event time ms[c], flops[c] and bytes[c] (any pointer may be
  * NULL).  Host-side state is global to the process; not thread-safe.
  */
-#define RQRCP_PROFILE_CLASSES 13
+#define RQRCP_PROFILE_CLASSES 14
 int rqrcp_profile_begin(void);
 int rqrcp_profile_end(int nmax, int64_t* launches, double* ms, double* flops, double* bytes);
 const char* rqrcp_profile_class_name(int cls);

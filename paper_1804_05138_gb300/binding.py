@@ -33,8 +33,9 @@ ABI_SYMBOLS = (
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
     "rqrcp_backward_f32", "rqrcp_reorth_workspace_size", "rqrcp_lowrank_reorth",
+    "rqrcp_batched_workspace_size", "rqrcp_factor_batched",
 )
-RQRCP_PROFILE_CLASSES = 13
+RQRCP_PROFILE_CLASSES = 14
 
 _lock = threading.Lock()
 _lib = None
@@ -82,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  _sz, _vp]),
             "rqrcp_backward_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
             "rqrcp_reorth_workspace_size": (_sz, [_i64, _i64, _i64]),
+            "rqrcp_batched_workspace_size": (_sz, [_i64, _i64, _i64, _i64]),
+            "rqrcp_factor_batched": (ctypes.c_int, [_i64, _vp, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _sz, _vp]),
             "rqrcp_lowrank_reorth": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64,
                                                     ctypes.c_double, _vp, _vp, _sz, _vp]),
             "rqrcp_backward": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64,
@@ -212,6 +215,68 @@ def rqrcp_lowrank_reorth(Afact, k, tau, Q1, R, tol, orth, work, stream=None) -> 
     m, n = Afact.shape
     return load().rqrcp_lowrank_reorth(m, n, k, _ptr(Afact), _ld(Afact), _ptr(tau), _ptr(Q1), _ld(Q1), _ptr(R),
                                        _ld(R), float(tol), _ptr(orth), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_batched_workspace_size(m_max, n_max, b_max, p) -> int:
+    return int(load().rqrcp_batched_workspace_size(m_max, n_max, b_max, p))
+
+
+def rqrcp_factor_batched(count, descs, order, m_max, n_max, b_max, p, seed, work, stream=None) -> int:
+    """descs: device uint8 tensor of count x 72-byte descriptors; order: device int32 tensor."""
+    return load().rqrcp_factor_batched(count, _ptr(descs), _ptr(order), m_max, n_max, b_max, p, seed, _ptr(work),
+                                       work.numel(), _stream(stream))
+
+
+BATCH_DESC_BYTES = 72
+
+
+def batch_descriptors(mats, jpvts, taus, ranks, ks, bs):
+    """Pack the 72-byte descriptors (layout of include/rqrcp.h) into a host uint8 array."""
+    import numpy as np
+    dt = np.dtype([("A", "<u8"), ("jpvt", "<u8"), ("tau", "<u8"), ("rank", "<u8"), ("m", "<i8"), ("n", "<i8"),
+                   ("k", "<i8"), ("lda", "<i8"), ("b", "<i4"), ("pad", "<i4")])
+    assert dt.itemsize == BATCH_DESC_BYTES
+    rec = np.zeros(len(mats), dtype=dt)
+    for i, (A, jp, tu, rk, k, b) in enumerate(zip(mats, jpvts, taus, ranks, ks, bs)):
+        rec[i] = (A.data_ptr(), jp.data_ptr(), tu.data_ptr(), rk.data_ptr(), A.shape[0], A.shape[1], k, _ld(A), b, 0)
+    return rec.view(np.uint8)
+
+
+def batch_cost(m, n, k, b, p):
+    """Counted flops of one RQRCP (sketch + Householder QR to rank k): the order key."""
+    l = b + p
+    return 2.0 * l * m * n + 4.0 * m * n * k - 2.0 * (m + n) * k * k + 4.0 * k ** 3 / 3.0
+
+
+class Batch:
+    """Prepared batched call: descriptors, order and workspace on the device; `run()` enqueues it."""
+
+    def __init__(self, mats, ks, bs, p=8, seed=0):
+        import numpy as np
+        import torch
+        self.mats = [colmajor(A) for A in mats]
+        dev = self.mats[0].device
+        self.ks, self.bs, self.p, self.seed = list(ks), list(bs), p, seed
+        self.jpvts = [torch.empty(A.shape[1], dtype=torch.int32, device=dev) for A in self.mats]
+        self.taus = [torch.empty(k, dtype=torch.float64, device=dev) for k in self.ks]
+        self.ranks = torch.zeros(len(self.mats), dtype=torch.int64, device=dev)
+        rank_views = [self.ranks[i:i + 1] for i in range(len(self.mats))]
+        host = batch_descriptors(self.mats, self.jpvts, self.taus, rank_views, self.ks, self.bs)
+        self.descs = torch.from_numpy(host.copy()).to(dev)
+        cost = [batch_cost(A.shape[0], A.shape[1], k, b, p) for A, k, b in zip(self.mats, self.ks, self.bs)]
+        self.order = torch.from_numpy(np.argsort(-np.asarray(cost), kind="stable").astype(np.int32)).to(dev)
+        self.m_max = max(A.shape[0] for A in self.mats)
+        self.n_max = max(A.shape[1] for A in self.mats)
+        self.b_max = max(self.bs)
+        need = rqrcp_batched_workspace_size(self.m_max, self.n_max, self.b_max, p)
+        if need == 0:
+            raise ValueError("invalid batch limits")
+        self.work = workspace(need, dev)
+        self.flops = float(sum(cost))
+
+    def run(self, stream=None) -> int:
+        return rqrcp_factor_batched(len(self.mats), self.descs, self.order, self.m_max, self.n_max, self.b_max,
+                                    self.p, self.seed, self.work, stream)
 
 
 def rqrcp_backward_workspace_size(m, n, k, precision=RQRCP_PREC_FP64) -> int:

@@ -1,0 +1,697 @@
+// batched.cu -- many independent randomized QRCPs (Alg. 2) of uneven shapes in one persistent
+// launch.  Every block (one per SM) repeatedly takes the next matrix from a work queue (an
+// atomic counter over a caller-given order, largest first) and factors that matrix alone,
+// with block-level synchronisation only:
+//   sketch      B = Omega(0:l, 0:m) A, tiled FP32 contraction, B kept row-major (ld = n);
+//   pivots      Alg. 1 on B with physical column swaps (ties to the smallest position), norms
+//               of rows t..l-1 recomputed while the reflector is applied, FP64 reflector;
+//   panel       left-looking in sub-panels of 8 columns held in shared memory, every
+//               reflector (norm, beta, tau) formed in FP64;
+//   update      W = V^T [V C] (Gram and V^T C in one pass), T (xLARFT order, FP64),
+//               Y = T^T W, C -= V Y, tiled FP32 with compensated accumulation;
+//   Eq. (4)     Omega_hat_11 = R_hat11 R11^{-1} row by row, B(0:bb, trail) -= Omega_hat_11 R12.
+// FP32 storage (the mixed form); the rank guard of the single-matrix path applies per matrix.
+#include "internal.cuh"
+
+namespace rq {
+
+struct BatchDesc {
+    float* A;
+    int32_t* jpvt;
+    double* tau;
+    long long* rank;  // pivots before the rank guard fired; -1 when the sketch is not finite
+    long long m, n, k, lda;
+    int b, pad;
+};
+
+namespace {
+
+constexpr int BT = 512;          // threads per block
+constexpr int NW = BT / 32;      // warps
+constexpr int SW = 8;            // sub-panel width of the panel factorization
+constexpr int kTile = 64;        // GEMM tile edge
+constexpr int kKs = 32;          // K slice of the TN contraction
+constexpr int kKu = 64;          // largest K of the update contraction (b <= 64)
+constexpr int kLdT = kTile + 1;  // padded shared-memory tile stride
+
+struct Smem {
+    float* S;       // SW x m_max sub-panel
+    double* nu;     // n_max sketch norms
+    double* Tm;     // b_max x b_max: T, then Omega_hat_11
+    float* Xs;      // kKu x kLdT GEMM tile
+    float* Cs;      // kKu x kLdT GEMM tile
+    float* vs;      // l_max reflector of the pivot search
+    double* red;    // NW x SW block-reduction scratch
+    double* sc;     // scalars: tau, beta, scal, guard, ...
+    int* piv;       // b_max pivot targets
+    long long* lpos;
+};
+
+__device__ __forceinline__ float vmask_f(float stored, long long q, long long r)
+{
+    return q > r ? stored : (q == r ? 1.f : 0.f);
+}
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
+{
+    const float t = hi + x;
+    const float z = t - hi;
+    lo += (hi - (t - z)) + (x - z);
+    hi = t;
+}
+
+// Sum of NV doubles over the block; result in out[0..NV) for every thread (fixed order).
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* red, double* out)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[w * NV + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int ww = 0; ww < NW; ++ww) s += red[ww * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Out(M x N) = X^T C; X is K x M (ldx), C is K x N (ldc), column-major.  maskX / maskC: unit-
+// lower reflector structure of X / of the first maskC columns of C.  out_rowmajor stores
+// Out(r, c) at r*ldo + c, else at c*ldo + r.  K is consumed in 32-deep slices; the next slice
+// is fetched into registers while the current one is multiplied out of shared memory.  Two
+// slices (64 terms) are summed in FP32 and folded into a compensated (TwoSum) total.
+__device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
+                            long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
+                            const Smem& sm)
+{
+    constexpr int PER = (kKs * kTile) / BT;  // elements per thread per operand and slice
+    const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;  // tn in 0..31
+    for (long long m0 = 0; m0 < M; m0 += kTile)
+        for (long long n0 = 0; n0 < N; n0 += kTile) {
+            float acc[4][2], hi[4][2], lo[4][2], xr[PER], cr[PER];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
+            auto fetch = [&](long long k0) {
+#pragma unroll
+                for (int it = 0; it < PER; ++it) {
+                    const int e = tid + it * BT, kk = e & (kKs - 1), mm = e / kKs;
+                    const long long q = k0 + kk, r = m0 + mm, c = n0 + mm;
+                    float xv = 0.f, cv = 0.f;
+                    if (q < K && r < M) {
+                        xv = X[r * ldx + q];
+                        if (maskX) xv = vmask_f(xv, q, r);
+                    }
+                    if (q < K && c < N) {
+                        cv = C[c * ldc + q];
+                        if (c < maskC) cv = vmask_f(cv, q, c);
+                    }
+                    xr[it] = xv;
+                    cr[it] = cv;
+                }
+            };
+            fetch(0);
+            int slice = 0;
+            for (long long k0 = 0; k0 < K; k0 += kKs) {
+#pragma unroll
+                for (int it = 0; it < PER; ++it) {
+                    const int e = tid + it * BT, kk = e & (kKs - 1), mm = e / kKs;
+                    sm.Xs[kk * kLdT + mm] = xr[it];
+                    sm.Cs[kk * kLdT + mm] = cr[it];
+                }
+                __syncthreads();
+                if (k0 + kKs < K) fetch(k0 + kKs);
+#pragma unroll 8
+                for (int kk = 0; kk < kKs; ++kk) {
+                    float xa[4], cb[2];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xa[a] = sm.Xs[kk * kLdT + tm + 16 * a];
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) cb[b] = sm.Cs[kk * kLdT + tn + 32 * b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(xa[a], cb[b], acc[a][b]);
+                }
+                __syncthreads();
+                if (++slice == 2) {
+                    slice = 0;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            two_sum_acc(hi[a][b], lo[a][b], acc[a][b]);
+                            acc[a][b] = 0.f;
+                        }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    two_sum_acc(hi[a][b], lo[a][b], acc[a][b]);
+                    const long long r = m0 + tm + 16 * a, c = n0 + tn + 32 * b;
+                    if (r < M && c < N) {
+                        const float v = hi[a][b] + lo[a][b];
+                        if (out_rowmajor) Out[r * ldo + c] = v;
+                        else Out[c * ldo + r] = v;
+                    }
+                }
+        }
+}
+
+// C(M x N) -= V(M x K) Y(K x N), column-major, K <= 64; V with the optional unit-lower
+// structure.  Each 64 x 64 tile issues all of its loads (V and Y tiles to shared memory, the
+// C tile to registers) in one batch, then multiplies and writes C back.
+__device__ void blk_gemm_update(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
+                                long long ldy, long long M, long long N, long long K, const Smem& sm)
+{
+    const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
+    for (long long r0 = 0; r0 < M; r0 += kTile)
+        for (long long c0 = 0; c0 < N; c0 += kTile) {
+            float cv[4][2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
+                    cv[a][b] = (r < M && c < N) ? C[c * ldc + r] : 0.f;
+                }
+#pragma unroll
+            for (int it = 0; it < (kKu * kTile) / BT; ++it) {
+                const int e = tid + it * BT;
+                const int rr = e & (kTile - 1), kk = e / kTile;  // V tile, rows fastest
+                const long long r = r0 + rr;
+                float vv = 0.f;
+                if (r < M && kk < K) {
+                    vv = V[(long long)kk * ldv + r];
+                    if (maskV) vv = vmask_f(vv, r, kk);
+                }
+                sm.Xs[kk * kLdT + rr] = vv;
+                const int kk2 = e & (kKu - 1), cc = e / kKu;  // Y tile, K fastest
+                const long long c = c0 + cc;
+                sm.Cs[kk2 * kLdT + cc] = (kk2 < K && c < N) ? Y[c * ldy + kk2] : 0.f;
+            }
+            __syncthreads();
+            float acc[4][2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.f;
+            for (int kk = 0; kk < K; ++kk) {
+                float va[4], yb[2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) va[a] = sm.Xs[kk * kLdT + tm + 16 * a];
+#pragma unroll
+                for (int b = 0; b < 2; ++b) yb[b] = sm.Cs[kk * kLdT + tn + 32 * b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(va[a], yb[b], acc[a][b]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
+                    if (r < M && c < N) C[c * ldc + r] = cv[a][b] - acc[a][b];
+                }
+        }
+}
+
+// argmax over (value, position), ties to the smaller position; result broadcast via sm.sc/lpos.
+__device__ void blk_argmax(double v, long long p, const Smem& sm, double& bv, long long& bp)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ov > v || (ov == v && op < p)) { v = ov; p = op; }
+    }
+    if (lane == 0) { sm.red[w] = v; sm.lpos[w] = p; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double vb = sm.red[0];
+        long long pb = sm.lpos[0];
+        for (int ww = 1; ww < NW; ++ww)
+            if (sm.red[ww] > vb || (sm.red[ww] == vb && sm.lpos[ww] < pb)) { vb = sm.red[ww]; pb = sm.lpos[ww]; }
+        sm.sc[8] = vb;
+        sm.lpos[NW] = pb;
+    }
+    __syncthreads();
+    bv = sm.sc[8];
+    bp = sm.lpos[NW];
+    __syncthreads();
+}
+
+// Partial QRCP (Alg. 1) on the row-major sketch B (l x n, ld n), trailing columns i..n-1, bb
+// steps.  Returns the number of pivots taken (< bb when the rank guard fires).
+__device__ int blk_pivot(float* B, long long n, int l, long long i, int bb, int32_t* jpvt, double guard,
+                         const Smem& sm)
+{
+    const int tid = threadIdx.x;
+    for (long long c = i + tid; c < n; c += BT) {
+        double s = 0.0;
+        for (int r = 0; r < l; ++r) {
+            const double x = B[(long long)r * n + c];
+            s += x * x;
+        }
+        sm.nu[c] = s;
+    }
+    __syncthreads();
+    for (int t = 0; t < bb; ++t) {
+        const long long c0 = i + t;
+        double mv = -1.0;
+        long long mp = 0x7fffffffffffffffLL;
+        for (long long c = c0 + tid; c < n; c += BT)
+            if (sm.nu[c] > mv || (sm.nu[c] == mv && c < mp)) { mv = sm.nu[c]; mp = c; }
+        double bv;
+        long long j;
+        blk_argmax(mv, mp, sm, bv, j);
+        if (!(bv > guard)) return t;
+        if (tid == 0) sm.piv[t] = (int)j;
+        if (j != c0) {
+            for (int r = tid; r < l; r += BT) {
+                const float a = B[(long long)r * n + c0];
+                B[(long long)r * n + c0] = B[(long long)r * n + j];
+                B[(long long)r * n + j] = a;
+            }
+            if (tid == 0) {
+                const double tn = sm.nu[c0];
+                sm.nu[c0] = sm.nu[j];
+                sm.nu[j] = tn;
+                const int32_t tj = jpvt[c0];
+                jpvt[c0] = jpvt[j];
+                jpvt[j] = tj;
+            }
+        }
+        __syncthreads();
+        // reflector of B(t:l, c0), FP64, xLARFG convention
+        if (tid < 32) {
+            double ss = 0.0;
+            for (int r = t + 1 + tid; r < l; r += 32) {
+                const double x = B[(long long)r * n + c0];
+                ss += x * x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            if (tid == 0) {
+                const double alpha = B[(long long)t * n + c0];
+                double tau = 0.0, beta = alpha, scal = 0.0;
+                if (ss != 0.0) {
+                    const double nrm = sqrt(alpha * alpha + ss);
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scal = 1.0 / (alpha - beta);
+                }
+                sm.sc[0] = tau;
+                sm.sc[1] = beta;
+                sm.sc[2] = scal;
+            }
+        }
+        __syncthreads();
+        const double tau = sm.sc[0];
+        for (int r = t + 1 + tid; r < l; r += BT) sm.vs[r] = (float)((double)B[(long long)r * n + c0] * sm.sc[2]);
+        if (tid == 0) sm.vs[t] = 1.f;
+        __syncthreads();
+        for (int r = t + tid; r < l; r += BT) B[(long long)r * n + c0] = (r == t) ? (float)sm.sc[1] : 0.f;
+        const float tauf = (float)tau;
+        for (long long c = c0 + 1 + tid; c < n; c += BT) {
+            float w = 0.f;
+            if (tau != 0.0)
+                for (int r = t; r < l; ++r) w = fmaf(sm.vs[r], B[(long long)r * n + c], w);
+            const float wt = w * tauf;
+            double nu = 0.0;
+            for (int r = t; r < l; ++r) {
+                float x = B[(long long)r * n + c];
+                if (tau != 0.0) {
+                    x = fmaf(-wt, sm.vs[r], x);
+                    B[(long long)r * n + c] = x;
+                }
+                if (r > t) nu += (double)x * (double)x;
+            }
+            sm.nu[c] = nu;
+        }
+        __syncthreads();
+    }
+    return bb;
+}
+
+// Householder QR of the panel P (m1 x bb, ldp) in place: left-looking over sub-panels of SW
+// columns held in shared memory; tau (FP64) out.
+__device__ void blk_panel(float* P, long long ldp, long long m1, int bb, double* tau, const Smem& sm)
+{
+    const int tid = threadIdx.x;
+    for (int s0 = 0; s0 < bb; s0 += SW) {
+        const int sw = (bb - s0) < SW ? (bb - s0) : SW;
+        for (int cc = 0; cc < sw; ++cc)
+            for (long long r = tid; r < m1; r += BT) sm.S[cc * m1 + r] = P[(s0 + cc) * ldp + r];
+        __syncthreads();
+        // earlier reflectors of this panel, in order
+        for (int h = 0; h < s0; ++h) {
+            double v[SW];
+#pragma unroll
+            for (int cc = 0; cc < SW; ++cc) v[cc] = 0.0;
+            const float* vh = P + (long long)h * ldp;
+            for (long long r = h + tid; r < m1; r += BT) {
+                const float x = (r == h) ? 1.f : vh[r];
+#pragma unroll
+                for (int cc = 0; cc < SW; ++cc)
+                    if (cc < sw) v[cc] += (double)(x * sm.S[cc * m1 + r]);
+            }
+            block_sum<SW>(v, sm.red, sm.sc + 16);
+            const double th = tau[h];
+            for (long long r = h + tid; r < m1; r += BT) {
+                const float x = (r == h) ? 1.f : vh[r];
+                for (int cc = 0; cc < sw; ++cc) sm.S[cc * m1 + r] -= (float)(th * sm.sc[16 + cc]) * x;
+            }
+            __syncthreads();
+        }
+        // factor the sub-panel columns
+        for (int jj = 0; jj < sw; ++jj) {
+            const long long j = s0 + jj;  // panel row/column index of the diagonal
+            double v[SW];
+#pragma unroll
+            for (int cc = 0; cc < SW; ++cc) v[cc] = 0.0;
+            for (long long r = j + 1 + tid; r < m1; r += BT) {
+                const float x = sm.S[jj * m1 + r];
+#pragma unroll
+                for (int cc = 0; cc < SW; ++cc)
+                    if (cc >= jj && cc < sw) v[cc] += (double)(x * sm.S[cc * m1 + r]);
+            }
+            block_sum<SW>(v, sm.red, sm.sc + 16);
+            if (tid == 0) {
+                const double alpha = sm.S[jj * m1 + j];
+                const double ss = sm.sc[16 + jj];
+                double tj = 0.0, beta = alpha, scal = 0.0;
+                if (ss != 0.0) {
+                    const double nrm = sqrt(alpha * alpha + ss);
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tj = (beta - alpha) / beta;
+                    scal = 1.0 / (alpha - beta);
+                }
+                sm.sc[0] = tj;
+                sm.sc[1] = beta;
+                sm.sc[2] = scal;
+                tau[j] = tj;
+                for (int cc = jj + 1; cc < sw; ++cc)
+                    sm.sc[24 + cc] = tj * ((double)sm.S[cc * m1 + j] + scal * sm.sc[16 + cc]);
+            }
+            __syncthreads();
+            const double tj = sm.sc[0], scal = sm.sc[2];
+            if (tj != 0.0) {
+                for (long long r = j + 1 + tid; r < m1; r += BT) {
+                    const float vr = (float)((double)sm.S[jj * m1 + r] * scal);
+                    sm.S[jj * m1 + r] = vr;
+                    for (int cc = jj + 1; cc < sw; ++cc) sm.S[cc * m1 + r] -= (float)sm.sc[24 + cc] * vr;
+                }
+                if (tid == 0)
+                    for (int cc = jj + 1; cc < sw; ++cc) sm.S[cc * m1 + j] -= (float)sm.sc[24 + cc];
+            }
+            __syncthreads();
+            if (tid == 0) sm.S[jj * m1 + j] = (float)sm.sc[1];
+            __syncthreads();
+        }
+        for (int cc = 0; cc < sw; ++cc)
+            for (long long r = tid; r < m1; r += BT) P[(s0 + cc) * ldp + r] = sm.S[cc * m1 + r];
+        __syncthreads();
+    }
+}
+
+// T (bb x bb, FP64, column-major in sm.Tm) from the Gram G(q, j) = W[j*bb + q] and tau.
+__device__ void blk_tform(const float* W, int bb, const double* tau, const Smem& sm)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < bb * bb; e += BT) sm.Tm[e] = 0.0;
+    __syncthreads();
+    for (int r = w; r < bb; r += NW) {
+        if (lane == 0) sm.Tm[r * bb + r] = tau[r];
+        __syncwarp();
+        for (int j = r + 1; j < bb; ++j) {
+            double s = 0.0;
+            for (int q = r + lane; q < j; q += 32) s += sm.Tm[q * bb + r] * (double)W[(long long)j * bb + q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) sm.Tm[j * bb + r] = -tau[j] * s;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// Omega_hat_11 (bb x bb, FP64, in sm.Tm) from R_hat11 = B(0:bb, i:i+bb) (row-major, ld n) and
+// R11 = A(i:i+bb, i:i+bb): row recurrences, one warp per row.
+__device__ void blk_bsolve(const float* B, long long n, const float* A, long long lda, long long i, int bb, const Smem& sm)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < bb * bb; e += BT) sm.Tm[e] = 0.0;
+    __syncthreads();
+    for (int r = w; r < bb; r += NW) {
+        for (int j = r; j < bb; ++j) {
+            double s = 0.0;
+            for (int q = r + lane; q < j; q += 32) s += sm.Tm[q * bb + r] * (double)A[(i + j) * lda + i + q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                const double rjj = (double)A[(i + j) * lda + i + j];
+                sm.Tm[j * bb + r] = (rjj == 0.0) ? 0.0 : ((double)B[(long long)r * n + i + j] - s) / rjj;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, int p, float* Bw, float* Ww, float* Yw,
+                           const Smem& sm)
+{
+    const int tid = threadIdx.x;
+    const long long m = d.m, n = d.n, k = d.k, lda = d.lda;
+    const int b = d.b;
+    const int l = b + p;
+    float* A = d.A;
+    for (long long c = tid; c < n; c += BT) d.jpvt[c] = (int32_t)c;
+    // sketch B = Omega(0:l, 0:m) A, row-major l x n
+    blk_gemm_tn(Om, ldo, 0, A, lda, 0, l, n, m, Bw, n, 1, sm);
+    __syncthreads();
+    // largest initial sketch column norm^2 and finiteness
+    double mx = 0.0;
+    bool finite = true;
+    for (long long c = tid; c < n; c += BT) {
+        double s = 0.0;
+        for (int r = 0; r < l; ++r) {
+            const double x = Bw[(long long)r * n + c];
+            s += x * x;
+        }
+        finite = finite && isfinite(s);
+        mx = fmax(mx, s);
+    }
+    const int all_finite = __syncthreads_and(finite ? 1 : 0);
+    double bv;
+    long long bp;
+    blk_argmax(mx, 0, sm, bv, bp);
+    if (!all_finite) {
+        if (tid == 0) *d.rank = -1;
+        __syncthreads();
+        return;
+    }
+    const double gtol = 10.0 * sqrt((double)(m > n ? m : n)) * 5.9604644775390625e-08;
+    const double guard = gtol * gtol * bv;
+    bool pivoting = true;
+    long long rank = k;
+    for (long long i = 0; i < k; i += b) {
+        const int bb = (int)(b < k - i ? b : k - i);
+        int steps = 0;
+        if (pivoting) {
+            steps = blk_pivot(Bw, n, l, i, bb, d.jpvt, guard, sm);
+            if (steps < bb) {
+                pivoting = false;
+                rank = i + steps;
+            }
+        }
+        // swap the chosen columns of A into place, in pivot order
+        for (int t = 0; t < steps; ++t) {
+            const long long a = i + t, j = sm.piv[t];
+            if (j != a)
+                for (long long r = tid; r < m; r += BT) {
+                    const float x = A[a * lda + r];
+                    A[a * lda + r] = A[j * lda + r];
+                    A[j * lda + r] = x;
+                }
+            __syncthreads();
+        }
+        float* Vp = A + i * lda + i;
+        const long long m1 = m - i;
+        blk_panel(Vp, lda, m1, bb, d.tau + i, sm);
+        const long long nt = n - i - bb;
+        if (nt <= 0) continue;
+        // W = V^T [V C] (bb x (n-i), column-major ld bb), T, Y = T^T W(:, bb:), C -= V Y
+        blk_gemm_tn(Vp, lda, 1, Vp, lda, bb, bb, n - i, m1, Ww, bb, 0, sm);
+        __syncthreads();
+        blk_tform(Ww, bb, d.tau + i, sm);
+        for (long long e = tid; e < (long long)bb * nt; e += BT) {
+            const int r = (int)(e % bb);
+            const long long c = e / bb;
+            double s = 0.0;
+            for (int q = 0; q <= r; ++q) s += sm.Tm[r * bb + q] * (double)Ww[(bb + c) * bb + q];
+            Yw[c * bb + r] = (float)s;
+        }
+        __syncthreads();
+        blk_gemm_update(Vp + (long long)bb * lda, lda, Vp, lda, 1, Yw, bb, m1, nt, bb, sm);
+        __syncthreads();
+        if (pivoting && i + bb < k) {
+            blk_bsolve(Bw, n, A, lda, i, bb, sm);
+            for (long long c = i + bb + tid; c < n; c += BT)
+                for (int r = 0; r < bb; ++r) {
+                    double s = 0.0;
+                    for (int q = r; q < bb; ++q) s += sm.Tm[q * bb + r] * (double)A[c * lda + i + q];
+                    Bw[(long long)r * n + c] -= (float)s;
+                }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) *d.rank = rank;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restrict__ descs, const int* __restrict__ order,
+                                                        int count, const float* __restrict__ Om, long long ldo, int p,
+                                                        long long m_max, long long n_max, int b_max, char* ws,
+                                                        size_t ws_per_block, int* counter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem sm;
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        unsigned char* ptr = smraw + off;
+        off = (off + bytes + 15) & ~(size_t)15;
+        return ptr;
+    };
+    const int l_max = b_max + p;
+    sm.S = reinterpret_cast<float*>(carve(sizeof(float) * SW * (size_t)m_max));
+    sm.nu = reinterpret_cast<double*>(carve(sizeof(double) * (size_t)n_max));
+    sm.Tm = reinterpret_cast<double*>(carve(sizeof(double) * (size_t)b_max * b_max));
+    sm.Xs = reinterpret_cast<float*>(carve(sizeof(float) * kKu * kLdT));
+    sm.Cs = reinterpret_cast<float*>(carve(sizeof(float) * kKu * kLdT));
+    sm.vs = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)l_max));
+    sm.red = reinterpret_cast<double*>(carve(sizeof(double) * NW * SW));
+    sm.sc = reinterpret_cast<double*>(carve(sizeof(double) * 40));
+    sm.piv = reinterpret_cast<int*>(carve(sizeof(int) * (size_t)b_max));
+    sm.lpos = reinterpret_cast<long long*>(carve(sizeof(long long) * (NW + 1)));
+
+    char* mine = ws + (size_t)blockIdx.x * ws_per_block;
+    float* Bw = reinterpret_cast<float*>(mine);
+    float* Ww = Bw + (size_t)l_max * n_max;
+    float* Yw = Ww + (size_t)b_max * (n_max + b_max);
+    __shared__ int s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = s_next;
+        __syncthreads();
+        if (idx >= count) break;
+        const BatchDesc d = descs[order[idx]];
+        factor_one(d, Om, ldo, p, Bw, Ww, Yw, sm);
+    }
+}
+
+size_t batched_smem_bytes(long long m_max, long long n_max, int b_max, int p)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~(size_t)15; };
+    take(sizeof(float) * SW * (size_t)m_max);
+    take(sizeof(double) * (size_t)n_max);
+    take(sizeof(double) * (size_t)b_max * b_max);
+    take(sizeof(float) * kKu * kLdT);
+    take(sizeof(float) * kKu * kLdT);
+    take(sizeof(float) * (size_t)(b_max + p));
+    take(sizeof(double) * NW * SW);
+    take(sizeof(double) * 40);
+    take(sizeof(int) * (size_t)b_max);
+    take(sizeof(long long) * (NW + 1));
+    return off;
+}
+
+size_t batched_ws_per_block(long long n_max, int b_max, int p)
+{
+    const size_t floats = (size_t)(b_max + p) * n_max + (size_t)b_max * (n_max + b_max) + (size_t)b_max * n_max;
+    return ((floats * sizeof(float)) + 255) & ~(size_t)255;
+}
+
+}  // namespace
+}  // namespace rq
+
+using namespace rq;
+
+extern "C" {
+
+__attribute__((visibility("default"))) size_t rqrcp_batched_workspace_size(int64_t m_max, int64_t n_max, int64_t b_max,
+                                                                           int64_t p)
+{
+    if (m_max < 1 || n_max < 1 || b_max < 1 || b_max > 64 || p < 0 || b_max + p > 1024) return 0;
+    const int blocks = dev_info().sms;
+    // Omega (l_max x m_max) + counter + per-block scratch
+    size_t off = ((size_t)(b_max + p) * m_max * sizeof(float) + 255) & ~(size_t)255;
+    off += 256;
+    off += (size_t)blocks * batched_ws_per_block(n_max, (int)b_max, (int)p);
+    return off;
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_batched(int64_t count, const void* descs, const int* order,
+                                                                int64_t m_max, int64_t n_max, int64_t b_max,
+                                                                int64_t p, uint64_t seed, void* work,
+                                                                size_t work_bytes, void* stream)
+{
+    if (count < 0) return -1;
+    if (count > 0 && descs == nullptr) return -2;
+    if (count > 0 && order == nullptr) return -3;
+    if (m_max < 1) return -4;
+    if (n_max < 1) return -5;
+    if (b_max < 1 || b_max > 64) return -6;
+    if (p < 0 || b_max + p > 1024) return -7;
+    const size_t need = rqrcp_batched_workspace_size(m_max, n_max, b_max, p);
+    if (work == nullptr || (reinterpret_cast<uintptr_t>(work) & 255) != 0 || work_bytes < need)
+        return RQRCP_ERR_WORKSPACE;
+    const size_t smem = batched_smem_bytes(m_max, n_max, (int)b_max, (int)p);
+    if (smem > (size_t)dev_info().max_smem_optin - 1024) return RQRCP_ERR_UNSUPPORTED;
+    if (count == 0) return RQRCP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(work);
+    float* Om = reinterpret_cast<float*>(w);
+    size_t off = ((size_t)(b_max + p) * m_max * sizeof(float) + 255) & ~(size_t)255;
+    int* counter = reinterpret_cast<int*>(w + off);
+    off += 256;
+    char* scratch = w + off;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (allow_max_dynamic_smem(batched_kernel) != cudaSuccess) {
+            cudaGetLastError();
+            return RQRCP_ERR_CUDA;
+        }
+        attr_set = true;
+    }
+    const bool prof = prof_on();
+    if (prof) prof_begin(K_BATCHED, s);
+    if (launch_omega<float>(b_max + p, m_max, seed, Om, m_max, s) != cudaSuccess) return RQRCP_ERR_CUDA;
+    if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return RQRCP_ERR_CUDA;
+    }
+    batched_kernel<<<dev_info().sms, BT, smem, s>>>(static_cast<const BatchDesc*>(descs), order, (int)count, Om,
+                                                     (long long)m_max, (int)p, (long long)m_max, (long long)n_max,
+                                                     (int)b_max, scratch, batched_ws_per_block(n_max, (int)b_max, (int)p),
+                                                     counter);
+    if (cudaGetLastError() != cudaSuccess) return RQRCP_ERR_CUDA;
+    if (prof) prof_end(K_BATCHED, 0.0, 0.0, s);
+    return RQRCP_OK;
+}
+
+}  // extern "C"

@@ -169,7 +169,7 @@ cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i
 // Opt-in kernel timing (prof.cu): classes in the order of rqrcp_profile_class_name.
 enum ProfClass {
     K_OMEGA = 0, K_SKETCH_GEMM, K_SKETCH_REDUCE, K_PIVOT, K_SWAP, K_PANEL,
-    K_WY_GEMM, K_TFORM, K_REDUCE_Y, K_WY_UPDATE, K_BUPDATE, K_LOWRANK_MISC, K_BACKWARD
+    K_WY_GEMM, K_TFORM, K_REDUCE_Y, K_WY_UPDATE, K_BUPDATE, K_LOWRANK_MISC, K_BACKWARD, K_BATCHED
 };
 bool prof_on();
 void prof_begin(int cls, cudaStream_t s);

@@ -33,7 +33,7 @@ cudaEvent_t take_event()
 
 const char* const kNames[RQRCP_PROFILE_CLASSES] = {
     "omega", "sketch_gemm", "sketch_reduce", "pivot", "swap", "panel",
-    "wy_gemm_tn", "tform", "reduce_y", "wy_update", "bupdate", "lowrank_misc", "backward",
+    "wy_gemm_tn", "tform", "reduce_y", "wy_update", "bupdate", "lowrank_misc", "backward", "batched",
 };
 
 }  // namespace

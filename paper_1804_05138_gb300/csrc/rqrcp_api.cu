@@ -10,6 +10,7 @@
 //   reduce_y: Y = T^T V^T A(i:m, i+bb:n)
 //   update  : A(i:m, i+bb:n) -= V Y                         (rows i..i+bb-1 become R12)
 //   bupdate : Eq. (4) on the top bb rows of the trailing sketch
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -165,7 +166,10 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         RQ_LAUNCH(K_SKETCH_REDUCE, 0, (double)ns * l * n * 8 + (double)l * n * es,
                   launch_sketch_reduce<T>(P, ns, l, n, B, l, st, s));
     }
-    const double gtol = 10.0 * (double)(m > n ? m : n) * Prec<T>::unit_roundoff;
+    // guard tolerance: 10 max(m,n) u for FP64 (the oracle's reading); FP32 storage uses
+    // 10 sqrt(max(m,n)) u, about ten times the rounding noise of an FP32 sketch column
+    const double mn = (double)(m > n ? m : n);
+    const double gtol = 10.0 * (sizeof(T) == 8 ? mn : sqrt(mn)) * Prec<T>::unit_roundoff;
     const double guard_rel2 = gtol * gtol;
     for (int64_t i = 0; i < k; i += b) {
         const int bb = (int)(b < k - i ? b : k - i);
