@@ -12,6 +12,7 @@
 //   bupdate : Eq. (4) on the top bb rows of the trailing sketch
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.cuh"
@@ -35,6 +36,17 @@ const DevInfo& dev_info()
 
 template <typename T>
 cudaError_t launch_lowrank_rk(const T* Af, int64_t ldaf, int64_t k, int64_t n, double* Rk, cudaStream_t s);
+
+// RQRCP_TENSOR_CORES=0 in the environment selects the SIMT contractions for the FP32 form.
+bool tensor_cores_enabled()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("RQRCP_TENSOR_CORES");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
 template <typename T>
 cudaError_t launch_eye(T* Q, int64_t ldq, int64_t m, int64_t k, cudaStream_t s);
 
@@ -160,9 +172,18 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     {
         int ns;
         int64_t kc;
-        choose_split(l, n, m, ns, kc);
-        RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
-                  launch_gemm_tn<T>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s));
+        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() &&
+                        tc_gemm_supported(l, ldo, lda, (const void*)Omega, (const void*)A);
+        if (tc) {
+            kc = tc_kchunk(n, m, ns);
+            RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
+                      launch_gemm_tn_tc((const float*)Omega, ldo, m, l, 0, 0, (const float*)A, lda, m, n, 0, 0, l, n, m,
+                                        kc, P, 0, 0, 1, st, s));
+        } else {
+            choose_split(l, n, m, ns, kc);
+            RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
+                      launch_gemm_tn<T>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s));
+        }
         RQ_LAUNCH(K_SKETCH_REDUCE, 0, (double)ns * l * n * 8 + (double)l * n * es,
                   launch_sketch_reduce<T>(P, ns, l, n, B, l, st, s));
     }
@@ -185,9 +206,18 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         if (nt <= 0) continue;
         int ns;
         int64_t kc;
-        choose_split(bb, n - i, mr, ns, kc);
-        RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
-                  launch_gemm_tn<T>(Vp, lda, Vp, lda, bb, n - i, mr, kc, P, 1, bb, st, s));
+        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && (i % 4) == 0 &&
+                        tc_gemm_supported(bb, lda, lda, (const void*)A, (const void*)A);
+        if (tc) {
+            kc = tc_kchunk(n - i, mr, ns);
+            RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
+                      launch_gemm_tn_tc((const float*)A, lda, m, n, (int)i, (int)i, (const float*)A, lda, m, n, (int)i,
+                                        (int)i, bb, n - i, mr, kc, P, bb, bb, 1, st, s));
+        } else {
+            choose_split(bb, n - i, mr, ns, kc);
+            RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
+                      launch_gemm_tn<T>(Vp, lda, Vp, lda, bb, n - i, mr, kc, P, 1, bb, st, s));
+        }
         RQ_LAUNCH(K_TFORM, (double)bb * bb * bb / 3.0, (double)ns * bb * bb * 8,
                   launch_tform(P, ns, n - i, bb, tau + i, Tm, st, s));
         RQ_LAUNCH(K_REDUCE_Y, (double)bb * bb * nt, ((double)ns + 1.0) * bb * nt * 8,
