@@ -1,21 +1,23 @@
 // gemm_tc.cu -- tensor-core (tcgen05, kind::tf32) form of the split-K contraction
-//   P[sp][c][r] = sum_{q in split sp} X(q, r) C(q, c),  r < M <= 128, c < N,
+//   P[sp][c][r] = sum_{q in split sp} X(q, r) C(q, c),  r < M <= 96, c < N,
 // for the FP32 form: the sketch B = Omega A (X = Omega^T) and W = V^T [V C] of the compact-WY
-// update (X = V).  Both use 3xTF32: each operand x = hi + lo with hi = tf32(x), lo = tf32(x - hi),
-// and x y ~ hi hi' + hi lo' + lo hi' (the lo lo' term, below 2^-22 |x y|, dropped).
+// update (X = V).  Each operand is split x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (exact to
+// about 2^-23 |x|), and x y = hi hi' + hi lo' + lo hi' + lo lo' on the TF32 tensor cores.
 //
-// One block of 128 threads computes 128 columns of C against all M rows of X over one K split.
-// Tiles are K-major (32 FP32 = one 128-byte swizzle row per column), brought in by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle) into a ring of stages with mbarrier completion.  All
-// threads round each tile to TF32 hi parts in place, write the lo parts to a twin buffer and
-// apply the unit-lower reflector mask where the tile covers the diagonal; one thread issues the
-// chunk's tcgen05.mma chain into tensor memory and commits it to the stage's "empty" barrier.
-// The accumulation over K happens outside the tensor core: each 32-row chunk's product is read
-// back (tcgen05.ld) and summed in FP32 registers with round-to-nearest, folded into a
-// compensated sum every TC_FOLD chunks, so the tensor core's own accumulator only ever adds the
-// twelve products of one chunk.  The epilogue writes the FP64 partials.  Every wait is bounded;
-// on timeout the block records RQRCP_ERR_TIMEOUT, waits (bounded) for its copies and MMA chains
-// in flight and frees its tensor memory.
+// One block (a TMA producer warp, an MMA warp and sixteen worker warps) computes 128 columns of C
+// against all M rows of X over one K split.  X is split into TF32 hi/lo parts once per launch
+// (xsplit_kernel) and used as one B operand of N = 2 Nb rows, [X_hi; X_lo]; C chunks of 32 rows
+// arrive raw by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a ring of stages.  The workers
+// split each C chunk into TF32 hi/lo parts and store them as the MMA's A operand in tensor memory
+// (tcgen05.st), so the tensor core reads only X from shared memory; one thread issues the chunk's
+// eight tcgen05.mma (A_lo and A_hi against [X_hi; X_lo], the four products hi hi', hi lo', lo hi',
+// lo lo' in two accumulator halves).  The accumulation over K happens outside the tensor core:
+// each chunk's product is read back (tcgen05.ld) and summed in FP32 registers with
+// round-to-nearest, folded into a compensated sum every TC_FOLD chunks, so the tensor core's own
+// accumulator only ever adds the eight products of one chunk.  The epilogue
+// writes the FP64 partials.  Every wait is bounded; on timeout the block records
+// RQRCP_ERR_TIMEOUT, waits (bounded) for its copies and MMA chains in flight and frees its
+// tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -24,10 +26,13 @@
 namespace rq {
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_WARPS_W = 16;                // worker warps (four per tensor-memory lane quarter)
+constexpr int TC_WORKERS = 32 * TC_WARPS_W;
+constexpr int TC_THREADS = 64 + TC_WORKERS;   // + TMA producer warp + MMA warp
 constexpr int TC_KC = 32;       // K per stage: one 128-byte swizzle row of FP32
 constexpr int TC_NA = 128;      // columns of C per block (MMA M)
-constexpr int TC_STAGES = 3;
+constexpr int TC_MAXST = 8;
+constexpr int TC_FOLD = 16;     // chunks summed in FP32 registers between compensated folds
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -40,17 +45,32 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity)
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
 {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or about
+// kTcSuspendNs pass, so a waiting warp costs no issue slots.
+constexpr unsigned kTcSuspendNs = 100000;
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(kTcSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity`; gives up after kTcWaitNs, or as soon as another
+// role of the block has recorded a failure in *fail (when fail is not null).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, const volatile int* fail)
+{
+    if (mbar_test(b, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(su32(b)), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_test(b, parity)) return true;
+        if (fail != nullptr && *fail) return false;
         if (globaltimer_ns() - t0 > kTcWaitNs) return false;
     }
 }
@@ -74,12 +94,13 @@ __device__ __forceinline__ uint32_t idesc_tf32(int m, int n)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, int acc)
+// A (M x K, lane m = row m, one TF32 element per 32-bit column) in tensor memory, B in shared memory.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc, int acc)
 {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(
             tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
@@ -87,47 +108,33 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                  : "memory");
 }
+// TF32 rounding of a finite FP32 value to its top 19 bits (10 explicit mantissa bits), ties away
+// from zero, by integer arithmetic on the bit pattern: adding half a TF32 ulp (bit 12) carries
+// into the kept bits (and the exponent) exactly when the dropped 13 bits are at least half.
 __device__ __forceinline__ float tf32_rn(float x)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Apply the unit-lower reflector mask and (split3) the TF32 hi/lo split to one tile of `rows`
-// 128-byte rows (row j holds K elements k0..k0+31 of column col0 + j, 16-byte chunks swizzled by
-// j mod 8).  Columns c = col0 + j < mask_lim carry the reflector structure: element (q, c) with
-// q = k0 + kk becomes 0 above the diagonal (q < c) and 1 on it.  hi = tf32(x), lo = tf32(x - hi).
-__device__ __forceinline__ void prep_tile(float* hi, float* lo, int rows, int k0, long long col0, long long mask_lim,
-                                          int split3)
+// X(q, r) (q < K, r < M, line r at X + r * ldx; unit-lower reflector structure for r < maskX) ->
+// TF32 parts xh[r * ldk + q] = tf32(x), xl[r * ldk + q] = tf32(x - tf32(x)); lines M <= r < gridDim.y
+// are zero.  One grid row per line r.
+__global__ void xsplit_kernel(const float* __restrict__ X, long long ldx, long long K, int M, long long maskX,
+                              long long ldk, float* __restrict__ xh, float* __restrict__ xl, const Status* st)
 {
-    for (int e4 = threadIdx.x; e4 < rows * 8; e4 += TC_THREADS) {
-        const int j = e4 >> 3, cp = e4 & 7;
-        float4 v = reinterpret_cast<float4*>(hi)[e4];
-        const long long c = col0 + j;
-        if (c < mask_lim) {
-            const int kk0 = ((cp ^ (j & 7)) << 2);
-            float* vv = reinterpret_cast<float*>(&v);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const long long q = (long long)k0 + kk0 + u;
-                if (q < c) vv[u] = 0.f;
-                else if (q == c) vv[u] = 1.f;
-            }
+    if (status_error(st)) return;
+    const long long r = blockIdx.y;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < K; q += (long long)gridDim.x * blockDim.x) {
+        float v = r < M ? X[r * ldx + q] : 0.f;
+        if (r < maskX) {
+            if (q < r) v = 0.f;
+            else if (q == r) v = 1.f;
         }
-        if (split3) {
-            float4 h, l;
-            h.x = tf32_rn(v.x); l.x = tf32_rn(v.x - h.x);
-            h.y = tf32_rn(v.y); l.y = tf32_rn(v.y - h.y);
-            h.z = tf32_rn(v.z); l.z = tf32_rn(v.z - h.z);
-            h.w = tf32_rn(v.w); l.w = tf32_rn(v.w - h.w);
-            reinterpret_cast<float4*>(hi)[e4] = h;
-            reinterpret_cast<float4*>(lo)[e4] = l;
-        } else if (c < mask_lim) {
-            reinterpret_cast<float4*>(hi)[e4] = v;
-        }
+        const float h = tf32_rn(v);
+        xh[r * ldk + q] = h;
+        xl[r * ldk + q] = tf32_rn(v - h);
     }
 }
 
@@ -135,42 +142,51 @@ struct TcArgs {
     int M, Nb;               // rows of X used (<= Nb), MMA N (multiple of 16)
     long long N, K;          // columns of C, contraction length
     long long kchunk;        // K per split (multiple of TC_KC)
-    int xx0, xy0, cx0, cy0;  // tensor-map coordinates of X(0,0) and C(0,0)
-    long long maskX, maskC;  // X columns r < maskX / C columns c < maskC carry the reflector mask
-    int split3;
-    int nst;                 // pipeline stages
+    long long maskC;         // C columns c < maskC carry the reflector mask
+    int nst;                 // pipeline stages (2..TC_MAXST)
     unsigned tmem_cols;
 };
 
-constexpr int TC_FOLD = 16;  // chunks summed in FP32 registers between compensated folds
-
-// Per block: 128 columns of C x all Nb rows of X over one K split.  Chunk kc's products go to
-// TMEM buffer kc % 2 (Nb columns each), started fresh (the hi*lo and lo*hi MMAs first, then hi*hi,
-// so that the accumulator's roundings on the large terms are only the four hi*hi steps).  While
-// chunk kc runs on the tensor pipe, every thread adds its row of chunk kc-1's buffer into FP32
-// registers (acc); every TC_FOLD chunks acc is folded into an FP32 shared-memory sum S with the
-// error-free TwoSum transformation, the rounding error carried back into acc (compensated sum).
+// Per block: 128 columns of C x all Nb rows of X over one K split, by three warp roles that hand
+// work to each other through mbarriers (no block-wide barrier inside the K loop).  Tensor memory
+// holds two accumulator buffers D0, D1 (2 Nb columns each: products with X_hi, then with X_lo)
+// and two operand buffers A0, A1 (64 columns: the TF32 hi parts of a 32-row chunk of C^T, then
+// its lo parts).
+//   warp 0 (one lane)  TMA producer: raw C chunk + the pre-split [X_hi; X_lo] chunk -> stage
+//                      kc % nst once the stage's previous MMA chain has completed (empty[s]).
+//   warps 2..17        workers (four per tensor-memory lane quarter, each on 8 of the chunk's 32
+//                      rows): read their C column's 8 values from the landed stage, apply the
+//                      reflector mask, split into TF32 hi/lo and store them to A[kc % 2] with
+//                      tcgen05.st (aready); then drain chunk kc-1's accumulator: tcgen05.ld of
+//                      their row and column quarter in both halves, FP32 round-to-nearest add
+//                      into registers (accempty).  Every TC_FOLD chunks a compensated fold (TwoSum, error carried
+//                      back) into a second register set.  A[kc % 2] is free again once chunk kc-2's
+//                      accumulator has been drained, which the worker itself waited for.
+//   warp 1 (one lane)  MMA issuer: D[kc % 2] = A_lo [X_hi; X_lo] + A_hi [X_hi; X_lo] over the
+//                      chunk (the small A_lo products first, so the accumulator of the large terms
+//                      rounds only the four hi*hi steps) once aready and accempty allow; commits to
+//                      empty[s] and accfull[kc % 2].
 template <int NBMAX>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tn_tc_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapX, TcArgs a,
                       double* __restrict__ P, Status* st)
 {
+    constexpr int CQ = NBMAX / 4;  // register columns per worker (a quarter of the MMA N)
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = status_error(st);
     __syncthreads();
-    if (s_skip) return;  // block-uniform: warp 0's tensor-memory allocation is warp-collective
+    if (s_skip) return;  // block-uniform: warp 1's tensor-memory allocation is warp-collective
     extern __shared__ unsigned char smraw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const int tileC = TC_NA * TC_KC * 4;     // 16 KB
-    const int tileX = a.Nb * TC_KC * 4;      // Nb * 128 bytes
-    const int stage_bytes = 2 * tileC + 2 * tileX;
+    const int tileX = 2 * a.Nb * TC_KC * 4;  // [X_hi; X_lo]: 2 Nb rows of 128 bytes
+    const int stage_bytes = tileC + tileX;
     const int nst = a.nst;
-    float* Ssum = reinterpret_cast<float*>(base + (size_t)nst * stage_bytes);  // [c][row], Nb x 128
-    __shared__ __align__(8) uint64_t full[4], empty[4];
+    __shared__ __align__(8) uint64_t full[TC_MAXST], empty[TC_MAXST], aready[2], accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
                      "r"(a.tmem_cols)
                      : "memory");
@@ -181,155 +197,210 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&aready[b], TC_WARPS_W);
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], TC_WARPS_W);
+        }
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int e = tid; e < TC_NA * a.Nb; e += TC_THREADS) Ssum[e] = 0.f;
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_base;
+    const uint32_t tA = tmem + (uint32_t)(4 * a.Nb);  // D0, D1 (2 Nb columns each), then A0, A1 (64)
     const long long n0 = (long long)blockIdx.x * TC_NA;
     const long long kbeg = (long long)blockIdx.y * a.kchunk;
     const long long kend = min(a.K, kbeg + a.kchunk);
     const int nchunks = (int)((kend - kbeg + TC_KC - 1) / TC_KC);
-    const uint32_t idesc = idesc_tf32(TC_NA, a.Nb);
     auto stage_ptr = [&](int s) { return base + (size_t)s * stage_bytes; };
-    int issued = 0;   // chunks whose TMA thread 0 has issued
-    int landed = 0;   // chunks whose TMA thread 0 has seen complete
-    int mma_done = 0; // chunks whose MMA chain this thread has seen complete
-    auto issue = [&](int kc) {
-        const int s = kc % nst;
-        unsigned char* sp = stage_ptr(s);
-        const int k0 = (int)(kbeg + (long long)kc * TC_KC);
-        mbar_expect_tx(&full[s], tileC + tileX);
-        tma_load_2d(sp, &mapC, a.cx0 + k0, a.cy0 + (int)n0, &full[s]);
-        tma_load_2d(sp + 2 * tileC, &mapX, a.xx0 + k0, a.xy0, &full[s]);
-    };
-    if (tid == 0)
-        for (; issued < nst && issued < nchunks; ++issued) issue(issued);
-
-    float acc[NBMAX];
-#pragma unroll
-    for (int j = 0; j < NBMAX; ++j) acc[j] = 0.f;
-    const int row = 32 * warp + lane;  // row of D = column n0 + row of C
-    // add chunk kc's TMEM buffer (after its MMA chain completed) into acc
-    auto drain = [&](int kc) -> bool {
-        bool ok = mbar_wait(&empty[kc % nst], (unsigned)(kc / nst) & 1u);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) return false;
-        mma_done = kc + 1;
-        fence_after();
-        const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((kc & 1) * a.Nb);
-#pragma unroll
-        for (int c0 = 0; c0 < NBMAX; c0 += 16) {
-            if (c0 < a.Nb) {
-                uint32_t r[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(tb + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
-            }
-        }
-        return true;
-    };
-    // compensated fold: (S, e) = TwoSum(S, acc), acc = e
-    auto fold = [&]() {
-#pragma unroll
-        for (int j = 0; j < NBMAX; ++j) {
-            if (j < a.Nb) {
-                const float sv = Ssum[j * TC_NA + row];
-                const float t = sv + acc[j];
-                const float bp = t - sv;
-                const float e = (sv - (t - bp)) + (acc[j] - bp);
-                Ssum[j * TC_NA + row] = t;
-                acc[j] = e;
-            }
-        }
+    auto fail = [&]() {
+        s_fail = 1;
+        set_error(st, RQRCP_ERR_TIMEOUT);
     };
 
-    bool ok = true;      // false once this thread's warp saw a wait run out
-    int mma_issued = 0;  // chunks whose MMA chain thread 0 has issued
-    for (int kc = 0; kc < nchunks; ++kc) {
-        const int s = kc % nst;
-        unsigned char* sp = stage_ptr(s);
-        float* cHi = reinterpret_cast<float*>(sp);
-        float* cLo = reinterpret_cast<float*>(sp + tileC);
-        float* xHi = reinterpret_cast<float*>(sp + 2 * tileC);
-        float* xLo = reinterpret_cast<float*>(sp + 2 * tileC + tileX);
-        const int k0 = (int)(kbeg + (long long)kc * TC_KC);
-        if (ok && !mbar_wait(&full[s], (unsigned)(kc / nst) & 1u)) ok = false;
-        if (!ok) s_fail = 1;
-        else if (tid == 0) landed = kc + 1;
-        const long long mc = (a.maskC > n0 && k0 < a.maskC) ? a.maskC : 0;
-        const long long mx = (k0 < a.maskX) ? a.maskX : 0;
-        if (ok) {
-            if (a.split3 || mc) prep_tile(cHi, cLo, TC_NA, k0, n0, mc, a.split3);
-            if (a.split3 || mx) prep_tile(xHi, xLo, a.Nb, k0, 0, mx, a.split3);
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kc = 0; kc < nchunks; ++kc) {
+                const int s = kc % nst;
+                if (kc >= nst && !mbar_wait(&empty[s], (unsigned)((kc - nst) / nst) & 1u, &s_fail)) {
+                    fail();
+                    break;
+                }
+                unsigned char* sp = stage_ptr(s);
+                const int k0 = (int)(kbeg + (long long)kc * TC_KC);
+                mbar_expect_tx(&full[s], tileC + tileX);
+                tma_load_2d(sp, &mapC, k0, (int)n0, &full[s]);
+                tma_load_2d(sp + tileC, &mapX, k0, 0, &full[s]);
+                issued = kc + 1;
+            }
+            // the copies still in flight land before the block leaves (bounded)
+            for (int kc = (issued > nst ? issued - nst : 0); kc < issued; ++kc)
+                mbar_wait(&full[kc % nst], (unsigned)(kc / nst) & 1u, nullptr);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (s_fail) break;  // block-uniform: read after the barrier, written only before it
-        if (tid == 0) {
-            const uint32_t td = tmem + (uint32_t)((kc & 1) * a.Nb);
-            int acc_on = 0;
-            if (a.split3) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(TC_NA, 2 * a.Nb);
+            int issued = 0;
+            for (int kc = 0; kc < nchunks; ++kc) {
+                const int s = kc % nst, b = kc & 1;
+                if (!mbar_wait(&aready[b], (unsigned)(kc >> 1) & 1u, &s_fail) ||
+                    (kc >= 2 && !mbar_wait(&accempty[b], (unsigned)((kc - 2) >> 1) & 1u, &s_fail))) {
+                    fail();
+                    break;
+                }
+                fence_after();
+                const unsigned char* xt = stage_ptr(s) + tileC;
+                const uint32_t td = tmem + (uint32_t)(b * 2 * a.Nb);
+                const uint32_t ta = tA + (uint32_t)(b * 64);
 #pragma unroll
-                for (int k = 0; k < TC_KC / 8; ++k) {
-                    mma_tf32(td, umma_desc(reinterpret_cast<unsigned char*>(cHi) + k * 32),
-                             umma_desc(reinterpret_cast<unsigned char*>(xLo) + k * 32), idesc, acc_on);
-                    acc_on = 1;
-                    mma_tf32(td, umma_desc(reinterpret_cast<unsigned char*>(cLo) + k * 32),
-                             umma_desc(reinterpret_cast<unsigned char*>(xHi) + k * 32), idesc, 1);
+                for (int k = 0; k < TC_KC / 8; ++k)
+                    mma_tf32_ts(td, ta + 32 + 8 * k, umma_desc(xt + k * 32), idesc, k > 0 ? 1 : 0);
+#pragma unroll
+                for (int k = 0; k < TC_KC / 8; ++k) mma_tf32_ts(td, ta + 8 * k, umma_desc(xt + k * 32), idesc, 1);
+                mma_commit(&empty[s]);
+                mma_commit(&accfull[b]);
+                issued = kc + 1;
+            }
+            // every MMA chain completes before tensor memory is freed (bounded)
+            if (issued > 0) mbar_wait(&empty[(issued - 1) % nst], (unsigned)((issued - 1) / nst) & 1u, nullptr);
+        }
+    } else {
+        const int q = warp & 3;             // tensor-memory lane quarter this warp may access
+        const int h = (warp - 2) >> 2;      // column quarter (drain) and 8-row slice (operand store)
+        const int qc = a.Nb >> 2;           // accumulator columns per worker warp (multiple of 4)
+        const int cb = h * qc;
+        const int row = 32 * q + lane;      // row of D / A = column n0 + row of C
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const long long c = n0 + row;
+        float acc[CQ], sum[CQ];
+#pragma unroll
+        for (int j = 0; j < CQ; ++j) acc[j] = sum[j] = 0.f;
+        auto drain = [&](int kc) -> bool {
+            const bool ok = mbar_wait(&accfull[kc & 1], (unsigned)(kc >> 1) & 1u, &s_fail);
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            fence_after();
+            // column j of this quarter: X_hi product at tb + j, X_lo product at tb + Nb + j;
+            // groups of up to 8 columns: all loads of a group in flight, one wait
+            const uint32_t tb = tmem + lane_base + (uint32_t)((kc & 1) * 2 * a.Nb + cb);
+#pragma unroll
+            for (int g0 = 0; g0 < CQ; g0 += 8) {
+                if (g0 < qc) {
+                    uint32_t rh[8], rl[8];
+#pragma unroll
+                    for (int c0 = 0; c0 < 8 && g0 + c0 < CQ; c0 += 4) {
+                        if (g0 + c0 < qc) {
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                         : "=r"(rh[c0]), "=r"(rh[c0 + 1]), "=r"(rh[c0 + 2]), "=r"(rh[c0 + 3])
+                                         : "r"(tb + (uint32_t)(g0 + c0)));
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                         : "=r"(rl[c0]), "=r"(rl[c0 + 1]), "=r"(rl[c0 + 2]), "=r"(rl[c0 + 3])
+                                         : "r"(tb + (uint32_t)(a.Nb + g0 + c0)));
+                        }
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int c0 = 0; c0 < 8 && g0 + c0 < CQ; c0 += 4) {
+                        if (g0 + c0 < qc) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                acc[g0 + c0 + u] += __uint_as_float(rl[c0 + u]) + __uint_as_float(rh[c0 + u]);
+                        }
+                    }
                 }
             }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[kc & 1]);
+            return true;
+        };
+        // compensated fold: (sum, e) = TwoSum(sum, acc), acc = e
+        auto fold = [&]() {
 #pragma unroll
-            for (int k = 0; k < TC_KC / 8; ++k) {
-                mma_tf32(td, umma_desc(reinterpret_cast<unsigned char*>(cHi) + k * 32),
-                         umma_desc(reinterpret_cast<unsigned char*>(xHi) + k * 32), idesc, acc_on);
-                acc_on = 1;
+            for (int j = 0; j < CQ; ++j) {
+                const float t = sum[j] + acc[j];
+                const float bp = t - sum[j];
+                const float e = (sum[j] - (t - bp)) + (acc[j] - bp);
+                sum[j] = t;
+                acc[j] = e;
             }
-            mma_commit(&empty[s]);
-            mma_issued = kc + 1;
-        }
-        if (kc >= 1) {
-            if (!drain(kc - 1)) {
+        };
+        bool ok = true;
+        for (int kc = 0; kc < nchunks; ++kc) {
+            const int s = kc % nst;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)(kc / nst) & 1u, &s_fail))) {
                 ok = false;
-                s_fail = 1;  // seen by every thread at the next iteration's barrier
-            } else {
+                break;
+            }
+            // this thread's 8 values: rows k0 + 8h .. k0 + 8h + 7 of column c, two swizzled
+            // 16-byte pieces of the tile's row `row`
+            const unsigned char* tile = stage_ptr(s);
+            const int k0 = (int)(kbeg + (long long)kc * TC_KC);
+            float v[8];
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+                const int piece = (2 * h + pc) ^ (row & 7);
+                const float4 f = *reinterpret_cast<const float4*>(tile + row * 128 + piece * 16);
+                v[4 * pc] = f.x;
+                v[4 * pc + 1] = f.y;
+                v[4 * pc + 2] = f.z;
+                v[4 * pc + 3] = f.w;
+            }
+            if (c < a.maskC && k0 < a.maskC) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const long long qq = (long long)k0 + 8 * h + u;
+                    if (qq < c) v[u] = 0.f;
+                    else if (qq == c) v[u] = 1.f;
+                }
+            }
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float hv = tf32_rn(v[u]);
+                hi[u] = __float_as_uint(hv);
+                lo[u] = __float_as_uint(tf32_rn(v[u] - hv));
+            }
+            const uint32_t ta = tA + lane_base + (uint32_t)((kc & 1) * 64 + 8 * h);
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+                         "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+                         "r"(hi[7])
+                         : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta + 32),
+                         "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
+                         "r"(lo[7])
+                         : "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aready[kc & 1]);
+            if (kc >= 1) {
+                if (!drain(kc - 1)) {
+                    ok = false;
+                    break;
+                }
                 if (kc % TC_FOLD == 0) fold();
-                // stage (kc - 1) % nst is free again: bring in chunk kc - 1 + nst
-                if (tid == 0 && issued < nchunks) issue(issued++);
             }
         }
-    }
-    if (ok && !s_fail && nchunks > 0 && !drain(nchunks - 1)) ok = false;
-    if (!ok) s_fail = 1;
-    __syncthreads();
-    if (!s_fail && nchunks > 0) {
-        fold();
-        const long long c = n0 + row;
-        double* Pz = P + (long long)blockIdx.y * a.N * a.M;
+        if (ok && nchunks > 0 && !drain(nchunks - 1)) ok = false;
+        if (!ok) {
+            fail();
+        } else if (nchunks > 0) {
+            fold();
+            double* Pz = P + (long long)blockIdx.y * a.N * a.M;
+            if (c < a.N) {
 #pragma unroll
-        for (int j = 0; j < NBMAX; ++j)
-            if (j < a.M && c < a.N) Pz[c * a.M + j] = (double)Ssum[j * TC_NA + row] + (double)acc[j];
-    } else if (s_fail && tid == 0) {
-        set_error(st, RQRCP_ERR_TIMEOUT);
-        // bounded waits for the copies and MMA chains still in flight
-        for (int kc = landed; kc < issued; ++kc) mbar_wait(&full[kc % nst], (unsigned)(kc / nst) & 1u);
-        for (int kc = mma_done; kc < mma_issued; ++kc) mbar_wait(&empty[kc % nst], (unsigned)(kc / nst) & 1u);
+                for (int j = 0; j < CQ; ++j)
+                    if (j < qc && cb + j < a.M) Pz[c * a.M + cb + j] = (double)sum[j] + (double)acc[j];
+            }
+        }
     }
     fence_before();
     __syncthreads();
-    if (warp == 0)
+    fence_after();
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
@@ -370,8 +441,7 @@ namespace {
 
 size_t tc_smem_bytes(int Nb, int nst)
 {
-    return 1024 + (size_t)nst * (2 * (size_t)TC_NA * TC_KC * 4 + 2 * (size_t)Nb * TC_KC * 4) +
-           (size_t)TC_NA * Nb * sizeof(float);
+    return 1024 + (size_t)nst * ((size_t)TC_NA * TC_KC * 4 + 2 * (size_t)Nb * TC_KC * 4);
 }
 
 // Dynamic shared memory a kernel may use next to its static shared memory.
@@ -392,26 +462,30 @@ size_t tc_dyn_limit()
 
 size_t tc_dyn_limit_for(int Nb)
 {
-    return Nb <= 32 ? tc_dyn_limit<32>() : Nb <= 64 ? tc_dyn_limit<64>() : tc_dyn_limit<128>();
+    return Nb <= 32 ? tc_dyn_limit<32>() : Nb <= 64 ? tc_dyn_limit<64>() : tc_dyn_limit<96>();
 }
 
-// Pipeline depth: 4 stages where they fit, else 3 or 2 (0: not even 2 fit).
+// Pipeline depth: TC_MAXST stages where they fit, else fewer (0: not even 2 fit).
 int tc_stages(int Nb)
 {
     const size_t lim = tc_dyn_limit_for(Nb);
-    for (int nst = 4; nst >= 2; --nst)
+    for (int nst = TC_MAXST; nst >= 2; --nst)
         if (tc_smem_bytes(Nb, nst) <= lim) return nst;
     return 0;
 }
 
 }  // namespace
 
-bool tc_gemm_supported(long long M, long long ldx, long long ldc, const void* X, const void* C)
+bool tc_gemm_supported(long long M, long long ldc, const void* C)
 {
-    if (!(M >= 1 && M <= 128 && (ldx % 4) == 0 && (ldc % 4) == 0 && ((uintptr_t)X % 16) == 0 &&
-          ((uintptr_t)C % 16) == 0 && tensor_map_encoder() != nullptr))
+    if (!(M >= 1 && M <= 96 && (ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tensor_map_encoder() != nullptr))
         return false;
     return tc_stages((int)(((M + 15) / 16) * 16)) >= 2;
+}
+
+size_t tc_xsplit_bytes(long long M, long long K)
+{
+    return 2 * (size_t)((M + 15) / 16 * 16) * (size_t)((K + 3) / 4 * 4) * sizeof(float);
 }
 
 // Split-K chunk for the tensor-core kernel (one resident block per SM): the split count S <= 16
@@ -440,37 +514,35 @@ long long tc_kchunk(long long N, long long K, int& nsplit)
     return kc;
 }
 
-// X given as (matrix base, ld, coordinates of X(0,0)): X(q, r) lives at
-// base[(xy0 + r) * ldx + xx0 + q] (each of the M lines holds K contiguous elements), the same
-// for C(q, c) at cbase[(cy0 + c) * ldc + cx0 + q].  Extents: X lines xlines, C lines clines,
-// inner lengths xinner / cinner (TMA fills zeros beyond the matrices).
-cudaError_t launch_gemm_tn_tc(const float* xbase, long long ldx, long long xinner, long long xlines, int xx0, int xy0,
-                              const float* cbase, long long ldc, long long cinner, long long clines, int cx0, int cy0,
-                              long long M, long long N, long long K, long long kchunk, double* P, long long maskX,
-                              long long maskC, int split3, const Status* st, cudaStream_t s)
+cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
+                              long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
+                              const Status* st, cudaStream_t s)
 {
-    CUtensorMap mapC, mapX;
     const int Nb = (int)(((M + 15) / 16) * 16);
     const int nst = tc_stages(Nb);
-    if (nst < 2) return cudaErrorInvalidValue;
-    if (!encode_map(&mapC, cbase, cinner, clines, ldc, TC_NA)) return cudaErrorInvalidValue;
-    if (!encode_map(&mapX, xbase, xinner, xlines, ldx, Nb)) return cudaErrorInvalidValue;
+    if (nst < 2 || ((uintptr_t)xs % 16) != 0) return cudaErrorInvalidValue;
+    const long long ldk = (K + 3) / 4 * 4;
+    float* xh = xs;  // Nb lines of ldk (lines M.. zero), then the lo parts
+    float* xl = xs + (size_t)Nb * ldk;
+    {
+        long long gx = (K + 255) / 256;
+        if (gx > 64) gx = 64;
+        xsplit_kernel<<<dim3((unsigned)gx, (unsigned)Nb), 256, 0, s>>>(X, ldx, K, (int)M, maskX, ldk, xh, xl, st);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    CUtensorMap mapC, mapX;
+    if (!encode_map(&mapC, C, K, N, ldc, TC_NA)) return cudaErrorInvalidValue;
+    if (!encode_map(&mapX, xh, K, 2 * Nb, ldk, 2 * Nb)) return cudaErrorInvalidValue;  // [X_hi; X_lo]
     TcArgs a;
     a.M = (int)M;
     a.Nb = Nb;
     a.N = N;
     a.K = K;
     a.kchunk = kchunk;
-    a.xx0 = xx0;
-    a.xy0 = xy0;
-    a.cx0 = cx0;
-    a.cy0 = cy0;
-    a.maskX = maskX;
     a.maskC = maskC;
-    a.split3 = split3;
     a.nst = nst;
     unsigned cols = 32;
-    while ((int)cols < 2 * Nb) cols <<= 1;
+    while ((int)cols < 4 * Nb + 128) cols <<= 1;  // D0, D1, A0, A1
     a.tmem_cols = cols;
     const size_t smem = tc_smem_bytes(Nb, nst);
     dim3 grid((unsigned)((N + TC_NA - 1) / TC_NA), (unsigned)((K + kchunk - 1) / kchunk));
@@ -482,10 +554,10 @@ cudaError_t launch_gemm_tn_tc(const float* xbase, long long ldx, long long xinne
         kern<<<grid, TC_THREADS, smem, s>>>(mapC, mapX, a, P, const_cast<Status*>(st));
         return cudaGetLastError();
     };
-    static bool set32 = false, set64 = false, set128 = false;
+    static bool set32 = false, set64 = false, set96 = false;
     if (Nb <= 32) return run(gemm_tn_tc_kernel<32>, set32);
     if (Nb <= 64) return run(gemm_tn_tc_kernel<64>, set64);
-    return run(gemm_tn_tc_kernel<128>, set128);
+    return run(gemm_tn_tc_kernel<96>, set96);
 }
 
 }  // namespace rq

@@ -117,15 +117,17 @@ cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int
                            int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,
                            const Status* st, cudaStream_t s);
 
-// Tensor-core (tcgen05 kind::tf32) split-K contraction with the same output as launch_gemm_tn:
-// X(q, r) = xbase[(xy0 + r) * ldx + xx0 + q], C(q, c) = cbase[(cy0 + c) * ldc + cx0 + q];
-// split3 selects the 3xTF32 hi/lo product.  kchunk must come from tc_kchunk (multiple of 32).
-bool tc_gemm_supported(long long M, long long ldx, long long ldc, const void* X, const void* C);
+// Tensor-core (tcgen05 kind::tf32, 3xTF32) split-K contraction with the output of
+// launch_gemm_tn<float>: X(q, r) = X[r * ldx + q] (q < K, r < M; unit-lower reflector structure
+// for r < maskX), C(q, c) = C[c * ldc + q] (c < N; the structure for c < maskC).  C must be
+// 16-byte aligned with ldc % 4 == 0 (tc_gemm_supported); xs (16-byte aligned,
+// tc_xsplit_bytes(M, K)) receives the TF32 parts of X.  kchunk must come from tc_kchunk.
+bool tc_gemm_supported(long long M, long long ldc, const void* C);
+size_t tc_xsplit_bytes(long long M, long long K);
 long long tc_kchunk(long long N, long long K, int& nsplit);
-cudaError_t launch_gemm_tn_tc(const float* xbase, long long ldx, long long xinner, long long xlines, int xx0, int xy0,
-                              const float* cbase, long long ldc, long long cinner, long long clines, int cx0, int cy0,
-                              long long M, long long N, long long K, long long kchunk, double* P, long long maskX,
-                              long long maskC, int split3, const Status* st, cudaStream_t s);
+cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
+                              long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
+                              const Status* st, cudaStream_t s);
 bool tensor_cores_enabled();
 
 // C(mr x nc) -= V(mr x kb) * Y(kb x nc).  maskV: V has the unit-lower reflector structure.

@@ -58,7 +58,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t status, omega, B, P, Y, Tm, What, piv, cand, part, tmp, total;
+    size_t status, omega, B, P, Y, Tm, What, piv, cand, part, tmp, xs, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
@@ -82,6 +82,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     L.cand = take(pivot_cand_bytes((int)l) + sizeof(long long) * (1 + 4 * (size_t)b));
     L.part = take(panel_part_bytes((int)b));
     L.tmp = take((size_t)2 * b * m * esz);
+    L.xs = take(esz == sizeof(float) ? tc_xsplit_bytes(l > b ? l : b, m) : 0);  // TF32 parts of Omega / V
     L.total = off;
     return L;
 }
@@ -172,13 +173,12 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     {
         int ns;
         int64_t kc;
-        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() &&
-                        tc_gemm_supported(l, ldo, lda, (const void*)Omega, (const void*)A);
+        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(l, lda, (const void*)A);
         if (tc) {
             kc = tc_kchunk(n, m, ns);
             RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
-                      launch_gemm_tn_tc((const float*)Omega, ldo, m, l, 0, 0, (const float*)A, lda, m, n, 0, 0, l, n, m,
-                                        kc, P, 0, 0, 1, st, s));
+                      launch_gemm_tn_tc((const float*)Omega, ldo, (const float*)A, lda, l, n, m, kc, P, 0, 0,
+                                        reinterpret_cast<float*>(w + L.xs), st, s));
         } else {
             choose_split(l, n, m, ns, kc);
             RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
@@ -206,13 +206,12 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         if (nt <= 0) continue;
         int ns;
         int64_t kc;
-        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && (i % 4) == 0 &&
-                        tc_gemm_supported(bb, lda, lda, (const void*)A, (const void*)A);
+        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(bb, lda, (const void*)Vp);
         if (tc) {
             kc = tc_kchunk(n - i, mr, ns);
             RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
-                      launch_gemm_tn_tc((const float*)A, lda, m, n, (int)i, (int)i, (const float*)A, lda, m, n, (int)i,
-                                        (int)i, bb, n - i, mr, kc, P, bb, bb, 1, st, s));
+                      launch_gemm_tn_tc((const float*)Vp, lda, (const float*)Vp, lda, bb, n - i, mr, kc, P, bb, bb,
+                                        reinterpret_cast<float*>(w + L.xs), st, s));
         } else {
             choose_split(bb, n - i, mr, ns, kc);
             RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
