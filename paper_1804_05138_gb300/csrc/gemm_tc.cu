@@ -18,10 +18,7 @@
 // writes the FP64 partials.  Every wait is bounded; on timeout the block records
 // RQRCP_ERR_TIMEOUT, waits (bounded) for its copies and MMA chains in flight and frees its
 // tensor memory.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "internal.cuh"
+#include "tc_common.cuh"
 
 namespace rq {
 namespace {
@@ -33,90 +30,7 @@ constexpr int TC_KC = 32;       // K per stage: one 128-byte swizzle row of FP32
 constexpr int TC_NA = 128;      // columns of C per block (MMA M)
 constexpr int TC_MAXST = 8;
 constexpr int TC_FOLD = 16;     // chunks summed in FP32 registers between compensated folds
-constexpr unsigned long long kTcWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned cnt)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(cnt) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-// try_wait with a suspend-time hint: the thread sleeps until the phase completes or about
-// kTcSuspendNs pass, so a waiting warp costs no issue slots.
-constexpr unsigned kTcSuspendNs = 100000;
-__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity), "r"(kTcSuspendNs)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of parity `parity`; gives up after kTcWaitNs, or as soon as another
-// role of the block has recorded a failure in *fail (when fail is not null).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, const volatile int* fail)
-{
-    if (mbar_test(b, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-        if (mbar_test(b, parity)) return true;
-        if (fail != nullptr && *fail) return false;
-        if (globaltimer_ns() - t0 > kTcWaitNs) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            su32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
-        : "memory");
-}
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart.
-__device__ __forceinline__ uint64_t umma_desc(const void* base)
-{
-    const uint64_t addr = su32(base);
-    return ((addr >> 4) & 0x3FFFull) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
-           ((uint64_t)2 << 61);
-}
-// Instruction descriptor: D FP32, A and B TF32, both K-major, N >> 3, M >> 4.
-__device__ __forceinline__ uint32_t idesc_tf32(int m, int n)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-// A (M x K, lane m = row m, one TF32 element per 32-bit column) in tensor memory, B in shared memory.
-__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc, int acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(
-            tmem_d),
-        "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-// TF32 rounding of a finite FP32 value to its top 19 bits (10 explicit mantissa bits), ties away
-// from zero, by integer arithmetic on the bit pattern: adding half a TF32 ulp (bit 12) carries
-// into the kept bits (and the exponent) exactly when the dropped 13 bits are at least half.
-__device__ __forceinline__ float tf32_rn(float x)
-{
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+using namespace tc;
 
 // X(q, r) (q < K, r < M, line r at X + r * ldx; unit-lower reflector structure for r < maskX) ->
 // TF32 parts xh[r * ldk + q] = tf32(x), xl[r * ldk + q] = tf32(x - tf32(x)); lines M <= r < gridDim.y
@@ -404,6 +318,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
+}  // namespace
+
+namespace {
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -420,24 +338,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// 2-D FP32 tensor map over a column-major (or row-major, by swapping roles) array with `inner`
-// contiguous elements per line, `outer` lines `ld` elements apart; box = 32 x box_outer, 128B swizzle.
+// TC_KC x box_outer box with 128-byte swizzle over K-major FP32 lines.
 bool encode_map(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld, int box_outer)
 {
-    auto enc = tensor_map_encoder();
-    if (enc == nullptr) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {(cuuint32_t)TC_KC, (cuuint32_t)box_outer};
-    cuuint32_t es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return tc_encode_2d(map, base, inner, outer, ld, TC_KC, box_outer, true);
 }
-
-}  // namespace
-
-namespace {
 
 size_t tc_smem_bytes(int Nb, int nst)
 {
@@ -475,6 +380,23 @@ int tc_stages(int Nb)
 }
 
 }  // namespace
+
+bool tc_encoder_available() { return tensor_map_encoder() != nullptr; }
+
+bool tc_encode_2d(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld, int box_inner,
+                  int box_outer, bool swizzle128)
+{
+    auto enc = tensor_map_encoder();
+    if (enc == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               swizzle128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool tc_gemm_supported(long long M, long long ldc, const void* C)
 {

@@ -128,6 +128,15 @@ long long tc_kchunk(long long N, long long K, int& nsplit);
 cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
                               long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
                               const Status* st, cudaStream_t s);
+// Tensor-core (tcgen05 kind::tf32, 3xTF32) form of launch_gemm_update<float> without colmap:
+// C(mr x nt) -= V(mr x kb) Y(kb x nt), kb <= 64, V unit-lower for rows r < maskV.  C must be
+// 16-byte aligned with ldc % 4 == 0 (tc_update_supported); ys (16-byte aligned,
+// tc_update_ws_bytes(nt)) receives the TF32 parts of Y.
+bool tc_update_supported(long long kb, long long ldc, const void* C);
+size_t tc_update_ws_bytes(long long nt);
+cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long long ldv, const double* Y, long long ldy,
+                                  long long mr, long long nt, int kb, long long maskV, float* ys, const Status* st,
+                                  cudaStream_t s);
 bool tensor_cores_enabled();
 
 // C(mr x nc) -= V(mr x kb) * Y(kb x nc).  maskV: V has the unit-lower reflector structure.

@@ -82,7 +82,11 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     L.cand = take(pivot_cand_bytes((int)l) + sizeof(long long) * (1 + 4 * (size_t)b));
     L.part = take(panel_part_bytes((int)b));
     L.tmp = take((size_t)2 * b * m * esz);
-    L.xs = take(esz == sizeof(float) ? tc_xsplit_bytes(l > b ? l : b, m) : 0);  // TF32 parts of Omega / V
+    {
+        // TF32 parts of Omega / V (contraction) and of Y (update); used one after the other
+        const size_t xs = tc_xsplit_bytes(l > b ? l : b, m), ys = tc_update_ws_bytes(n);
+        L.xs = take(esz == sizeof(float) ? (xs > ys ? xs : ys) : 0);
+    }
     L.total = off;
     return L;
 }
@@ -221,8 +225,13 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
                   launch_tform(P, ns, n - i, bb, tau + i, Tm, st, s));
         RQ_LAUNCH(K_REDUCE_Y, (double)bb * bb * nt, ((double)ns + 1.0) * bb * nt * 8,
                   launch_reduce_y(P, ns, n - i, bb, bb, Tm, 1, Y, nt, st, s));
-        RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
-                  launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st, s));
+        if (sizeof(T) == 4 && tensor_cores_enabled() && tc_update_supported(bb, lda, Vp + (int64_t)bb * lda))
+            RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
+                      launch_gemm_update_tc((float*)(Vp + (int64_t)bb * lda), lda, (const float*)Vp, lda, Y, bb, mr, nt,
+                                            bb, bb, reinterpret_cast<float*>(w + L.xs), st, s));
+        else
+            RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
+                      launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st, s));
         if (i + bb < k)
             RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
                       launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));

@@ -1,0 +1,341 @@
+// update_tc.cu -- tensor-core (tcgen05, kind::tf32) form of the compact-WY trailing update of the
+// FP32 form (Alg. 2's block step, the Householder block applied as I - V T V^T):
+//   C(mr x nt) -= V(mr x kb) Y(kb x nt),  kb <= 64,
+// with Y = T^T W coming from the FP64 reduction.  Both operands are split into TF32 parts
+// (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)) and V Y = V_hi [Y_hi Y_lo] + V_lo [Y_hi Y_lo].
+//
+// A persistent kernel: block b of G owns the contiguous run [b T / G, (b+1) T / G) of the T tiles
+// (128 rows x 64 columns of C) in band-major order.  Per 128-row band the workers load V's band,
+// split it and store it to tensor memory as the MMA's A operand (hi parts in 64 columns, lo parts
+// in 64 more).  Per tile, a TMA producer warp loads the pre-split Y tile ([Y_hi; Y_lo] as a
+// 128-row K-major B operand, 128-byte swizzle) and the C tile (128 rows x 64 columns, column-major)
+// into a stage; one thread issues 2 ceil(kb / 8) MMAs (the A_lo products first) into one of two
+// accumulators (128 x 128: the Y_hi half, then the Y_lo half); sixteen worker warps read the
+// accumulator (tcgen05.ld), subtract it from the C tile in shared memory and hand the tile back
+// to the producer, which writes it with a TMA store.  Every wait is bounded; on timeout the block
+// records RQRCP_ERR_TIMEOUT, lets its copies land and frees its tensor memory.
+#include "tc_common.cuh"
+
+namespace rq {
+namespace {
+using namespace tc;
+
+constexpr int UT_WARPS_W = 16;               // worker warps (four per tensor-memory lane quarter)
+constexpr int UT_WORKERS = 32 * UT_WARPS_W;
+constexpr int UT_THREADS = 64 + UT_WORKERS;  // + TMA producer warp + MMA warp
+constexpr int UT_BM = 128;                   // rows of C per band (MMA M)
+constexpr int UT_BN = 64;                    // columns of C per tile (MMA N = 2 UT_BN)
+constexpr int UT_KP = 64;                    // contraction length padded (kb <= 64)
+constexpr int UT_NST = 3;                    // pipeline stages
+constexpr int UT_TILE_Y = 2 * UT_BN * UT_KP * 4;  // 32 KB: two K halves of 128 rows x 128 bytes
+constexpr int UT_TILE_C = UT_BM * UT_BN * 4;      // 32 KB: [column][row]
+constexpr int UT_STAGE = UT_TILE_Y + UT_TILE_C;
+constexpr unsigned UT_TMEM_COLS = 512;       // D0 (0..127), D1 (128..255), A hi (256..319), A lo (320..383)
+
+// Y (kb x nt FP64, column c at Y + c * ldy) -> ys: for tile t = c / 64, j = c % 64, line t * 128 + j
+// holds tf32(y(:, c)) and line t * 128 + 64 + j holds tf32(y - tf32(y)), 64 values per line (zero
+// for k >= kb and for c >= nt).
+__global__ void ysplit_kernel(const double* __restrict__ Y, long long ldy, int kb, long long nt, long long ntiles,
+                              float* __restrict__ ys, const Status* st)
+{
+    if (status_error(st)) return;
+    const long long total = ntiles * UT_BN * UT_KP;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % UT_KP);
+        const long long c = e / UT_KP;
+        const long long t = c / UT_BN;
+        const int j = (int)(c % UT_BN);
+        float h = 0.f, l = 0.f;
+        if (c < nt && k < kb) {
+            const double y = Y[c * ldy + k];
+            h = tf32_rn((float)y);
+            l = tf32_rn((float)(y - (double)h));
+        }
+        ys[(t * 2 * UT_BN + j) * UT_KP + k] = h;
+        ys[(t * 2 * UT_BN + UT_BN + j) * UT_KP + k] = l;
+    }
+}
+
+struct UtArgs {
+    long long mr, nt;      // rows and columns of C
+    int kb, ksteps;        // contraction length (<= 64), MMA k-steps ceil(kb / 8)
+    long long maskV;       // rows r < maskV of V carry the unit-lower structure
+    long long ntiles;      // 64-column tiles per band
+    long long total;       // bands * ntiles
+};
+
+__global__ void __launch_bounds__(UT_THREADS, 1)
+    update_tc_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapY,
+                     const float* __restrict__ V, long long ldv, UtArgs a, Status* st)
+{
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = status_error(st);
+    __syncthreads();
+    if (s_skip) return;  // block-uniform: warp 1's tensor-memory allocation is warp-collective
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[UT_NST], cdone[UT_NST], aready, accfull[2], accempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 1) tmem_alloc(&tmem_base, UT_TMEM_COLS);
+    if (tid == 0) {
+        for (int s = 0; s < UT_NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&cdone[s], UT_WARPS_W);
+        }
+        mbar_init(&aready, UT_WARPS_W);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], UT_WARPS_W);
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t tA = tmem + 256;
+    const long long g0 = a.total * blockIdx.x / gridDim.x;
+    const long long g1 = a.total * (blockIdx.x + 1) / gridDim.x;
+    auto stage_ptr = [&](int s) { return base + (size_t)s * UT_STAGE; };
+    auto fail = [&]() {
+        s_fail = 1;
+        set_error(st, RQRCP_ERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int px[UT_NST], py[UT_NST];  // C coordinates of the tile held by each stage
+            long long t = 0;
+            bool ok = true;
+            for (long long g = g0; g < g1; ++g, ++t) {
+                const int s = (int)(t % UT_NST);
+                unsigned char* sp = stage_ptr(s);
+                if (t >= UT_NST) {
+                    // the stage's previous tile is finished: store it, and reuse the stage once the
+                    // store has read it
+                    if (!mbar_wait(&cdone[s], (unsigned)((t - UT_NST) / UT_NST) & 1u, &s_fail)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tma_store_2d(&mapC, px[s], py[s], sp + UT_TILE_Y);
+                    bulk_commit();
+                    bulk_wait_read();
+                }
+                const long long band = g / a.ntiles, ct = g % a.ntiles;
+                px[s] = (int)(band * UT_BM);
+                py[s] = (int)(ct * UT_BN);
+                mbar_expect_tx(&full[s], UT_STAGE);
+                tma_load_2d(sp, &mapY, 0, (int)(ct * 2 * UT_BN), &full[s]);
+                tma_load_2d(sp + UT_TILE_Y / 2, &mapY, 32, (int)(ct * 2 * UT_BN), &full[s]);
+                tma_load_2d(sp + UT_TILE_Y, &mapC, px[s], py[s], &full[s]);
+            }
+            if (ok) {
+                for (long long u = (t > UT_NST ? t - UT_NST : 0); u < t; ++u) {
+                    const int s = (int)(u % UT_NST);
+                    if (!mbar_wait(&cdone[s], (unsigned)(u / UT_NST) & 1u, &s_fail)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tma_store_2d(&mapC, px[s], py[s], stage_ptr(s) + UT_TILE_Y);
+                    bulk_commit();
+                }
+            }
+            bulk_wait_all();
+            if (!ok)  // loads still in flight (tiles t - UT_NST .. t - 1) land before the block leaves
+                for (long long u = (t > UT_NST ? t - UT_NST : 0); u < t; ++u)
+                    mbar_wait(&full[u % UT_NST], (unsigned)(u / UT_NST) & 1u, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(UT_BM, 2 * UT_BN);
+            long long t = 0, run = 0, prev_band = -1, issued = 0;
+            for (long long g = g0; g < g1; ++g, ++t) {
+                const long long band = g / a.ntiles;
+                if (band != prev_band) {
+                    if (!mbar_wait(&aready, (unsigned)(run & 1), &s_fail)) {
+                        fail();
+                        break;
+                    }
+                    ++run;
+                    prev_band = band;
+                }
+                const int s = (int)(t % UT_NST), b = (int)(t & 1);
+                if (!mbar_wait(&full[s], (unsigned)(t / UT_NST) & 1u, &s_fail) ||
+                    (t >= 2 && !mbar_wait(&accempty[b], (unsigned)((t - 2) >> 1) & 1u, &s_fail))) {
+                    fail();
+                    break;
+                }
+                fence_after();
+                const unsigned char* yt = stage_ptr(s);
+                const uint32_t td = tmem + (uint32_t)(b * 2 * UT_BN);
+                for (int kk = 0; kk < a.ksteps; ++kk)
+                    mma_tf32_ts(td, tA + 64 + 8 * kk, umma_desc(yt + (kk >> 2) * (UT_TILE_Y / 2) + (kk & 3) * 32), idesc,
+                                kk > 0 ? 1 : 0);
+                for (int kk = 0; kk < a.ksteps; ++kk)
+                    mma_tf32_ts(td, tA + 8 * kk, umma_desc(yt + (kk >> 2) * (UT_TILE_Y / 2) + (kk & 3) * 32), idesc, 1);
+                mma_commit(&accfull[b]);
+                issued = t + 1;
+            }
+            // every MMA chain completes before tensor memory is freed (bounded)
+            if (issued > 0)
+                mbar_wait(&accfull[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), nullptr);
+        }
+    } else {
+        const int q = warp & 3;         // tensor-memory lane quarter
+        const int h = (warp - 2) >> 2;  // 16-column quarter of the tile (and of V's 64 columns)
+        const int row = 32 * q + lane;  // row within the band
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        long long t = 0, prev_band = -1;
+        bool ok = true;
+        for (long long g = g0; g < g1; ++g, ++t) {
+            const long long band = g / a.ntiles;
+            if (band != prev_band) {
+                // A <- V's band: row band * 128 + row, columns 16h .. 16h + 15 (every MMA of the
+                // previous band has completed: this thread drained its last accumulator)
+                const long long r = band * UT_BM + row;
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int j = 16 * h + u;
+                    float v = 0.f;
+                    if (r < a.mr && j < a.kb) {
+                        v = V[(long long)j * ldv + r];
+                        if (r < a.maskV) {
+                            if (r < j) v = 0.f;
+                            else if (r == j) v = 1.f;
+                        }
+                    }
+                    const float hv = tf32_rn(v);
+                    hi[u] = __float_as_uint(hv);
+                    lo[u] = __float_as_uint(tf32_rn(v - hv));
+                }
+                const uint32_t ta = tA + lane_base + (uint32_t)(16 * h);
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                        ta),
+                    "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]),
+                    "r"(hi[8]), "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]), "r"(hi[15])
+                    : "memory");
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                        ta + 64),
+                    "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+                    "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]), "r"(lo[15])
+                    : "memory");
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&aready);
+                prev_band = band;
+            }
+            const int s = (int)(t % UT_NST), b = (int)(t & 1);
+            bool okw = mbar_wait(&accfull[b], (unsigned)(t >> 1) & 1u, &s_fail);
+            okw = okw && mbar_wait(&full[s], (unsigned)(t / UT_NST) & 1u, &s_fail);  // C tile visible here
+            if (!__all_sync(0xffffffffu, okw)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            uint32_t rh[16], rl[16];
+            const uint32_t td = tmem + lane_base + (uint32_t)(b * 2 * UT_BN + 16 * h);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(rh[0]), "=r"(rh[1]), "=r"(rh[2]), "=r"(rh[3]), "=r"(rh[4]), "=r"(rh[5]), "=r"(rh[6]), "=r"(rh[7]),
+                  "=r"(rh[8]), "=r"(rh[9]), "=r"(rh[10]), "=r"(rh[11]), "=r"(rh[12]), "=r"(rh[13]), "=r"(rh[14]),
+                  "=r"(rh[15])
+                : "r"(td));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(rl[0]), "=r"(rl[1]), "=r"(rl[2]), "=r"(rl[3]), "=r"(rl[4]), "=r"(rl[5]), "=r"(rl[6]), "=r"(rl[7]),
+                  "=r"(rl[8]), "=r"(rl[9]), "=r"(rl[10]), "=r"(rl[11]), "=r"(rl[12]), "=r"(rl[13]), "=r"(rl[14]),
+                  "=r"(rl[15])
+                : "r"(td + UT_BN));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[b]);
+            float* ctile = reinterpret_cast<float*>(stage_ptr(s) + UT_TILE_Y);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                float* x = ctile + (16 * h + u) * UT_BM + row;
+                *x = *x - (__uint_as_float(rl[u]) + __uint_as_float(rh[u]));
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cdone[s]);
+        }
+        if (!ok) fail();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) tmem_dealloc(tmem, UT_TMEM_COLS);
+}
+
+size_t ut_smem_bytes() { return 1024 + (size_t)UT_NST * UT_STAGE; }
+
+}  // namespace
+
+bool tc_update_supported(long long kb, long long ldc, const void* C)
+{
+    if (!(kb >= 1 && kb <= UT_KP && (ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tc_encoder_available())) return false;
+    static int fits = -1;
+    if (fits < 0) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, (const void*)update_tc_kernel) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        fits = ut_smem_bytes() + fa.sharedSizeBytes <= (size_t)dev_info().max_smem_optin ? 1 : 0;
+    }
+    return fits == 1;
+}
+
+size_t tc_update_ws_bytes(long long nt)
+{
+    return (size_t)((nt + UT_BN - 1) / UT_BN) * 2 * UT_BN * UT_KP * sizeof(float);
+}
+
+cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long long ldv, const double* Y, long long ldy,
+                                  long long mr, long long nt, int kb, long long maskV, float* ys, const Status* st,
+                                  cudaStream_t s)
+{
+    if (mr <= 0 || nt <= 0) return cudaSuccess;
+    if (((uintptr_t)ys % 16) != 0) return cudaErrorInvalidValue;
+    const long long ntiles = (nt + UT_BN - 1) / UT_BN;
+    {
+        const long long total = ntiles * UT_BN * UT_KP;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 4L * dev_info().sms) blocks = 4L * dev_info().sms;
+        ysplit_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, ldy, kb, nt, ntiles, ys, st);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    CUtensorMap mapC, mapY;
+    if (!tc_encode_2d(&mapC, C, mr, nt, ldc, UT_BM, UT_BN, false)) return cudaErrorInvalidValue;
+    if (!tc_encode_2d(&mapY, ys, UT_KP, ntiles * 2 * UT_BN, UT_KP, 32, 2 * UT_BN, true)) return cudaErrorInvalidValue;
+    UtArgs a;
+    a.mr = mr;
+    a.nt = nt;
+    a.kb = kb;
+    a.ksteps = (kb + 7) / 8;
+    a.maskV = maskV;
+    a.ntiles = ntiles;
+    a.total = ((mr + UT_BM - 1) / UT_BM) * ntiles;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaError_t e = allow_max_dynamic_smem(update_tc_kernel)) return e;
+        attr_set = true;
+    }
+    long long grid = dev_info().sms;
+    if (grid > a.total) grid = a.total;
+    update_tc_kernel<<<(unsigned)grid, UT_THREADS, ut_smem_bytes(), s>>>(mapC, mapY, V, ldv, a, const_cast<Status*>(st));
+    return cudaGetLastError();
+}
+
+}  // namespace rq
