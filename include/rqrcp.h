@@ -97,15 +97,29 @@ int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_
                             void* work, size_t work_bytes, void* stream);
 
 /*
- * Mixed form of Alg. 2: A is FP32 (lda >= m); the sketch, pivot search, trailing
- * updates and Eq. (4) run in FP32 arithmetic; every Householder reflector (column norm,
- * beta, tau) of the panel is generated in FP64 and tau is returned in FP64.  Arguments
- * and output layout as in rqrcp_factor; the rank guard uses 10*sqrt(max(m,n))*2^-24 in place
- * of 10*max(m,n)*2^-53 (about ten times the rounding noise of an FP32 sketch column).
+ * Mixed form of Alg. 2: A is FP32 (lda >= m).  The sketch B = Omega A (Alg. 2, the sketch
+ * step) is formed from Omega and A rounded to BF16 (round to nearest even) with FP32
+ * accumulation; the pivot search, the compact-WY trailing updates (TF32 hi/lo parts on the
+ * tensor cores, FP32-level accuracy) and Eq. (4) run in FP32 arithmetic; every Householder
+ * reflector (column norm, beta, tau) of the panel is generated in FP64 and tau is returned in
+ * FP64.  Arguments and output layout as in rqrcp_factor; the rank guard uses 2^-6 in place of
+ * 10*max(m,n)*2^-53 (about five times the relative noise BF16 rounding leaves in a sketch column:
+ * rank below that level is not resolved by this sketch).
  */
 int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
                        uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
                        void* stream);
+
+#define RQRCP_SKETCH_BF16 0 /* sketch operands rounded to BF16, FP32 accumulation */
+#define RQRCP_SKETCH_FP32 1 /* sketch with FP32-level accuracy (TF32 hi/lo parts, or FP32 FMA) */
+
+/* rqrcp_factor_mixed with the sketch precision chosen by `sketch` (RQRCP_SKETCH_*; any other
+ * value returns -9, later arguments shift by one).  RQRCP_SKETCH_BF16 is rqrcp_factor_mixed;
+ * RQRCP_SKETCH_FP32 uses the rank guard 10*sqrt(max(m,n))*2^-24 (about ten times the rounding
+ * noise of an FP32 sketch column). */
+int rqrcp_factor_mixed_ex(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                          uint64_t seed, int sketch, int32_t* jpvt, double* tau, void* work,
+                          size_t work_bytes, void* stream);
 
 /*
  * Synchronises `stream`, then reads the device-side status left in `work` by the last

@@ -70,6 +70,11 @@ def _load():
         lib.orc_rqrcp.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _i64, _dp, ctypes.c_int,
                                   _i32p, _dp, _i64p, _dp, _dp]
         lib.orc_rqrcp.restype = ctypes.c_int
+        lib.orc_rqrcp2.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _i64, _dp, ctypes.c_int, ctypes.c_int,
+                                   _i32p, _dp, _i64p, _dp, _dp]
+        lib.orc_rqrcp2.restype = ctypes.c_int
+        lib.orc_round_bf16.argtypes = [_i64, _dp, _dp]
+        lib.orc_round_bf16.restype = None
         lib.orc_form_q.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
         lib.orc_form_q.restype = None
         lib.orc_apply_q.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp]
@@ -128,10 +133,13 @@ class RQRCPResult:
         self.A, self.jpvt, self.tau, self.rank, self.gaps, self.B = A, jpvt, tau, rank, gaps, B
 
 
-def rqrcp(A: np.ndarray, k: int, b: int, p: int, Omega: np.ndarray, formula: int = 4) -> RQRCPResult:
+def rqrcp(A: np.ndarray, k: int, b: int, p: int, Omega: np.ndarray, formula: int = 4,
+          sketch_bf16: bool = False) -> RQRCPResult:
     """Alg. 2 (RQRCP) with the sketch Omega given explicitly (l x m, l = b + p).
 
     formula=4 updates B with Eq. (4) (Duersch-Gu), formula=5 with Eq. (5) (Martinsson et al.).
+    sketch_bf16: the mixed form's BF16 sketch (Omega and A rounded to FP32 then BF16 for the
+    initial B = Omega A only; exact products and FP64 sums).
     """
     lib = _load()
     Af = _fortran64(A)
@@ -145,17 +153,27 @@ def rqrcp(A: np.ndarray, k: int, b: int, p: int, Omega: np.ndarray, formula: int
     rank = np.zeros(1, dtype=np.int64)
     gaps = np.zeros(max(k, 1), dtype=np.float64)
     B = np.zeros((l, n), dtype=np.float64, order="F")
-    rc = lib.orc_rqrcp(m, n, _ptr(Af, ctypes.c_double), max(m, 1), k, b, p, _ptr(Om, ctypes.c_double),
-                       formula, _ptr(jpvt, ctypes.c_int32), _ptr(tau, ctypes.c_double),
-                       _ptr(rank, ctypes.c_int64), _ptr(gaps, ctypes.c_double), _ptr(B, ctypes.c_double))
+    rc = lib.orc_rqrcp2(m, n, _ptr(Af, ctypes.c_double), max(m, 1), k, b, p, _ptr(Om, ctypes.c_double),
+                        formula, 1 if sketch_bf16 else 0, _ptr(jpvt, ctypes.c_int32), _ptr(tau, ctypes.c_double),
+                        _ptr(rank, ctypes.c_int64), _ptr(gaps, ctypes.c_double), _ptr(B, ctypes.c_double))
     if rc != 0:
         raise ValueError(f"orc_rqrcp: error {rc}")
     return RQRCPResult(Af, jpvt, tau[:k], int(rank[0]), gaps[:k], B)
 
 
-def rqrcp_seeded(A: np.ndarray, k: int, b: int, p: int, seed: int, formula: int = 4) -> RQRCPResult:
+def rqrcp_seeded(A: np.ndarray, k: int, b: int, p: int, seed: int, formula: int = 4,
+                 sketch_bf16: bool = False) -> RQRCPResult:
     """Alg. 2 with Omega drawn from the seed by the oracle's own Philox generator."""
-    return rqrcp(A, k, b, p, omega(b + p, A.shape[0], seed), formula)
+    return rqrcp(A, k, b, p, omega(b + p, A.shape[0], seed), formula, sketch_bf16)
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Each element rounded to FP32, then to BF16 (round to nearest, ties to even), as FP64."""
+    lib = _load()
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(xa)
+    lib.orc_round_bf16(xa.size, _ptr(xa, ctypes.c_double), _ptr(out, ctypes.c_double))
+    return out
 
 
 # --------------------------------------------------------------------------- Q, R, low rank

@@ -29,6 +29,10 @@
  *    static boundaries and B is no longer updated.
  *  - if a diagonal entry of R11 is exactly zero the matching column of
  *    Omega_hat_11 is set to zero instead of dividing.
+ *  - BF16 sketch (the mixed form's sketch step, orc_rqrcp2 with sketch_bf16 = 1): every
+ *    element of Omega and of A is first rounded to FP32, then to BF16 (8 significant bits,
+ *    round to nearest, ties to even); the products and their sums are then formed exactly
+ *    as in the FP64 sketch.  Only the initial sketch sees the rounding.
  */
 #include <math.h>
 #include <stdint.h>
@@ -38,6 +42,29 @@
 #define ORC_EXPORT __attribute__((visibility("default")))
 
 #define AT(X, ld, i, j) (X)[(size_t)(j) * (size_t)(ld) + (size_t)(i)]
+
+/* ------------------------------------------------------------------------- */
+/* BF16 rounding from the format's definition: BF16 keeps the sign, the 8-bit  */
+/* exponent and the top 7 fraction bits of an IEEE single.  x is rounded to     */
+/* single first; the 16 dropped bits are rounded to nearest, ties to the even   */
+/* kept pattern.  Finite inputs below the BF16 overflow threshold only.         */
+/* ------------------------------------------------------------------------- */
+static double round_bf16(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    const uint32_t dropped = u & 0xFFFFu;
+    uint32_t kept = u & 0xFFFF0000u;
+    if (dropped > 0x8000u || (dropped == 0x8000u && (kept & 0x10000u))) kept += 0x10000u;
+    memcpy(&f, &kept, sizeof f);
+    return (double)f;
+}
+
+ORC_EXPORT void orc_round_bf16(int64_t n, const double* x, double* y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = round_bf16(x[i]);
+}
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x64-10 counter-based generator, from its published definition:      */
@@ -175,9 +202,21 @@ ORC_EXPORT int orc_qrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
 /* optional) receives B after the last block (formula 4: the transformed and    */
 /* updated sketch; formula 5: the permuted sketch Omega_bar_2 R22).             */
 /* ------------------------------------------------------------------------- */
+ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
+                          int64_t p, const double* Omega, int formula, int sketch_bf16, int32_t* jpvt,
+                          double* tau, int64_t* rank_out, double* gaps, double* Bout);
+
 ORC_EXPORT int orc_rqrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
                          int64_t p, const double* Omega, int formula, int32_t* jpvt, double* tau,
                          int64_t* rank_out, double* gaps, double* Bout)
+{
+    return orc_rqrcp2(m, n, A, lda, k, b, p, Omega, formula, 0, jpvt, tau, rank_out, gaps, Bout);
+}
+
+/* orc_rqrcp with the choice of sketch: sketch_bf16 = 0 the FP64 sketch, 1 the BF16 sketch.    */
+ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
+                          int64_t p, const double* Omega, int formula, int sketch_bf16, int32_t* jpvt,
+                          double* tau, int64_t* rank_out, double* gaps, double* Bout)
 {
     if (m < 1 || n < 1) return -1;
     if (lda < m) return -4;
@@ -197,14 +236,29 @@ ORC_EXPORT int orc_rqrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k
         memcpy(Ob, Omega, sizeof(double) * (size_t)(l * m));
     }
 
-    /* Alg. 2: B = Omega A, summed over q in increasing order. */
+    /* Alg. 2: B = Omega A, summed over q in increasing order (BF16 sketch: on the rounded
+       operands). */
+    if (sketch_bf16) {
+        double* Or = (double*)malloc(sizeof(double) * (size_t)(l * m));
+        if (!Or) { free(B); free(Bq); free(Wh); free(Ob); return 1; }
+        for (int64_t e = 0; e < l * m; ++e) Or[e] = round_bf16(Omega[e]);
 #pragma omp parallel for schedule(static)
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t r = 0; r < l; ++r) {
-            double s = 0.0;
-            for (int64_t q = 0; q < m; ++q) s += Omega[r * m + q] * AT(A, lda, q, j);
-            AT(B, l, r, j) = s;
-        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t r = 0; r < l; ++r) {
+                double s = 0.0;
+                for (int64_t q = 0; q < m; ++q) s += Or[r * m + q] * round_bf16(AT(A, lda, q, j));
+                AT(B, l, r, j) = s;
+            }
+        free(Or);
+    } else {
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t r = 0; r < l; ++r) {
+                double s = 0.0;
+                for (int64_t q = 0; q < m; ++q) s += Omega[r * m + q] * AT(A, lda, q, j);
+                AT(B, l, r, j) = s;
+            }
+    }
     for (int64_t j = 0; j < n; ++j) jpvt[j] = (int32_t)j;
     if (gaps) for (int64_t c = 0; c < k; ++c) gaps[c] = -1.0;
 

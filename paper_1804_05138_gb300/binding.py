@@ -24,11 +24,13 @@ RQRCP_ERR_WORKSPACE = 4
 RQRCP_ERR_UNSUPPORTED = 5
 RQRCP_PREC_FP64 = 0
 RQRCP_PREC_MIXED = 1
+RQRCP_SKETCH_BF16 = 0
+RQRCP_SKETCH_FP32 = 1
 
 # Every symbol include/rqrcp.h declares.
 ABI_SYMBOLS = (
     "rqrcp_error_string", "rqrcp_workspace_size", "rqrcp_generate_omega", "rqrcp_generate_omega_f32",
-    "rqrcp_sketch", "rqrcp_factor", "rqrcp_factor_with_omega", "rqrcp_factor_mixed",
+    "rqrcp_sketch", "rqrcp_factor", "rqrcp_factor_with_omega", "rqrcp_factor_mixed", "rqrcp_factor_mixed_ex",
     "rqrcp_read_status", "rqrcp_lowrank_workspace_size", "rqrcp_lowrank",
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
@@ -69,6 +71,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                        _vp, _vp, _sz, _vp]),
             "rqrcp_factor_mixed": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp,
                                                   _sz, _vp]),
+            "rqrcp_factor_mixed_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, ctypes.c_int, _vp,
+                                                     _vp, _vp, _sz, _vp]),
             "rqrcp_read_status": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
             "rqrcp_lowrank_workspace_size": (_sz, [_i64, _i64, _i64]),
             "rqrcp_lowrank": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
@@ -190,6 +194,12 @@ def rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
     m, n = A.shape
     return load().rqrcp_factor_mixed(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(work),
                                      work.numel(), _stream(stream))
+
+
+def rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream=None) -> int:
+    m, n = A.shape
+    return load().rqrcp_factor_mixed_ex(m, n, _ptr(A), _ld(A), k, b, p, seed, sketch, _ptr(jpvt), _ptr(tau),
+                                        _ptr(work), work.numel(), _stream(stream))
 
 
 def rqrcp_read_status(work, stream=None) -> tuple[int, int]:
@@ -321,7 +331,7 @@ class Factorization:
     k: int
 
 
-def _run_factor(A, k, b, p, seed, omega, mixed, work, stream):
+def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETCH_BF16):
     import torch
     m, n = A.shape
     dev = A.device
@@ -333,7 +343,7 @@ def _run_factor(A, k, b, p, seed, omega, mixed, work, stream):
     if work is None or work.numel() < need:
         work = workspace(need, dev)
     if mixed:
-        code = rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream)
+        code = rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream)
     elif omega is None:
         code = rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream)
     else:
@@ -358,15 +368,21 @@ def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=N
 
 
 def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,
-                 overwrite: bool = False) -> Factorization:
-    """Randomized QRCP of a float32 CUDA matrix (mixed form, FP64 reflectors)."""
+                 overwrite: bool = False, sketch: str = "bf16") -> Factorization:
+    """Randomized QRCP of a float32 CUDA matrix (mixed form, FP64 reflectors).
+
+    sketch: "bf16" (operands rounded to BF16, FP32 accumulation) or "fp32" (FP32-level sketch).
+    """
     import torch
     if A.dtype != torch.float32:
         raise TypeError("factor_mixed expects float32")
+    if sketch not in ("bf16", "fp32"):
+        raise ValueError("sketch must be 'bf16' or 'fp32'")
     Acm = colmajor(A)
     if not overwrite:
         Acm = Acm.t().clone().t()
-    return _run_factor(Acm, k, b, p, seed, None, True, work, stream)
+    return _run_factor(Acm, k, b, p, seed, None, True, work, stream,
+                       RQRCP_SKETCH_BF16 if sketch == "bf16" else RQRCP_SKETCH_FP32)
 
 
 def lowrank(f: Factorization, stream=None):

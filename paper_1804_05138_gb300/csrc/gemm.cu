@@ -11,12 +11,18 @@
 // Both contractions are K-major reads of column-major operands staged through shared
 // memory in 16-deep slices; each thread owns a 4x4 register tile strided by 16 so that
 // shared-memory reads are conflict-free and global reads are 128-byte coalesced.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace rq {
 namespace {
 
 constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+
+// Round to BF16 (round to nearest even) and back: the operand rounding of the BF16 sketch.
+__device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ double round_bf16(double v) { return v; }
 
 // Value of the reflector matrix V at (row q, column r) given the stored entry.
 template <typename T>
@@ -30,7 +36,7 @@ __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, in
                                                      const T* __restrict__ C, int64_t ldc, int64_t M,
                                                      int64_t N, int64_t K, int64_t kchunk,
                                                      double* __restrict__ P, int maskX, int64_t maskC,
-                                                     const Status* st)
+                                                     int bf16, const Status* st)
 {
     if (status_error(st)) return;
     __shared__ T Xs[TK][TM + 1];
@@ -62,6 +68,7 @@ __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, in
             if (q < kend && r < M) {
                 v = X[r * ldx + q];
                 if (maskX) v = vmask(v, q, r);
+                if (bf16) v = round_bf16(v);
             }
             Xs[kk][mm] = v;
         }
@@ -76,6 +83,7 @@ __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, in
             if (q < kend && c < N) {
                 v = C[c * ldc + q];
                 if (c < maskC) v = vmask(v, q, c);
+                if (bf16) v = round_bf16(v);
             }
             Cs[kk][nn] = v;
         }
@@ -293,11 +301,11 @@ __global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_
 template <typename T>
 cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int64_t M, int64_t N,
                            int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,
-                           const Status* st, cudaStream_t s)
+                           const Status* st, cudaStream_t s, int bf16)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((N + TN - 1) / TN), (unsigned)((K + kchunk - 1) / kchunk));
-    gemm_tn_kernel<T><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, st);
+    gemm_tn_kernel<T><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, bf16, st);
     return cudaGetLastError();
 }
 
@@ -357,7 +365,7 @@ cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t 
 #define RQ_INST(T)                                                                                   \
     template cudaError_t launch_gemm_tn<T>(const T*, int64_t, const T*, int64_t, int64_t, int64_t,  \
                                            int64_t, int64_t, double*, int, int64_t, const Status*,  \
-                                           cudaStream_t);                                           \
+                                           cudaStream_t, int);                                      \
     template cudaError_t launch_gemm_update<T>(T*, int64_t, const T*, int64_t, const double*,       \
                                                int64_t, int64_t, int64_t, int64_t, int,             \
                                                const int32_t*, const Status*, cudaStream_t);        \

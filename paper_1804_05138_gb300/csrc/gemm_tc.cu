@@ -52,6 +52,17 @@ __global__ void xsplit_kernel(const float* __restrict__ X, long long ldx, long l
     }
 }
 
+// BF16 form of xsplit_kernel: xb[r * ldk + q] = bf16(x) (round to nearest even); lines M <= r <
+// gridDim.y are zero.
+__global__ void xsplit_bf16_kernel(const float* __restrict__ X, long long ldx, long long K, int M, long long ldk,
+                                   __nv_bfloat16* __restrict__ xb, const Status* st)
+{
+    if (status_error(st)) return;
+    const long long r = blockIdx.y;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < K; q += (long long)gridDim.x * blockDim.x)
+        xb[r * ldk + q] = __float2bfloat16_rn(r < M ? X[r * ldx + q] : 0.f);
+}
+
 struct TcArgs {
     int M, Nb;               // rows of X used (<= Nb), MMA N (multiple of 16)
     long long N, K;          // columns of C, contraction length
@@ -80,20 +91,28 @@ struct TcArgs {
 //                      chunk (the small A_lo products first, so the accumulator of the large terms
 //                      rounds only the four hi*hi steps) once aready and accempty allow; commits to
 //                      empty[s] and accfull[kc % 2].
-template <int NBMAX>
+//
+// BF16 form (the sketch): 64-row chunks (two 32-row C boxes), A = the chunk rounded to BF16 (pairs
+// of rows packed per 32-bit tensor-memory column, 32 columns per buffer), X pre-rounded to BF16
+// (one Nb-row operand, 64 K per 128-byte row), four kind::f16 MMAs per chunk into an Nb-column
+// accumulator; no reflector mask.
+template <int NBMAX, bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tn_tc_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapX, TcArgs a,
                       double* __restrict__ P, Status* st)
 {
-    constexpr int CQ = NBMAX / 4;  // register columns per worker (a quarter of the MMA N)
+    constexpr int CQ = NBMAX / 4;          // register columns per worker (a quarter of the MMA N)
+    constexpr int KC = BF ? 64 : TC_KC;    // rows of C per chunk
+    constexpr int ACOLS = BF ? 32 : 64;    // tensor-memory columns of one A buffer
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = status_error(st);
     __syncthreads();
     if (s_skip) return;  // block-uniform: warp 1's tensor-memory allocation is warp-collective
     extern __shared__ unsigned char smraw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    const int tileC = TC_NA * TC_KC * 4;     // 16 KB
-    const int tileX = 2 * a.Nb * TC_KC * 4;  // [X_hi; X_lo]: 2 Nb rows of 128 bytes
+    const int tileC = TC_NA * KC * 4;                      // raw FP32 C chunk (16 or 32 KB)
+    const int tileX = (BF ? a.Nb : 2 * a.Nb) * 128;        // BF16 X, or [X_hi; X_lo]: rows of 128 bytes
+    const int dcols = BF ? a.Nb : 2 * a.Nb;                // MMA N = accumulator columns
     const int stage_bytes = tileC + tileX;
     const int nst = a.nst;
     __shared__ __align__(8) uint64_t full[TC_MAXST], empty[TC_MAXST], aready[2], accfull[2], accempty[2];
@@ -123,11 +142,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t tA = tmem + (uint32_t)(4 * a.Nb);  // D0, D1 (2 Nb columns each), then A0, A1 (64)
+    const uint32_t tA = tmem + (uint32_t)(2 * dcols);  // D0, D1 (dcols each), then A0, A1 (ACOLS each)
     const long long n0 = (long long)blockIdx.x * TC_NA;
     const long long kbeg = (long long)blockIdx.y * a.kchunk;
     const long long kend = min(a.K, kbeg + a.kchunk);
-    const int nchunks = (int)((kend - kbeg + TC_KC - 1) / TC_KC);
+    const int nchunks = (int)((kend - kbeg + KC - 1) / KC);
     auto stage_ptr = [&](int s) { return base + (size_t)s * stage_bytes; };
     auto fail = [&]() {
         s_fail = 1;
@@ -144,9 +163,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 unsigned char* sp = stage_ptr(s);
-                const int k0 = (int)(kbeg + (long long)kc * TC_KC);
+                const int k0 = (int)(kbeg + (long long)kc * KC);
                 mbar_expect_tx(&full[s], tileC + tileX);
                 tma_load_2d(sp, &mapC, k0, (int)n0, &full[s]);
+                if (BF) tma_load_2d(sp + tileC / 2, &mapC, k0 + 32, (int)n0, &full[s]);
                 tma_load_2d(sp + tileC, &mapX, k0, 0, &full[s]);
                 issued = kc + 1;
             }
@@ -156,7 +176,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(TC_NA, 2 * a.Nb);
+            const uint32_t idesc = BF ? idesc_bf16(TC_NA, a.Nb) : idesc_tf32(TC_NA, 2 * a.Nb);
             int issued = 0;
             for (int kc = 0; kc < nchunks; ++kc) {
                 const int s = kc % nst, b = kc & 1;
@@ -167,13 +187,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 fence_after();
                 const unsigned char* xt = stage_ptr(s) + tileC;
-                const uint32_t td = tmem + (uint32_t)(b * 2 * a.Nb);
-                const uint32_t ta = tA + (uint32_t)(b * 64);
+                const uint32_t td = tmem + (uint32_t)(b * dcols);
+                const uint32_t ta = tA + (uint32_t)(b * ACOLS);
+                if (BF) {
 #pragma unroll
-                for (int k = 0; k < TC_KC / 8; ++k)
-                    mma_tf32_ts(td, ta + 32 + 8 * k, umma_desc(xt + k * 32), idesc, k > 0 ? 1 : 0);
+                    for (int k = 0; k < 4; ++k) mma_bf16_ts(td, ta + 8 * k, umma_desc(xt + k * 32), idesc, k > 0 ? 1 : 0);
+                } else {
 #pragma unroll
-                for (int k = 0; k < TC_KC / 8; ++k) mma_tf32_ts(td, ta + 8 * k, umma_desc(xt + k * 32), idesc, 1);
+                    for (int k = 0; k < TC_KC / 8; ++k)
+                        mma_tf32_ts(td, ta + 32 + 8 * k, umma_desc(xt + k * 32), idesc, k > 0 ? 1 : 0);
+#pragma unroll
+                    for (int k = 0; k < TC_KC / 8; ++k) mma_tf32_ts(td, ta + 8 * k, umma_desc(xt + k * 32), idesc, 1);
+                }
                 mma_commit(&empty[s]);
                 mma_commit(&accfull[b]);
                 issued = kc + 1;
@@ -196,9 +221,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const bool ok = mbar_wait(&accfull[kc & 1], (unsigned)(kc >> 1) & 1u, &s_fail);
             if (!__all_sync(0xffffffffu, ok)) return false;
             fence_after();
-            // column j of this quarter: X_hi product at tb + j, X_lo product at tb + Nb + j;
-            // groups of up to 8 columns: all loads of a group in flight, one wait
-            const uint32_t tb = tmem + lane_base + (uint32_t)((kc & 1) * 2 * a.Nb + cb);
+            // column j of this quarter: X_hi product at tb + j, X_lo product at tb + Nb + j (BF16:
+            // the one product at tb + j); groups of up to 8 columns: all loads in flight, one wait
+            const uint32_t tb = tmem + lane_base + (uint32_t)((kc & 1) * dcols + cb);
 #pragma unroll
             for (int g0 = 0; g0 < CQ; g0 += 8) {
                 if (g0 < qc) {
@@ -209,9 +234,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                                          : "=r"(rh[c0]), "=r"(rh[c0 + 1]), "=r"(rh[c0 + 2]), "=r"(rh[c0 + 3])
                                          : "r"(tb + (uint32_t)(g0 + c0)));
-                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                                         : "=r"(rl[c0]), "=r"(rl[c0 + 1]), "=r"(rl[c0 + 2]), "=r"(rl[c0 + 3])
-                                         : "r"(tb + (uint32_t)(a.Nb + g0 + c0)));
+                            if (!BF)
+                                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                             : "=r"(rl[c0]), "=r"(rl[c0 + 1]), "=r"(rl[c0 + 2]), "=r"(rl[c0 + 3])
+                                             : "r"(tb + (uint32_t)(a.Nb + g0 + c0)));
                         }
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -220,7 +246,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (g0 + c0 < qc) {
 #pragma unroll
                             for (int u = 0; u < 4; ++u)
-                                acc[g0 + c0 + u] += __uint_as_float(rl[c0 + u]) + __uint_as_float(rh[c0 + u]);
+                                acc[g0 + c0 + u] += BF ? __uint_as_float(rh[c0 + u])
+                                                       : __uint_as_float(rl[c0 + u]) + __uint_as_float(rh[c0 + u]);
                         }
                     }
                 }
@@ -248,44 +275,65 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ok = false;
                 break;
             }
-            // this thread's 8 values: rows k0 + 8h .. k0 + 8h + 7 of column c, two swizzled
-            // 16-byte pieces of the tile's row `row`
             const unsigned char* tile = stage_ptr(s);
-            const int k0 = (int)(kbeg + (long long)kc * TC_KC);
-            float v[8];
+            const int k0 = (int)(kbeg + (long long)kc * KC);
+            if (BF) {
+                // rows 16h .. 16h + 15 of the chunk for column c: box h / 2, four swizzled 16-byte
+                // pieces of its row `row`; packed as BF16 pairs (even row in the low half)
+                const unsigned char* box = tile + (h >> 1) * (tileC / 2) + row * 128;
+                uint32_t pk[8];
 #pragma unroll
-            for (int pc = 0; pc < 2; ++pc) {
-                const int piece = (2 * h + pc) ^ (row & 7);
-                const float4 f = *reinterpret_cast<const float4*>(tile + row * 128 + piece * 16);
-                v[4 * pc] = f.x;
-                v[4 * pc + 1] = f.y;
-                v[4 * pc + 2] = f.z;
-                v[4 * pc + 3] = f.w;
-            }
-            if (c < a.maskC && k0 < a.maskC) {
+                for (int pc = 0; pc < 4; ++pc) {
+                    const int piece = (4 * (h & 1) + pc) ^ (row & 7);
+                    const float4 f = *reinterpret_cast<const float4*>(box + piece * 16);
+                    const __nv_bfloat162 p0 = __floats2bfloat162_rn(f.x, f.y);
+                    const __nv_bfloat162 p1 = __floats2bfloat162_rn(f.z, f.w);
+                    pk[2 * pc] = *reinterpret_cast<const uint32_t*>(&p0);
+                    pk[2 * pc + 1] = *reinterpret_cast<const uint32_t*>(&p1);
+                }
+                const uint32_t ta = tA + lane_base + (uint32_t)((kc & 1) * ACOLS + 8 * h);
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+                             "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3]), "r"(pk[4]), "r"(pk[5]), "r"(pk[6]),
+                             "r"(pk[7])
+                             : "memory");
+            } else {
+                // this thread's 8 values: rows k0 + 8h .. k0 + 8h + 7 of column c, two swizzled
+                // 16-byte pieces of the tile's row `row`
+                float v[8];
+#pragma unroll
+                for (int pc = 0; pc < 2; ++pc) {
+                    const int piece = (2 * h + pc) ^ (row & 7);
+                    const float4 f = *reinterpret_cast<const float4*>(tile + row * 128 + piece * 16);
+                    v[4 * pc] = f.x;
+                    v[4 * pc + 1] = f.y;
+                    v[4 * pc + 2] = f.z;
+                    v[4 * pc + 3] = f.w;
+                }
+                if (c < a.maskC && k0 < a.maskC) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const long long qq = (long long)k0 + 8 * h + u;
+                        if (qq < c) v[u] = 0.f;
+                        else if (qq == c) v[u] = 1.f;
+                    }
+                }
+                uint32_t hi[8], lo[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const long long qq = (long long)k0 + 8 * h + u;
-                    if (qq < c) v[u] = 0.f;
-                    else if (qq == c) v[u] = 1.f;
+                    const float hv = tf32_rn(v[u]);
+                    hi[u] = __float_as_uint(hv);
+                    lo[u] = __float_as_uint(tf32_rn(v[u] - hv));
                 }
+                const uint32_t ta = tA + lane_base + (uint32_t)((kc & 1) * ACOLS + 8 * h);
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+                             "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+                             "r"(hi[7])
+                             : "memory");
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta + 32),
+                             "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
+                             "r"(lo[7])
+                             : "memory");
             }
-            uint32_t hi[8], lo[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float hv = tf32_rn(v[u]);
-                hi[u] = __float_as_uint(hv);
-                lo[u] = __float_as_uint(tf32_rn(v[u] - hv));
-            }
-            const uint32_t ta = tA + lane_base + (uint32_t)((kc & 1) * 64 + 8 * h);
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
-                         "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
-                         "r"(hi[7])
-                         : "memory");
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta + 32),
-                         "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]),
-                         "r"(lo[7])
-                         : "memory");
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             fence_before();
             __syncwarp();
@@ -344,19 +392,20 @@ bool encode_map(CUtensorMap* map, const float* base, long long inner, long long 
     return tc_encode_2d(map, base, inner, outer, ld, TC_KC, box_outer, true);
 }
 
-size_t tc_smem_bytes(int Nb, int nst)
+size_t tc_smem_bytes(int Nb, int nst, bool bf)
 {
-    return 1024 + (size_t)nst * ((size_t)TC_NA * TC_KC * 4 + 2 * (size_t)Nb * TC_KC * 4);
+    const size_t stage = bf ? (size_t)TC_NA * 64 * 4 + (size_t)Nb * 128 : (size_t)TC_NA * TC_KC * 4 + 2 * (size_t)Nb * 128;
+    return 1024 + (size_t)nst * stage;
 }
 
 // Dynamic shared memory a kernel may use next to its static shared memory.
-template <int NBMAX>
+template <int NBMAX, bool BF>
 size_t tc_dyn_limit()
 {
     static size_t lim = 0;
     if (lim == 0) {
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, (const void*)gemm_tn_tc_kernel<NBMAX>) != cudaSuccess) {
+        if (cudaFuncGetAttributes(&fa, (const void*)gemm_tn_tc_kernel<NBMAX, BF>) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -365,17 +414,18 @@ size_t tc_dyn_limit()
     return lim;
 }
 
-size_t tc_dyn_limit_for(int Nb)
+size_t tc_dyn_limit_for(int Nb, bool bf)
 {
-    return Nb <= 32 ? tc_dyn_limit<32>() : Nb <= 64 ? tc_dyn_limit<64>() : tc_dyn_limit<96>();
+    if (bf) return Nb <= 32 ? tc_dyn_limit<32, true>() : Nb <= 64 ? tc_dyn_limit<64, true>() : tc_dyn_limit<96, true>();
+    return Nb <= 32 ? tc_dyn_limit<32, false>() : Nb <= 64 ? tc_dyn_limit<64, false>() : tc_dyn_limit<96, false>();
 }
 
 // Pipeline depth: TC_MAXST stages where they fit, else fewer (0: not even 2 fit).
-int tc_stages(int Nb)
+int tc_stages(int Nb, bool bf)
 {
-    const size_t lim = tc_dyn_limit_for(Nb);
+    const size_t lim = tc_dyn_limit_for(Nb, bf);
     for (int nst = TC_MAXST; nst >= 2; --nst)
-        if (tc_smem_bytes(Nb, nst) <= lim) return nst;
+        if (tc_smem_bytes(Nb, nst, bf) <= lim) return nst;
     return 0;
 }
 
@@ -386,23 +436,30 @@ bool tc_encoder_available() { return tensor_map_encoder() != nullptr; }
 bool tc_encode_2d(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld, int box_inner,
                   int box_outer, bool swizzle128)
 {
+    return tc_encode_2d_typed(map, base, 4, inner, outer, ld, box_inner, box_outer, swizzle128);
+}
+
+bool tc_encode_2d_typed(CUtensorMap* map, const void* base, int elem_bytes, long long inner, long long outer,
+                        long long ld, int box_inner, int box_outer, bool swizzle128)
+{
     auto enc = tensor_map_encoder();
-    if (enc == nullptr) return false;
+    if (enc == nullptr || (elem_bytes != 4 && elem_bytes != 2)) return false;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * elem_bytes};
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     cuuint32_t es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+    return enc(map, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               const_cast<void*>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                swizzle128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_gemm_supported(long long M, long long ldc, const void* C)
+bool tc_gemm_supported(long long M, long long ldc, const void* C, int bf16)
 {
     if (!(M >= 1 && M <= 96 && (ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tensor_map_encoder() != nullptr))
         return false;
-    return tc_stages((int)(((M + 15) / 16) * 16)) >= 2;
+    return tc_stages((int)(((M + 15) / 16) * 16), bf16 != 0) >= 2;
 }
 
 size_t tc_xsplit_bytes(long long M, long long K)
@@ -412,9 +469,10 @@ size_t tc_xsplit_bytes(long long M, long long K)
 
 // Split-K chunk for the tensor-core kernel (one resident block per SM): the split count S <= 16
 // minimising waves x (rows per split + a pipeline fill of about three chunks), splits of at
-// least 256 rows; a multiple of 32.
-long long tc_kchunk(long long N, long long K, int& nsplit)
+// least 256 rows; a multiple of the chunk height (32, or 64 for the BF16 form).
+long long tc_kchunk(long long N, long long K, int& nsplit, int bf16)
 {
+    const long long KC = bf16 ? 64 : TC_KC;
     const long long ntiles = (N + TC_NA - 1) / TC_NA;
     const long long sms = dev_info().sms;
     long long smax = (K + 255) / 256;
@@ -422,39 +480,50 @@ long long tc_kchunk(long long N, long long K, int& nsplit)
     if (smax < 1) smax = 1;
     long long best = 1, best_cost = -1;
     for (long long S = 1; S <= smax; ++S) {
-        const long long rows = ((K + S - 1) / S + TC_KC - 1) / TC_KC * TC_KC;
+        const long long rows = ((K + S - 1) / S + KC - 1) / KC * KC;
         const long long waves = (ntiles * S + sms - 1) / sms;
-        const long long cost = waves * (rows + 3 * TC_KC);
+        const long long cost = waves * (rows + 3 * KC);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best = S;
         }
     }
     long long kc = (K + best - 1) / best;
-    kc = ((kc + TC_KC - 1) / TC_KC) * TC_KC;
+    kc = ((kc + KC - 1) / KC) * KC;
     nsplit = (int)((K + kc - 1) / kc);
     return kc;
 }
 
 cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
                               long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
-                              const Status* st, cudaStream_t s)
+                              const Status* st, cudaStream_t s, int bf16)
 {
+    const bool bf = bf16 != 0;
     const int Nb = (int)(((M + 15) / 16) * 16);
-    const int nst = tc_stages(Nb);
-    if (nst < 2 || ((uintptr_t)xs % 16) != 0) return cudaErrorInvalidValue;
-    const long long ldk = (K + 3) / 4 * 4;
-    float* xh = xs;  // Nb lines of ldk (lines M.. zero), then the lo parts
-    float* xl = xs + (size_t)Nb * ldk;
+    const int nst = tc_stages(Nb, bf);
+    if (nst < 2 || ((uintptr_t)xs % 16) != 0 || (bf && (maskX != 0 || maskC != 0))) return cudaErrorInvalidValue;
+    CUtensorMap mapC, mapX;
     {
         long long gx = (K + 255) / 256;
         if (gx > 64) gx = 64;
-        xsplit_kernel<<<dim3((unsigned)gx, (unsigned)Nb), 256, 0, s>>>(X, ldx, K, (int)M, maskX, ldk, xh, xl, st);
-        if (cudaError_t e = cudaGetLastError()) return e;
+        if (bf) {
+            // Nb lines of ldk BF16 values (lines M.. zero)
+            const long long ldk = (K + 7) / 8 * 8;
+            __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(xs);
+            xsplit_bf16_kernel<<<dim3((unsigned)gx, (unsigned)Nb), 256, 0, s>>>(X, ldx, K, (int)M, ldk, xb, st);
+            if (cudaError_t e = cudaGetLastError()) return e;
+            if (!tc_encode_2d_typed(&mapX, xb, 2, K, Nb, ldk, 64, Nb, true)) return cudaErrorInvalidValue;
+        } else {
+            // Nb lines of ldk FP32 hi parts (lines M.. zero), then the lo parts: [X_hi; X_lo]
+            const long long ldk = (K + 3) / 4 * 4;
+            float* xh = xs;
+            float* xl = xs + (size_t)Nb * ldk;
+            xsplit_kernel<<<dim3((unsigned)gx, (unsigned)Nb), 256, 0, s>>>(X, ldx, K, (int)M, maskX, ldk, xh, xl, st);
+            if (cudaError_t e = cudaGetLastError()) return e;
+            if (!encode_map(&mapX, xh, K, 2 * Nb, ldk, 2 * Nb)) return cudaErrorInvalidValue;
+        }
     }
-    CUtensorMap mapC, mapX;
     if (!encode_map(&mapC, C, K, N, ldc, TC_NA)) return cudaErrorInvalidValue;
-    if (!encode_map(&mapX, xh, K, 2 * Nb, ldk, 2 * Nb)) return cudaErrorInvalidValue;  // [X_hi; X_lo]
     TcArgs a;
     a.M = (int)M;
     a.Nb = Nb;
@@ -464,9 +533,10 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
     a.maskC = maskC;
     a.nst = nst;
     unsigned cols = 32;
-    while ((int)cols < 4 * Nb + 128) cols <<= 1;  // D0, D1, A0, A1
+    const int need = bf ? 2 * Nb + 64 : 4 * Nb + 128;  // D0, D1, A0, A1
+    while ((int)cols < need) cols <<= 1;
     a.tmem_cols = cols;
-    const size_t smem = tc_smem_bytes(Nb, nst);
+    const size_t smem = tc_smem_bytes(Nb, nst, bf);
     dim3 grid((unsigned)((N + TC_NA - 1) / TC_NA), (unsigned)((K + kchunk - 1) / kchunk));
     auto run = [&](auto kern, bool& attr_set) -> cudaError_t {
         if (!attr_set) {
@@ -476,10 +546,15 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
         kern<<<grid, TC_THREADS, smem, s>>>(mapC, mapX, a, P, const_cast<Status*>(st));
         return cudaGetLastError();
     };
-    static bool set32 = false, set64 = false, set96 = false;
-    if (Nb <= 32) return run(gemm_tn_tc_kernel<32>, set32);
-    if (Nb <= 64) return run(gemm_tn_tc_kernel<64>, set64);
-    return run(gemm_tn_tc_kernel<96>, set96);
+    static bool set[6] = {false, false, false, false, false, false};
+    if (bf) {
+        if (Nb <= 32) return run(gemm_tn_tc_kernel<32, true>, set[3]);
+        if (Nb <= 64) return run(gemm_tn_tc_kernel<64, true>, set[4]);
+        return run(gemm_tn_tc_kernel<96, true>, set[5]);
+    }
+    if (Nb <= 32) return run(gemm_tn_tc_kernel<32, false>, set[0]);
+    if (Nb <= 64) return run(gemm_tn_tc_kernel<64, false>, set[1]);
+    return run(gemm_tn_tc_kernel<96, false>, set[2]);
 }
 
 }  // namespace rq

@@ -111,23 +111,26 @@ cudaError_t launch_omega(int64_t l, int64_t m, uint64_t seed, T* Om, int64_t ldo
 // Split-K partial products P[sp][c][r] = sum_{q in chunk sp} X(q, r) * C(q, c), r < M, c < N.
 // X is K x M column-major (ldx), C is K x N column-major (ldc).  maskX: X has the unit-lower
 // reflector structure (X(q,r) = 0 for q < r, 1 for q == r).  maskC: the first maskC columns
-// of C have the same structure.  kchunk must be a multiple of 16.
+// of C have the same structure.  kchunk must be a multiple of 16.  bf16 (FP32 only): both operands
+// are rounded to BF16 (round to nearest even) as they are read (the BF16 sketch).
 template <typename T>
 cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int64_t M, int64_t N,
                            int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,
-                           const Status* st, cudaStream_t s);
+                           const Status* st, cudaStream_t s, int bf16 = 0);
 
 // Tensor-core (tcgen05 kind::tf32, 3xTF32) split-K contraction with the output of
 // launch_gemm_tn<float>: X(q, r) = X[r * ldx + q] (q < K, r < M; unit-lower reflector structure
 // for r < maskX), C(q, c) = C[c * ldc + q] (c < N; the structure for c < maskC).  C must be
 // 16-byte aligned with ldc % 4 == 0 (tc_gemm_supported); xs (16-byte aligned,
-// tc_xsplit_bytes(M, K)) receives the TF32 parts of X.  kchunk must come from tc_kchunk.
-bool tc_gemm_supported(long long M, long long ldc, const void* C);
+// tc_xsplit_bytes(M, K)) receives the TF32 parts of X.  kchunk must come from tc_kchunk with
+// the same bf16 flag.  bf16: both operands rounded to BF16 (round to nearest even), products on
+// the kind::f16 tensor path with FP32 accumulation (the BF16 sketch; no reflector masks).
+bool tc_gemm_supported(long long M, long long ldc, const void* C, int bf16 = 0);
 size_t tc_xsplit_bytes(long long M, long long K);
-long long tc_kchunk(long long N, long long K, int& nsplit);
+long long tc_kchunk(long long N, long long K, int& nsplit, int bf16 = 0);
 cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
                               long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
-                              const Status* st, cudaStream_t s);
+                              const Status* st, cudaStream_t s, int bf16 = 0);
 // Tensor-core (tcgen05 kind::tf32, 3xTF32) form of launch_gemm_update<float> without colmap:
 // C(mr x nt) -= V(mr x kb) Y(kb x nt), kb <= 64, V unit-lower for rows r < maskV.  C must be
 // 16-byte aligned with ldc % 4 == 0 (tc_update_supported); ys (16-byte aligned,

@@ -144,7 +144,7 @@ int check_work(void* work, size_t work_bytes, size_t need)
 template <typename T>
 int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, int64_t p, uint64_t seed,
                 const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
-                cudaStream_t s)
+                cudaStream_t s, int sketch_bf16 = 0)
 {
     const int64_t l = b + p;
     const Layout L = make_layout(m, n, b, p, sizeof(T));
@@ -177,24 +177,30 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     {
         int ns;
         int64_t kc;
-        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(l, lda, (const void*)A);
+        // FP32 form: the BF16 sketch (operands rounded to BF16, FP32 accumulation) or the
+        // FP32-accurate one; both on the tensor cores when the layout allows
+        const int bf = sizeof(T) == 4 && sketch_bf16 ? 1 : 0;
+        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(l, lda, (const void*)A, bf);
         if (tc) {
-            kc = tc_kchunk(n, m, ns);
+            kc = tc_kchunk(n, m, ns, bf);
             RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
                       launch_gemm_tn_tc((const float*)Omega, ldo, (const float*)A, lda, l, n, m, kc, P, 0, 0,
-                                        reinterpret_cast<float*>(w + L.xs), st, s));
+                                        reinterpret_cast<float*>(w + L.xs), st, s, bf));
         } else {
             choose_split(l, n, m, ns, kc);
             RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
-                      launch_gemm_tn<T>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s));
+                      launch_gemm_tn<T>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s, bf));
         }
         RQ_LAUNCH(K_SKETCH_REDUCE, 0, (double)ns * l * n * 8 + (double)l * n * es,
                   launch_sketch_reduce<T>(P, ns, l, n, B, l, st, s));
     }
     // guard tolerance: 10 max(m,n) u for FP64 (the oracle's reading); FP32 storage uses
-    // 10 sqrt(max(m,n)) u, about ten times the rounding noise of an FP32 sketch column
+    // 10 sqrt(max(m,n)) u, about ten times the rounding noise of an FP32 sketch column; the BF16
+    // sketch 2^-6, about five times the 2^-8.5 relative noise its operand rounding leaves in a
+    // sketch column
     const double mn = (double)(m > n ? m : n);
-    const double gtol = 10.0 * (sizeof(T) == 8 ? mn : sqrt(mn)) * Prec<T>::unit_roundoff;
+    const double gtol = (sizeof(T) == 4 && sketch_bf16) ? ldexp(1.0, -6)
+                                                        : 10.0 * (sizeof(T) == 8 ? mn : sqrt(mn)) * Prec<T>::unit_roundoff;
     const double guard_rel2 = gtol * gtol;
     for (int64_t i = 0; i < k; i += b) {
         const int bb = (int)(b < k - i ? b : k - i);
@@ -436,7 +442,18 @@ __attribute__((visibility("default"))) int rqrcp_factor_mixed(int64_t m, int64_t
 {
     if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e;
     return factor_impl<float>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
-                              (cudaStream_t)stream);
+                              (cudaStream_t)stream, 1);
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_mixed_ex(int64_t m, int64_t n, float* A, int64_t lda,
+                                                                 int64_t k, int64_t b, int64_t p, uint64_t seed,
+                                                                 int sketch, int32_t* jpvt, double* tau, void* work,
+                                                                 size_t work_bytes, void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 1 : e;
+    if (sketch != RQRCP_SKETCH_BF16 && sketch != RQRCP_SKETCH_FP32) return -9;
+    return factor_impl<float>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
+                              (cudaStream_t)stream, sketch == RQRCP_SKETCH_BF16 ? 1 : 0);
 }
 
 __attribute__((visibility("default"))) int rqrcp_read_status(const void* work, int64_t* rank, void* stream)

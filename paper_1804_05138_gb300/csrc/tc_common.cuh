@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 
 #include "internal.cuh"
 
@@ -70,6 +71,21 @@ __device__ __forceinline__ uint32_t idesc_tf32(int m, int n)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+// Instruction descriptor: D FP32, A and B BF16, both K-major, N >> 3, M >> 4.
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// A (M x K BF16, lane m = row m, two consecutive K elements per 32-bit column, the lower index in
+// the low half) in tensor memory, B in shared memory; K = 16 per instruction.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc, int acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(
+            tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
 // A (M x K, lane m = row m, one TF32 element per 32-bit column) in tensor memory, B in shared memory.
 __device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc, int acc)
 {
@@ -124,6 +140,9 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t tmem, unsigned cols)
 // encoder is unavailable or rejects the map.
 bool tc_encode_2d(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld, int box_inner,
                   int box_outer, bool swizzle128);
+// The same for FP32 (elem_bytes 4) or BF16 (elem_bytes 2) elements; ld in elements.
+bool tc_encode_2d_typed(CUtensorMap* map, const void* base, int elem_bytes, long long inner, long long outer,
+                        long long ld, int box_inner, int box_outer, bool swizzle128);
 bool tc_encoder_available();
 
 }  // namespace rq

@@ -5,8 +5,9 @@ The error against the FP64 oracle is stated per result:
   * ||R22||_2 >= sigma_{k+1} (interlacing) and no worse than max(2, 1.1 x the FP64 oracle's
     own ratio) (the 2 sigma_{k+1} target is statistical: the oracle itself reaches 1.6-2.5 on
     these spectra with these oversamplings);
-  * pivots identical to the oracle's up to the first step where the oracle's top-two sketch
-    norms are within 1e-4 relative (an FP32 sketch resolves only gaps well above 2^-24);
+  * pivots identical to the oracle's (run with the same sketch reading: BF16-rounded operands
+    or the exact sketch) up to the first step where the oracle's top-two sketch norms are within
+    1e-4 relative (FP32 accumulation resolves only gaps well above 2^-24);
   * R within 1e-5 normwise of the oracle's R when all pivots agree.
 """
 import numpy as np
@@ -33,17 +34,19 @@ def _f32_gpu(A, gpu):
     return gpu.colmajor(torch.from_numpy(np.asfortranarray(A)).to("cuda").float())
 
 
+@pytest.mark.parametrize("sketch", ["bf16", "fp32"])
 @pytest.mark.parametrize("m,n,k,b,p,scale", [
     (1000, 1000, 64, 32, 8, 100.0),
     (2048, 1536, 200, 64, 16, 200.0),
     (777, 500, 130, 32, 16, 60.0),
     (4096, 256, 256, 64, 16, 40.0),
 ])
-def test_mixed_against_oracle(gpu, orc, m, n, k, b, p, scale):
+def test_mixed_against_oracle(gpu, orc, m, n, k, b, p, scale, sketch):
     A0 = inputs.spectrum_matrix(m, n, inputs.sigma_exp_decay(min(m, n), scale))
     A32 = A0.astype(np.float32).astype(np.float64)          # the matrix the mixed form sees
-    ref = orc.rqrcp_seeded(A32, k, b, p, seed=0)
-    f = gpu.factor_mixed(_f32_gpu(A0, gpu), k, b, p, seed=0)
+    # the oracle with the same sketch reading: BF16-rounded operands, or the exact sketch
+    ref = orc.rqrcp_seeded(A32, k, b, p, seed=0, sketch_bf16=(sketch == "bf16"))
+    f = gpu.factor_mixed(_f32_gpu(A0, gpu), k, b, p, seed=0, sketch=sketch)
     Af = f.A.cpu().double().numpy()
     jp = f.jpvt.cpu().numpy()
     tau = f.tau.cpu().numpy()
@@ -64,10 +67,11 @@ def test_mixed_against_oracle(gpu, orc, m, n, k, b, p, scale):
         assert 1.0 - 1e-4 <= ratio <= max(2.0, 1.1 * ratio_o), (ratio, ratio_o)
 
 
-def test_mixed_rank_deficient_guard(gpu, orc):
+@pytest.mark.parametrize("sketch", ["bf16", "fp32"])
+def test_mixed_rank_deficient_guard(gpu, orc, sketch):
     m, n, r, k, b, p = 600, 500, 40, 200, 32, 8
     A0 = inputs.rank_r_product(m, n, r)
-    f = gpu.factor_mixed(_f32_gpu(A0, gpu), k, b, p, seed=0)
+    f = gpu.factor_mixed(_f32_gpu(A0, gpu), k, b, p, seed=0, sketch=sketch)
     assert f.rank == r
     R = orc.r_factor(f.A.cpu().double().numpy(), k)
     assert np.linalg.norm(R[r:, r:]) / np.linalg.norm(A0) < 1e-5

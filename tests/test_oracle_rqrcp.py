@@ -192,3 +192,50 @@ def test_argument_errors(orc):
         orc.rqrcp(A, 5, 2, 1, inputs.gaussian_sketch(3, 5, 0))   # k > min(m, n)
     with pytest.raises(ValueError):
         orc.rqrcp(A, 0, 2, 1, inputs.gaussian_sketch(3, 5, 0))   # k < 1
+
+
+# ------------------------------------------------------------------------------ P11
+# The mixed form's BF16 sketch, the oracle's reading of it: Omega and A rounded to FP32, then to
+# BF16 (round to nearest, ties to even) for the initial sketch only.
+def test_round_bf16_matches_library_conversion(orc):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = np.concatenate([
+        rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000),
+        # exact ties between two BF16 neighbours (even and odd kept patterns), and near-ties
+        1.0 + np.array([1, 3, 5, 7]) * 2.0 ** -8, -(2.0 + np.array([1, 3]) * 2.0 ** -7),
+        1.0 + 2.0 ** -8 + np.array([2.0 ** -20, -2.0 ** -20]),
+        [0.0, -0.0, 1e-40, -3e-39],                   # zeros and FP32 subnormals
+    ])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    got = orc.round_bf16(x)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(orc.round_bf16(got), got)  # BF16 values are fixed points
+
+
+def test_bf16_sketch_is_identity_on_bf16_inputs(orc):
+    # inputs already representable in BF16: the rounding is the identity, so the BF16-sketch
+    # oracle must reproduce the FP64-sketch oracle bit for bit
+    m, n, k, b, p = 120, 90, 40, 16, 6
+    A = orc.round_bf16(inputs.spectrum_matrix(m, n, inputs.sigma_exp_decay(n, 30.0)))
+    Om = orc.round_bf16(inputs.gaussian_sketch(b + p, m, seed=4))
+    r64 = orc.rqrcp(A, k, b, p, Om)
+    r16 = orc.rqrcp(A, k, b, p, Om, sketch_bf16=True)
+    assert np.array_equal(r64.jpvt, r16.jpvt)
+    assert np.array_equal(r64.A, r16.A)
+    assert np.array_equal(r64.tau, r16.tau)
+
+
+def test_bf16_sketch_changes_only_pivot_choice(orc):
+    # the rounding only steers pivots: the factorization stays backward stable, and where the
+    # sketch norms are well separated the pivots agree with the FP64 sketch
+    m, n, k, b, p = 300, 200, 60, 20, 10
+    A = inputs.spectrum_matrix(m, n, inputs.sigma_exp_decay(n, 40.0))
+    Om = inputs.gaussian_sketch(b + p, m, seed=5)
+    r64 = orc.rqrcp(A, k, b, p, Om)
+    r16 = orc.rqrcp(A, k, b, p, Om, sketch_bf16=True)
+    assert orc.rel_residual(A, r16.A, r16.tau, r16.jpvt, k) < 1e-14
+    sep = r64.gaps >= 1e-2  # BF16 moves the sketch norms by ~1e-3 relative
+    upto = k if sep.all() else int(np.argmin(sep))
+    assert upto >= 1
+    assert np.array_equal(r64.jpvt[:upto], r16.jpvt[:upto])
