@@ -50,6 +50,9 @@ WORKLOADS = {
                         desc="batched RQRCP: 512 FP32 matrices, m~U[256,4096], n~U[128,min(m,2048)], "
                              "k~U[16,256], sigma_i = exp(-i/(0.1 n)), p=8, b per shape from the autotuner, "
                              "one persistent launch replayed from a CUDA graph"),
+    "mixed_16384x8192_k128": dict(m=16384, n=8192, k=128, b=64, p=16, kind="expspec200", prec="mixed",
+                                  desc="mixed partial RQRCP k=128 on 16384x8192 FP32 U diag(exp(-i/200)) V^T, "
+                                       "b=64, p=16 (profiling size)"),
     "mixed_32768x16384_k512": dict(m=32768, n=16384, k=512, b=64, p=16, kind="expspec200", prec="mixed",
                                    desc="mixed partial RQRCP k=512 on 32768x16384 FP32 U diag(exp(-i/200)) V^T, "
                                         "b=64, p=16"),
@@ -63,6 +66,33 @@ FP64_NOMINAL_TFLOPS = 1.25
 # by the launch's algorithmic bytes, on the 4096^2 FP64 capture summarised in
 # profiles/gemm_fp64_4096_wy_kernels.md; scaled to a full launch by the algorithmic bytes.
 MEASURED_TRAFFIC_RATIO = {"fp64": {"wy_gemm_tn": 1.028, "wy_update": 0.604}}
+
+
+# Roofline of each kernel class.  FP64 form: the SIMT contractions run on the DFMA pipe; the
+# tensor-core contractions of the FP32 form stream A once per launch and are bound by HBM; the
+# remaining kernels (pivot search, panel QR, small reductions, swaps) are latency-bound chains of
+# grid-wide steps, reported against HBM for their algorithmic bytes.
+ALU_CLASSES = {"fp64": {"sketch_gemm", "wy_gemm_tn", "wy_update"}, "mixed": set()}
+
+
+def kernel_rooflines(prof, prec, hbm_peak_gbs):
+    """Per kernel class: time, share, launches and the roofline fraction against its bound."""
+    total = sum(v["ms"] for v in prof.values()) or 1e-9
+    table = {}
+    for name, v in prof.items():
+        if not v["launches"] or v["ms"] <= 0:
+            continue
+        row = {"launches": v["launches"], "ms": round(v["ms"], 4), "share": round(v["ms"] / total, 4)}
+        if name in ALU_CLASSES.get(prec, set()):
+            ach = v["flops"] / (v["ms"] * 1e-3) / 1e12
+            row.update(bound="alu", achieved=round(ach, 4), peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s",
+                       frac=round(ach / FP64_NOMINAL_TFLOPS, 4))
+        else:
+            ach = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+            row.update(bound="hbm", achieved=round(ach, 2), peak=hbm_peak_gbs, unit="GB/s",
+                       frac=round(ach / hbm_peak_gbs, 4))
+        table[name] = row
+    return table
 
 
 def counted_flops(m, n, k, l):
@@ -298,14 +328,21 @@ def run_ours(args, w, rank, world, local_rank):
     dname, d = dom
     launches_total = sum(v["launches"] for v in prof.values())
     kernels_per_launch_class = {"swap": 2, "bupdate": 2}
+    if mixed:  # tensor-core contractions: an operand-splitting kernel, then the contraction
+        kernels_per_launch_class.update({"sketch_gemm": 2, "wy_gemm_tn": 2, "wy_update": 2})
     gpu_launches = sum(v["launches"] * kernels_per_launch_class.get(kname, 1) for kname, v in prof.items())
     gpu_launches += args.steps  # status/jpvt init kernel, one per factorization
     achieved_tflops = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    peaks = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (copy, measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    kernels = kernel_rooflines(prof, "mixed" if mixed else "fp64", hbm_peak)
     if mixed:
-        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max clock
-        roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp32_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp32_peak, 4), "traffic": None,
-                "kernel": dname, "peak_source": "FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+        # every kernel of the FP32 form is bound by memory traffic or by latency: HBM roofline
+        kr = kernels.get(dname, {})
+        roof = {"bound": "hbm", "achieved": kr.get("achieved"), "peak": hbm_peak, "unit": "GB/s",
+                "frac": kr.get("frac"), "traffic": None, "kernel": dname, "peak_source": hbm_src + ", of measured",
+                "algorithmic_bytes_per_launch": round(d["bytes"] / max(1, d["launches"]))}
     else:
         ratio = MEASURED_TRAFFIC_RATIO["fp64"].get(dname)
         traffic = None
@@ -362,6 +399,38 @@ def run_ours(args, w, rank, world, local_rank):
            "ms_per_step": round(e2e_ms, 3)}
 
     extra = {}
+    if not diff and not args.no_other_form:
+        # the other form on the same matrix: plain FP64 for the mixed workload, mixed for FP64
+        other = "fp64" if mixed else "mixed"
+        Ao = binding.colmajor(A0.double() if other == "fp64" else A0.float())
+        Aw = torch.empty_like(Ao.t()).t()
+        jo = torch.empty(n, dtype=torch.int32, device=dev)
+        to = torch.empty(k, dtype=torch.float64, device=dev)
+        wo = binding.workspace(binding.rqrcp_workspace_size(
+            m, n, k, b, p, binding.RQRCP_PREC_FP64 if other == "fp64" else binding.RQRCP_PREC_MIXED), dev)
+        co = binding.rqrcp_factor if other == "fp64" else binding.rqrcp_factor_mixed
+        times = []
+        for it in range(3):
+            Aw.copy_(Ao)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            code = co(Aw, k, b, p, 0, jo, to, wo)
+            e1.record(stream)
+            if code != 0:
+                raise binding.RQRCPError(code, "factor (other form)")
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(e0.elapsed_time(e1))
+        code, _ = binding.rqrcp_read_status(wo)
+        if code != 0:
+            raise binding.RQRCPError(code, "device status (other form)")
+        oms = sum(times) / len(times)
+        fp64_ms, mixed_ms = (oms, ms_per_step) if other == "fp64" else (ms_per_step, oms)
+        extra["same_problem"] = {"form": other, "ms_per_step": round(oms, 3),
+                                 "plain_fp64_ms": round(fp64_ms, 3), "mixed_ms": round(mixed_ms, 3),
+                                 "mixed_speedup": round(fp64_ms / mixed_ms, 3),
+                                 "sketch": "bf16"}
+        del Ao, Aw, wo
     if mixed and not diff:
         # FP64 Q1 / R of the factorization just timed, with the CholQR pass forced (tol = 0)
         Q1 = torch.empty((k, m), dtype=torch.float64, device=dev).t()
@@ -395,6 +464,7 @@ def run_ours(args, w, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single", "rank_out": rank_out},
         "roofline": roof,
         "kernel_time_share": kernel_share,
+        "kernels": kernels,
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
@@ -523,6 +593,8 @@ def main():
     ap.add_argument("--workload", default="fp64_8192_iid", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-form", action="store_true",
+                    help="skip timing the other form (mixed / plain FP64) on the same matrix")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
