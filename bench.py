@@ -75,14 +75,21 @@ MEASURED_TRAFFIC_RATIO = {"fp64": {"wy_gemm_tn": 1.028, "wy_update": 0.604}}
 ALU_CLASSES = {"fp64": {"sketch_gemm", "wy_gemm_tn", "wy_update"}, "mixed": set()}
 
 
-def kernel_rooflines(prof, prec, hbm_peak_gbs):
-    """Per kernel class: time, share, launches and the roofline fraction against its bound."""
+LATENCY_CLASSES = {"pivot", "panel"}  # one grid-wide step per pivot / per panel column
+
+
+def kernel_rooflines(prof, prec, hbm_peak_gbs, steps_per_launch=None):
+    """Per kernel class: time, share, launches and the roofline fraction against its bound;
+    the latency-bound classes report microseconds per grid-wide step (steps_per_launch = the
+    mean block width bb) next to their HBM fraction."""
     total = sum(v["ms"] for v in prof.values()) or 1e-9
     table = {}
     for name, v in prof.items():
         if not v["launches"] or v["ms"] <= 0:
             continue
         row = {"launches": v["launches"], "ms": round(v["ms"], 4), "share": round(v["ms"] / total, 4)}
+        if name in LATENCY_CLASSES and steps_per_launch:
+            row["us_per_step"] = round(1e3 * v["ms"] / (v["launches"] * steps_per_launch), 3)
         if name in ALU_CLASSES.get(prec, set()):
             ach = v["flops"] / (v["ms"] * 1e-3) / 1e12
             row.update(bound="alu", achieved=round(ach, 4), peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s",
@@ -336,7 +343,7 @@ def run_ours(args, w, rank, world, local_rank):
     peaks = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (copy, measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
-    kernels = kernel_rooflines(prof, "mixed" if mixed else "fp64", hbm_peak)
+    kernels = kernel_rooflines(prof, "mixed" if mixed else "fp64", hbm_peak, steps_per_launch=k / ((k + b - 1) // b))
     if mixed:
         # every kernel of the FP32 form is bound by memory traffic or by latency: HBM roofline
         kr = kernels.get(dname, {})
