@@ -269,10 +269,15 @@ __global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_
 {
     if (status_error(st)) return;
     extern __shared__ double sm[];
-    double* Ts = sm;                      // bb x bb
+    // Ts[q * ldT + r] = op(T)(r, q): lanes (r) read consecutive words
+    const int ldT = bb | 1;
+    double* Ts = sm;                      // bb x ldT
     const int nw = blockDim.x / 32;
-    double* Wsh = sm + bb * bb;           // nw x bb
-    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Ts[e] = Tm[e];
+    double* Wsh = sm + (size_t)bb * ldT;  // nw x bb
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
+        const int r = e % bb, q = e / bb;  // T column-major: T(a, b) = Tm[b * bb + a]
+        Ts[q * ldT + r] = transT ? Tm[r * bb + q] : Tm[q * bb + r];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double* Wc = Wsh + w * bb;
@@ -287,9 +292,9 @@ __global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_
         for (int r = lane; r < bb; r += 32) {
             double s = 0.0;
             if (transT)
-                for (int q = 0; q <= r; ++q) s += Ts[r * bb + q] * Wc[q];
+                for (int q = 0; q <= r; ++q) s += Ts[q * ldT + r] * Wc[q];
             else
-                for (int q = r; q < bb; ++q) s += Ts[q * bb + r] * Wc[q];
+                for (int q = r; q < bb; ++q) s += Ts[q * ldT + r] * Wc[q];
             Y[c * bb + r] = s;
         }
         __syncwarp();
@@ -349,7 +354,7 @@ cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t 
 {
     if (nc <= 0) return cudaSuccess;
     const int threads = 256, nw = threads / 32;
-    const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)nw * bb);
+    const size_t smem = sizeof(double) * ((size_t)bb * (bb | 1) + (size_t)nw * bb);
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(reduce_y_kernel)) return e;

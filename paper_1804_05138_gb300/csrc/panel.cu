@@ -24,6 +24,27 @@ __host__ __device__ inline int pow2_at_least(int x)
     return p;
 }
 
+// Sum of p[h * stride] for h = start, start + step, ... < G in increasing h, with up to 40 loads
+// in flight before their additions (the partials sit in L2 and every block reads all of them:
+// one round trip instead of one per few loads).  Same order, so the same value, in every block.
+__device__ __forceinline__ double sum_partials(const double* p, int G, int start, int step, size_t stride)
+{
+    constexpr int U = 40;
+    double s = 0.0;
+    for (int h0 = start; h0 < G; h0 += U * step) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int h = h0 + u * step;
+            v[u] = h < G ? ld_cg(p + (size_t)h * stride) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (h0 + u * step < G) s += v[u];
+    }
+    return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t lda, int64_t m1, int bb,
                                                     int64_t rpb, double* __restrict__ tau,
@@ -77,10 +98,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
         //    column, then the nchunk group sums are added in group order: identical in every block)
         {
             double s = 0.0;
-            if (kidx < nk) {
-#pragma unroll 8
-                for (int h = chunk; h < G; h += nchunk) s += ld_cg(&part[((size_t)buf * G + h) * bb + kidx]);
-            }
+            if (kidx < nk) s = sum_partials(part + (size_t)buf * G * bb + kidx, G, chunk, nchunk, (size_t)bb);
             red[chunk * bbp + kidx] = s;
             if (tid < nk) dg[tid] = ld_cg(&diag[(size_t)buf * bb + tid]);
         }
@@ -195,10 +213,7 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
         if (!grid_barrier(st)) return;
         {
             double sv = 0.0;
-            if (kidx < nk) {
-#pragma unroll 8
-                for (int h = chunk; h < G; h += nchunk) sv += ld_cg(&part[((size_t)buf * G + h) * bb + kidx]);
-            }
+            if (kidx < nk) sv = sum_partials(part + (size_t)buf * G * bb + kidx, G, chunk, nchunk, (size_t)bb);
             red[chunk * bbp + kidx] = sv;
             if (tid < nk) dg[tid] = ld_cg(&diag[(size_t)buf * bb + tid]);
         }

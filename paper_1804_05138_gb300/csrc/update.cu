@@ -86,25 +86,69 @@ __global__ void bsolve_kernel(const T* __restrict__ B, int64_t ldb, const T* __r
     for (int j = threadIdx.x; j < bb; j += blockDim.x) What[(int64_t)j * bb + r] = (j < r) ? 0.0 : Wr[j - r];
 }
 
-// B(r, c) -= sum_{q >= r} What(r, q) * A(i+q, c) for the trailing columns c.
+// B(r, c) -= sum_{q >= r} What(r, q) * A(i+q, c) for the trailing columns c (the top bb rows of
+// Eq. (4)), in T arithmetic.  One block per 64 trailing columns: the R12 tile A(i:i+bb, c0:c0+64)
+// and B's top rows land in shared memory with coalesced column reads; Omega_hat_11 (zero below
+// its diagonal) is staged as T, 64 of its rows at a time; every thread owns a 4 x 4 register
+// tile (rows tm + 16 a, columns tn + 16 b) and runs the contraction over q >= the chunk's first
+// row, the zeros taking the rest of the triangle.
 template <typename T>
-__global__ void bapply_kernel(T* __restrict__ B, int64_t ldb, const T* __restrict__ A, int64_t lda,
-                              int64_t i, int bb, int64_t n, const double* __restrict__ What, const Status* st)
+__global__ void __launch_bounds__(256) bapply_kernel(T* __restrict__ B, int64_t ldb, const T* __restrict__ A,
+                                                     int64_t lda, int64_t i, int bb, int64_t n,
+                                                     const double* __restrict__ What, const Status* st)
 {
     if (status_error(st) || *(volatile const int*)&st->guard) return;
-    extern __shared__ double Ws[];  // bb x bb column-major
-    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Ws[e] = What[e];
+    constexpr int TC = 64;                        // columns per block, and rows per What chunk
+    constexpr int LD = TC + 1;                    // padded row stride of the A and B tiles
+    extern __shared__ __align__(16) unsigned char smb[];
+    T* As = reinterpret_cast<T*>(smb);            // [q][c]: A(i+q, c0+c), bb x LD
+    T* Bs = As + (size_t)bb * LD;                 // [r][c]: B(r, c0+c),   bb x LD
+    T* Ws = Bs + (size_t)bb * LD;                 // [q][r - r0]: What(r, q), bb x TC
+    const int tid = threadIdx.x;
+    const int64_t c0 = i + bb + (int64_t)blockIdx.x * TC;
+    const int nc = (int)min((int64_t)TC, n - c0);
+    for (int e = tid; e < bb * TC; e += blockDim.x) {
+        const int q = e % bb, c = e / bb;         // consecutive threads read one column: coalesced
+        const bool in = c < nc;
+        As[(size_t)q * LD + c] = in ? A[(c0 + c) * lda + i + q] : T(0);
+        Bs[(size_t)q * LD + c] = in ? B[(c0 + c) * ldb + q] : T(0);
+    }
+    const int tm = tid & 15, tn = tid >> 4;
+    for (int r0 = 0; r0 < bb; r0 += TC) {
+        __syncthreads();
+        for (int e = tid; e < bb * TC; e += blockDim.x) {
+            const int rr = e % TC, q = e / TC;    // What is column-major: What[q * bb + r]
+            Ws[e] = r0 + rr < bb ? (T)What[(size_t)q * bb + r0 + rr] : T(0);
+        }
+        __syncthreads();
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+        for (int q = r0; q < bb; ++q) {           // What(r, q) = 0 for q < r
+            T w[4], x[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) w[a] = Ws[(size_t)q * TC + tm + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) x[b] = As[(size_t)q * LD + tn + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(w[a], x[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int r = r0 + tm + 16 * a;
+            if (r < bb)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) Bs[(size_t)r * LD + tn + 16 * b] -= acc[a][b];
+        }
+    }
     __syncthreads();
-    const int64_t c0 = i + bb + (int64_t)blockIdx.x * 64;
-    const int64_t c1 = min(n, c0 + 64);
-    const int64_t total = (c1 - c0) * bb;
-    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-        const int r = (int)(e % bb);
-        const int64_t c = c0 + e / bb;
-        const T* a = A + c * lda + i;
-        double acc = (double)B[c * ldb + r];
-        for (int q = r; q < bb; ++q) acc -= Ws[q * bb + r] * (double)a[q];
-        B[c * ldb + r] = (T)acc;
+    for (int e = tid; e < bb * TC; e += blockDim.x) {
+        const int q = e % bb, c = e / bb;
+        if (c < nc) B[(c0 + c) * ldb + q] = Bs[(size_t)q * LD + c];
     }
 }
 
@@ -144,7 +188,9 @@ cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i
     const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)bb);
     bsolve_kernel<T><<<bb, 128, smem, s>>>(B, ldb, A, lda, i, bb, What, st);
     const int64_t nt = n - i - bb;
-    if (nt > 0) bapply_kernel<T><<<(unsigned)((nt + 63) / 64), 256, smem, s>>>(B, ldb, A, lda, i, bb, n, What, st);
+    const size_t smem_apply = sizeof(T) * (size_t)bb * (2 * 65 + 64);
+    if (nt > 0)
+        bapply_kernel<T><<<(unsigned)((nt + 63) / 64), 256, smem_apply, s>>>(B, ldb, A, lda, i, bb, n, What, st);
     return cudaGetLastError();
 }
 
