@@ -226,6 +226,19 @@ __device__ void blk_gemm_update(float* C, long long ldc, const float* V, long lo
         }
 }
 
+// Order key of a squared norm: non-negative doubles order as their bit patterns read as signed
+// 64-bit integers and negative values map below them, so the compares stay off the FP64 pipe.
+__device__ __forceinline__ long long nkey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b < 0 ? -1LL : b;
+}
+__device__ __forceinline__ bool beats(double v1, long long p1, double v2, long long p2)
+{
+    const long long k1 = nkey(v1), k2 = nkey(v2);
+    return k1 > k2 || (k1 == k2 && p1 < p2);
+}
+
 // argmax over (value, position), ties to the smaller position; result broadcast via sm.sc/lpos.
 __device__ void blk_argmax(double v, long long p, const Smem& sm, double& bv, long long& bp)
 {
@@ -234,7 +247,7 @@ __device__ void blk_argmax(double v, long long p, const Smem& sm, double& bv, lo
     for (int o = 16; o > 0; o >>= 1) {
         const double ov = __shfl_xor_sync(0xffffffffu, v, o);
         const long long op = __shfl_xor_sync(0xffffffffu, p, o);
-        if (ov > v || (ov == v && op < p)) { v = ov; p = op; }
+        if (beats(ov, op, v, p)) { v = ov; p = op; }
     }
     if (lane == 0) { sm.red[w] = v; sm.lpos[w] = p; }
     __syncthreads();
@@ -242,7 +255,7 @@ __device__ void blk_argmax(double v, long long p, const Smem& sm, double& bv, lo
         double vb = sm.red[0];
         long long pb = sm.lpos[0];
         for (int ww = 1; ww < NW; ++ww)
-            if (sm.red[ww] > vb || (sm.red[ww] == vb && sm.lpos[ww] < pb)) { vb = sm.red[ww]; pb = sm.lpos[ww]; }
+            if (beats(sm.red[ww], sm.lpos[ww], vb, pb)) { vb = sm.red[ww]; pb = sm.lpos[ww]; }
         sm.sc[8] = vb;
         sm.lpos[NW] = pb;
     }
@@ -272,7 +285,7 @@ __device__ int blk_pivot(float* B, long long n, int l, long long i, int bb, int3
         double mv = -1.0;
         long long mp = 0x7fffffffffffffffLL;
         for (long long c = c0 + tid; c < n; c += BT)
-            if (sm.nu[c] > mv || (sm.nu[c] == mv && c < mp)) { mv = sm.nu[c]; mp = c; }
+            if (beats(sm.nu[c], c, mv, mp)) { mv = sm.nu[c]; mp = c; }
         double bv;
         long long j;
         blk_argmax(mv, mp, sm, bv, j);

@@ -24,15 +24,25 @@ namespace {
 
 constexpr int kMaxCand = 1024;  // maximum blocks of the cooperative launch
 
-__device__ __forceinline__ bool better(double v1, long long p1, double v2, long long p2)
+// Order key of a squared norm: non-negative doubles order as their bit patterns read as signed
+// 64-bit integers, and every negative value (the "no candidate" -1.0) maps below them.  Integer
+// compares keep the argmax off the FP64 pipe; the order is that of the values.
+__device__ __forceinline__ long long norm_key(double v)
 {
-    return v1 > v2 || (v1 == v2 && p1 < p2);
+    const long long b = __double_as_longlong(v);
+    return b < 0 ? -1LL : b;
 }
 
-// Block-wide argmax over (value, position) pairs; result broadcast through shared memory.
-__device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long long* sp, int* si)
+__device__ __forceinline__ bool better(double v1, long long p1, double v2, long long p2)
 {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const long long k1 = norm_key(v1), k2 = norm_key(v2);
+    return k1 > k2 || (k1 == k2 && p1 < p2);
+}
+
+// Warp-wide argmax over (value, position, index) triples by shuffles; every lane ends with the
+// warp's winner.
+__device__ __forceinline__ void warp_argmax(double& v, long long& p, int& idx)
+{
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -40,15 +50,26 @@ __device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (better(ov, op, v, p)) { v = ov; p = op; idx = oi; }
     }
-    __syncthreads();
+}
+
+// Block-wide argmax: warp shuffles, then warp 0 reduces the warps' winners (slots 0..31 of the
+// shared arrays); the result goes through slot 32, which the next call writes only after its
+// first barrier, so every thread has read it by then.
+__device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long long* sp, int* si)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_argmax(v, p, idx);
     if (lane == 0) { sv[w] = v; sp[w] = p; si[w] = idx; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < nw; ++k)
-            if (better(sv[k], sp[k], sv[0], sp[0])) { sv[0] = sv[k]; sp[0] = sp[k]; si[0] = si[k]; }
+    if (w == 0) {
+        double vv = lane < nw ? sv[lane] : -1.0;
+        long long pp = lane < nw ? sp[lane] : LLONG_MAX;
+        int ii = lane < nw ? si[lane] : -1;
+        warp_argmax(vv, pp, ii);
+        if (lane == 0) { sv[32] = vv; sp[32] = pp; si[32] = ii; }
     }
     __syncthreads();
-    v = sv[0]; p = sp[0]; idx = si[0];
+    v = sv[32]; p = sp[32]; idx = si[32];
 }
 
 // Per-column reduction over the TPC threads that share a column (adjacent lanes).
@@ -92,9 +113,9 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     off += (size_t)cpb * sizeof(int);
     double* nus = reinterpret_cast<double*>(smem_raw + ((off + 7) & ~(size_t)7));
 
-    __shared__ double red_v[32];
-    __shared__ long long red_p[32];
-    __shared__ int red_i[32];
+    __shared__ double red_v[33];
+    __shared__ long long red_p[33];
+    __shared__ int red_i[33];
     __shared__ double sh_tau, sh_beta, sh_scal;
 
     const int64_t nprime = n - i;
@@ -150,16 +171,32 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
                 ccol[((size_t)buf * kMaxCand + g) * l + r] = cols[(size_t)mys * ldS + r];
         // 2. barrier
         if (!grid_barrier(st)) return;
-        // 3. global winner (identical in every block)
-        double wv = -1.0;
-        long long wp = LLONG_MAX;
-        int wg = -1;
-        for (int h = tid; h < G; h += NTH) {
-            const double v = ld_cg(&cval[buf * kMaxCand + h]);
-            const long long p = ld_cg(&cpos[buf * kMaxCand + h]);
-            if (better(v, p, wv, wp)) { wv = v; wp = p; wg = h; }
+        // 3. global winner (identical in every block): warp 0 reads the G candidates, eight
+        //    per lane in flight at a time, and reduces them; slot 32 broadcasts the result
+        if (tid < 32) {
+            double wv = -1.0;
+            long long wp = LLONG_MAX;
+            int wg = -1;
+            for (int h0 = tid; h0 < G; h0 += 8 * 32) {
+                double vv[8];
+                long long pp[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int h = h0 + 32 * u;
+                    vv[u] = h < G ? ld_cg(&cval[buf * kMaxCand + h]) : -1.0;
+                    pp[u] = h < G ? ld_cg(&cpos[buf * kMaxCand + h]) : LLONG_MAX;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (better(vv[u], pp[u], wv, wp)) { wv = vv[u]; wp = pp[u]; wg = h0 + 32 * u; }
+            }
+            warp_argmax(wv, wp, wg);
+            if (tid == 0) { red_v[32] = wv; red_p[32] = wp; red_i[32] = wg; }
         }
-        block_argmax(wv, wp, wg, red_v, red_p, red_i);
+        __syncthreads();
+        const double wv = red_v[32];
+        const long long wp = red_p[32];
+        const int wg = red_i[32];
         if (!(wv > guard)) {  // also catches "no candidate" (-1) and NaN
             if (g == 0 && tid == 0) {
                 st->guard = 1;
