@@ -303,6 +303,24 @@ __global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_
 
 }  // namespace
 
+int gemm_tn_blocks_per_sm(int elem_bytes)
+{
+    static int occ[2] = {0, 0};
+    const int idx = elem_bytes == 8 ? 0 : 1;
+    if (occ[idx] == 0) {
+        int v = 0;
+        const cudaError_t e = elem_bytes == 8
+                                  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_tn_kernel<double>, NT, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_tn_kernel<float>, NT, 0);
+        if (e != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        occ[idx] = v;
+    }
+    return occ[idx];
+}
+
 template <typename T>
 cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int64_t M, int64_t N,
                            int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,

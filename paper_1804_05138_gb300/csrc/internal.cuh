@@ -118,6 +118,10 @@ cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int
                            int64_t K, int64_t kchunk, double* P, int maskX, int64_t maskC,
                            const Status* st, cudaStream_t s, int bf16 = 0);
 
+// Blocks of the SIMT split-K contraction (launch_gemm_tn) resident per SM for FP64 (8) or FP32 (4)
+// elements.
+int gemm_tn_blocks_per_sm(int elem_bytes);
+
 // Tensor-core (tcgen05 kind::tf32, 3xTF32) split-K contraction with the output of
 // launch_gemm_tn<float>: X(q, r) = X[r * ldx + q] (q < K, r < M; unit-lower reflector structure
 // for r < maskX), C(q, c) = C[c * ldc + q] (c < N; the structure for c < maskC).  C must be

@@ -91,17 +91,27 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     return L;
 }
 
-// Split-K factor for an M x N result contracted over K: about four blocks per SM.
-void choose_split(int64_t M, int64_t N, int64_t K, int& nsplit, int64_t& kchunk)
+// Split-K factor for an M x N result contracted over K on the SIMT contraction (64 x 64 tiles):
+// the split count S <= kMaxSplit minimising waves x (rows per split + a fixed cost of 64 rows),
+// a wave being the blocks resident on the whole GPU at once; splits of at least 64 rows.
+void choose_split(int64_t M, int64_t N, int64_t K, int& nsplit, int64_t& kchunk, int elem_bytes = 8)
 {
     const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
-    const int64_t target = 4 * (int64_t)dev_info().sms;
-    int64_t S = (target + tiles - 1) / tiles;
-    if (S < 1) S = 1;
-    if (S > kMaxSplit) S = kMaxSplit;
-    const int64_t maxS = (K + 63) / 64;
-    if (S > maxS) S = maxS < 1 ? 1 : maxS;
-    kchunk = (K + S - 1) / S;
+    const int64_t wave = (int64_t)gemm_tn_blocks_per_sm(elem_bytes) * dev_info().sms;
+    int64_t smax = (K + 63) / 64;
+    if (smax > kMaxSplit) smax = kMaxSplit;
+    if (smax < 1) smax = 1;
+    int64_t best = 1, best_cost = -1;
+    for (int64_t S = 1; S <= smax; ++S) {
+        const int64_t rows = ((K + S - 1) / S + 15) / 16 * 16;
+        const int64_t waves = (tiles * S + wave - 1) / wave;
+        const int64_t cost = waves * (rows + 64);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = S;
+        }
+    }
+    kchunk = (K + best - 1) / best;
     kchunk = ((kchunk + 15) / 16) * 16;
     nsplit = (int)((K + kchunk - 1) / kchunk);
 }
@@ -187,7 +197,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
                       launch_gemm_tn_tc((const float*)Omega, ldo, (const float*)A, lda, l, n, m, kc, P, 0, 0,
                                         reinterpret_cast<float*>(w + L.xs), st, s, bf));
         } else {
-            choose_split(l, n, m, ns, kc);
+            choose_split(l, n, m, ns, kc, (int)sizeof(T));
             RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
                       launch_gemm_tn<T>(Omega, ldo, A, lda, l, n, m, kc, P, 0, 0, st, s, bf));
         }
@@ -223,7 +233,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
                       launch_gemm_tn_tc((const float*)Vp, lda, (const float*)Vp, lda, bb, n - i, mr, kc, P, bb, bb,
                                         reinterpret_cast<float*>(w + L.xs), st, s));
         } else {
-            choose_split(bb, n - i, mr, ns, kc);
+            choose_split(bb, n - i, mr, ns, kc, (int)sizeof(T));
             RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
                       launch_gemm_tn<T>(Vp, lda, Vp, lda, bb, n - i, mr, kc, P, 1, bb, st, s));
         }
@@ -308,11 +318,11 @@ int lowrank_impl(int64_t m, int64_t n, int64_t k, const T* Afact, int64_t ldaf, 
         const int64_t mr = m - i;
         int ns;
         int64_t kc;
-        choose_split(kb, kb, mr, ns, kc);
+        choose_split(kb, kb, mr, ns, kc, (int)sizeof(T));
         RQ_CHECK(launch_gemm_tn<T>(Vp, ldaf, Vp, ldaf, kb, kb, mr, kc, P, 1, kb, st, s));
         RQ_CHECK(launch_tform(P, ns, kb, kb, tau + i, Tm, st, s));
         const int64_t nq = k - i;  // columns of Q1 touched by this block: i..k-1
-        choose_split(kb, nq, mr, ns, kc);
+        choose_split(kb, nq, mr, ns, kc, (int)sizeof(T));
         RQ_CHECK(launch_gemm_tn<T>(Vp, ldaf, Q1 + i * ldq + i, ldq, kb, nq, mr, kc, P, 1, 0, st, s));
         RQ_CHECK(launch_reduce_y(P, ns, nq, 0, kb, Tm, 0, Y, nq, st, s));
         RQ_CHECK(launch_gemm_update<T>(Q1 + i * ldq + i, ldq, Vp, ldaf, Y, kb, mr, nq, kb, 1, nullptr, st, s));
