@@ -30,7 +30,6 @@ constexpr int BT = 512;          // threads per block
 constexpr int NW = BT / 32;      // warps
 constexpr int SW = 8;            // sub-panel width of the panel factorization
 constexpr int kTile = 64;        // GEMM tile edge
-constexpr int kKs = 32;          // K slice of the TN contraction
 constexpr int kKu = 64;          // largest K of the update contraction (b <= 64)
 constexpr int kLdT = kTile + 1;  // padded shared-memory tile stride
 
@@ -84,65 +83,85 @@ __device__ void block_sum(double (&v)[NV], double* red, double* out)
 
 // Out(M x N) = X^T C; X is K x M (ldx), C is K x N (ldc), column-major.  maskX / maskC: unit-
 // lower reflector structure of X / of the first maskC columns of C.  out_rowmajor stores
-// Out(r, c) at r*ldo + c, else at c*ldo + r.  K is consumed in 32-deep slices; the next slice
-// is fetched into registers while the current one is multiplied out of shared memory.  Two
-// slices (64 terms) are summed in FP32 and folded into a compensated (TwoSum) total.
-__device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
-                            long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
-                            const Smem& sm)
+// Out(r, c) at r*ldo + c, else at c*ldo + r.  Output tiles are RT x CT (RT * CT = 4096: 16 x 256,
+// 32 x 128 or 64 x 64, the smallest RT >= M when M <= 32, so a short X wastes no rows); every
+// thread owns 4 rows x 2 columns.  K is consumed in KS-deep slices; the next slice is fetched into
+// registers while the current one is multiplied out of shared memory.  Up to 64 terms are summed
+// in FP32 and folded into a compensated (TwoSum) total.
+template <int RT>
+__device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
+                               long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
+                               const Smem& sm)
 {
-    constexpr int PER = (kKs * kTile) / BT;  // elements per thread per operand and slice
-    const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;  // tn in 0..31
-    for (long long m0 = 0; m0 < M; m0 += kTile)
-        for (long long n0 = 0; n0 < N; n0 += kTile) {
-            float acc[4][2], hi[4][2], lo[4][2], xr[PER], cr[PER];
+    constexpr int CT = 4096 / RT;
+    constexpr int KS = RT == 16 ? 16 : 32;
+    constexpr int LX = RT + 1, LC = CT + 1;
+    constexpr int PX = (KS * RT + BT - 1) / BT, PC = (KS * CT) / BT;
+    constexpr int FOLD = 64 / KS;  // slices per FP32 partial sum
+    static_assert(KS * (LX + LC) <= 2 * kKu * kLdT, "tiles exceed the shared-memory GEMM region");
+    float* Xs = sm.Xs;            // KS x LX
+    float* Cs = sm.Xs + KS * LX;  // KS x LC (the Xs/Cs region is contiguous)
+    const int tid = threadIdx.x, tm = tid % (RT / 4), tn = tid / (RT / 4);
+    for (long long m0 = 0; m0 < M; m0 += RT)
+        for (long long n0 = 0; n0 < N; n0 += CT) {
+            float acc[4][2], hi[4][2], lo[4][2], xr[PX], cr[PC];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
             auto fetch = [&](long long k0) {
 #pragma unroll
-                for (int it = 0; it < PER; ++it) {
-                    const int e = tid + it * BT, kk = e & (kKs - 1), mm = e / kKs;
-                    const long long q = k0 + kk, r = m0 + mm, c = n0 + mm;
-                    float xv = 0.f, cv = 0.f;
-                    if (q < K && r < M) {
+                for (int it = 0; it < PX; ++it) {
+                    const int e = tid + it * BT, kk = e % KS, mm = e / KS;
+                    const long long q = k0 + kk, r = m0 + mm;
+                    float xv = 0.f;
+                    if (e < KS * RT && q < K && r < M) {
                         xv = X[r * ldx + q];
                         if (maskX) xv = vmask_f(xv, q, r);
                     }
+                    xr[it] = xv;
+                }
+#pragma unroll
+                for (int it = 0; it < PC; ++it) {
+                    const int e = tid + it * BT, kk = e % KS, mm = e / KS;
+                    const long long q = k0 + kk, c = n0 + mm;
+                    float cv = 0.f;
                     if (q < K && c < N) {
                         cv = C[c * ldc + q];
                         if (c < maskC) cv = vmask_f(cv, q, c);
                     }
-                    xr[it] = xv;
                     cr[it] = cv;
                 }
             };
             fetch(0);
             int slice = 0;
-            for (long long k0 = 0; k0 < K; k0 += kKs) {
+            for (long long k0 = 0; k0 < K; k0 += KS) {
 #pragma unroll
-                for (int it = 0; it < PER; ++it) {
-                    const int e = tid + it * BT, kk = e & (kKs - 1), mm = e / kKs;
-                    sm.Xs[kk * kLdT + mm] = xr[it];
-                    sm.Cs[kk * kLdT + mm] = cr[it];
+                for (int it = 0; it < PX; ++it) {
+                    const int e = tid + it * BT;
+                    if (e < KS * RT) Xs[(e % KS) * LX + e / KS] = xr[it];
+                }
+#pragma unroll
+                for (int it = 0; it < PC; ++it) {
+                    const int e = tid + it * BT;
+                    Cs[(e % KS) * LC + e / KS] = cr[it];
                 }
                 __syncthreads();
-                if (k0 + kKs < K) fetch(k0 + kKs);
+                if (k0 + KS < K) fetch(k0 + KS);
 #pragma unroll 8
-                for (int kk = 0; kk < kKs; ++kk) {
+                for (int kk = 0; kk < KS; ++kk) {
                     float xa[4], cb[2];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) xa[a] = sm.Xs[kk * kLdT + tm + 16 * a];
+                    for (int a = 0; a < 4; ++a) xa[a] = Xs[kk * LX + tm + (RT / 4) * a];
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) cb[b] = sm.Cs[kk * kLdT + tn + 32 * b];
+                    for (int b = 0; b < 2; ++b) cb[b] = Cs[kk * LC + tn + (CT / 2) * b];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
                         for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(xa[a], cb[b], acc[a][b]);
                 }
                 __syncthreads();
-                if (++slice == 2) {
+                if (++slice == FOLD) {
                     slice = 0;
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
@@ -158,7 +177,7 @@ __device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const floa
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     two_sum_acc(hi[a][b], lo[a][b], acc[a][b]);
-                    const long long r = m0 + tm + 16 * a, c = n0 + tn + 32 * b;
+                    const long long r = m0 + tm + (RT / 4) * a, c = n0 + tn + (CT / 2) * b;
                     if (r < M && c < N) {
                         const float v = hi[a][b] + lo[a][b];
                         if (out_rowmajor) Out[r * ldo + c] = v;
@@ -168,62 +187,96 @@ __device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const floa
         }
 }
 
+__device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
+                            long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
+                            const Smem& sm)
+{
+    if (M <= 16) blk_gemm_tn_rt<16>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+    else if (M <= 32) blk_gemm_tn_rt<32>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+    else blk_gemm_tn_rt<64>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+}
+
 // C(M x N) -= V(M x K) Y(K x N), column-major, K <= 64; V with the optional unit-lower
-// structure.  Each 64 x 64 tile issues all of its loads (V and Y tiles to shared memory, the
-// C tile to registers) in one batch, then multiplies and writes C back.
+// structure.  64 x 64 tiles, rows of tiles outermost: V's 64-row band stays in shared memory for
+// a whole row of tiles; the next tile's C values and Y tile (and the next band of V) are fetched
+// into registers while the current tile is multiplied, so the loads of one tile overlap the
+// arithmetic of the previous one.
 __device__ void blk_gemm_update(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
                                 long long ldy, long long M, long long N, long long K, const Smem& sm)
 {
+    constexpr int PV = (kKu * kTile) / BT;  // 8 elements of V and of Y per thread
     const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
-    for (long long r0 = 0; r0 < M; r0 += kTile)
-        for (long long c0 = 0; c0 < N; c0 += kTile) {
-            float cv[4][2];
+    const long long nrt = (M + kTile - 1) / kTile, nct = (N + kTile - 1) / kTile;
+    const long long ntile = nrt * nct;
+    if (ntile == 0) return;
+    float cv[4][2], vr[PV], yr[PV];
+    auto fetch = [&](long long t, bool band) {
+        const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
-                    cv[a][b] = (r < M && c < N) ? C[c * ldc + r] : 0.f;
-                }
+            for (int b = 0; b < 2; ++b) {
+                const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
+                cv[a][b] = (r < M && c < N) ? C[c * ldc + r] : 0.f;
+            }
 #pragma unroll
-            for (int it = 0; it < (kKu * kTile) / BT; ++it) {
-                const int e = tid + it * BT;
-                const int rr = e & (kTile - 1), kk = e / kTile;  // V tile, rows fastest
+        for (int it = 0; it < PV; ++it) {
+            const int e = tid + it * BT;
+            if (band) {
+                const int rr = e & (kTile - 1), kk = e / kTile;  // V band, rows fastest
                 const long long r = r0 + rr;
                 float vv = 0.f;
                 if (r < M && kk < K) {
                     vv = V[(long long)kk * ldv + r];
                     if (maskV) vv = vmask_f(vv, r, kk);
                 }
-                sm.Xs[kk * kLdT + rr] = vv;
-                const int kk2 = e & (kKu - 1), cc = e / kKu;  // Y tile, K fastest
-                const long long c = c0 + cc;
-                sm.Cs[kk2 * kLdT + cc] = (kk2 < K && c < N) ? Y[c * ldy + kk2] : 0.f;
+                vr[it] = vv;
             }
-            __syncthreads();
-            float acc[4][2];
+            const int kk2 = e & (kKu - 1), cc = e / kKu;  // Y tile, K fastest
+            const long long c = c0 + cc;
+            yr[it] = (kk2 < K && c < N) ? Y[c * ldy + kk2] : 0.f;
+        }
+    };
+    fetch(0, true);
+    for (long long t = 0; t < ntile; ++t) {
+        const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
+        const bool new_band = (t % nct) == 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.f;
-            for (int kk = 0; kk < K; ++kk) {
-                float va[4], yb[2];
+        for (int it = 0; it < PV; ++it) {
+            const int e = tid + it * BT;
+            if (new_band) sm.Xs[(e / kTile) * kLdT + (e & (kTile - 1))] = vr[it];
+            sm.Cs[(e & (kKu - 1)) * kLdT + e / kKu] = yr[it];
+        }
+        float cur[4][2];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) va[a] = sm.Xs[kk * kLdT + tm + 16 * a];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) yb[b] = sm.Cs[kk * kLdT + tn + 32 * b];
+            for (int b = 0; b < 2; ++b) cur[a][b] = cv[a][b];
+        __syncthreads();
+        if (t + 1 < ntile) fetch(t + 1, ((t + 1) % nct) == 0);
+        float acc[4][2];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.f;
+        for (int kk = 0; kk < K; ++kk) {
+            float va[4], yb[2];
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(va[a], yb[b], acc[a][b]);
-            }
-            __syncthreads();
+            for (int a = 0; a < 4; ++a) va[a] = sm.Xs[kk * kLdT + tm + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 2; ++b) yb[b] = sm.Cs[kk * kLdT + tn + 32 * b];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
-                    if (r < M && c < N) C[c * ldc + r] = cv[a][b] - acc[a][b];
-                }
+                for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(va[a], yb[b], acc[a][b]);
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
+                if (r < M && c < N) C[c * ldc + r] = cur[a][b] - acc[a][b];
+            }
+        __syncthreads();
+    }
 }
 
 // Order key of a squared norm: non-negative doubles order as their bit patterns read as signed
@@ -550,24 +603,65 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
         blk_gemm_tn(Vp, lda, 1, Vp, lda, bb, bb, n - i, m1, Ww, bb, 0, sm);
         __syncthreads();
         blk_tform(Ww, bb, d.tau + i, sm);
-        for (long long e = tid; e < (long long)bb * nt; e += BT) {
-            const int r = (int)(e % bb);
-            const long long c = e / bb;
-            double s = 0.0;
-            for (int q = 0; q <= r; ++q) s += sm.Tm[r * bb + q] * (double)Ww[(bb + c) * bb + q];
-            Yw[c * bb + r] = (float)s;
+        {
+            // Y = T^T W(:, bb:) in FP32 with FP64-class accuracy: T = Th + Tl (two floats), the
+            // products and their sum compensated (Dot2: error-free product by FMA, TwoSum)
+            const int ldt = bb + 1;
+            float* Th = sm.Xs;                  // [q][r], ldt-padded: lanes (r) read consecutive words
+            float* Tl = sm.Xs + kKu * kLdT;     // the Cs half of the GEMM region
+            for (int e = tid; e < bb * bb; e += BT) {
+                const int q = e % bb, r = e / bb;
+                const double tv = q <= r ? sm.Tm[r * bb + q] : 0.0;
+                const float h = (float)tv;
+                Th[q * ldt + r] = h;
+                Tl[q * ldt + r] = (float)(tv - (double)h);
+            }
+            __syncthreads();
+            for (long long e = tid; e < (long long)bb * nt; e += BT) {
+                const int r = (int)(e % bb);
+                const long long c = e / bb;
+                const float* w = Ww + (bb + c) * bb;
+                float sacc = 0.f, cmp = 0.f;
+                for (int q = 0; q <= r; ++q) {
+                    const float wq = w[q], th = Th[q * ldt + r];
+                    const float pr = th * wq;
+                    const float pe = fmaf(th, wq, -pr);
+                    const float t2 = sacc + pr;
+                    const float z = t2 - sacc;
+                    cmp += ((sacc - (t2 - z)) + (pr - z)) + pe + Tl[q * ldt + r] * wq;
+                    sacc = t2;
+                }
+                Yw[c * bb + r] = sacc + cmp;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         blk_gemm_update(Vp + (long long)bb * lda, lda, Vp, lda, 1, Yw, bb, m1, nt, bb, sm);
         __syncthreads();
         if (pivoting && i + bb < k) {
             blk_bsolve(Bw, n, A, lda, i, bb, sm);
-            for (long long c = i + bb + tid; c < n; c += BT)
-                for (int r = 0; r < bb; ++r) {
-                    double s = 0.0;
-                    for (int q = r; q < bb; ++q) s += sm.Tm[q * bb + r] * (double)A[c * lda + i + q];
-                    Bw[(long long)r * n + c] -= (float)s;
+            // Eq. (4): B(0:bb, c) -= Omega_hat_11 R12(:, c) in FP32 (Omega_hat_11 upper, from FP64):
+            // every thread owns columns c, register accumulators for the bb rows, R12 read once
+            float* Wf = sm.Xs;  // [q][r] = Omega_hat_11(r, q), row q contiguous
+            for (int e = tid; e < bb * bb; e += BT) Wf[e] = (float)sm.Tm[e];  // Tm[q * bb + r]
+            __syncthreads();
+            for (long long c = i + bb + tid; c < n; c += BT) {
+                float acc[kKu];
+#pragma unroll
+                for (int r = 0; r < kKu; ++r) acc[r] = 0.f;
+                const float* a = A + c * lda + i;
+#pragma unroll
+                for (int q = 0; q < kKu; ++q) {
+                    if (q < bb) {
+                        const float aq = a[q];
+                        const float* wq = Wf + q * bb;
+#pragma unroll
+                        for (int r = 0; r <= q; ++r) acc[r] = fmaf(wq[r], aq, acc[r]);  // Omega_hat_11(r, q), r <= q
+                    }
                 }
+#pragma unroll
+                for (int r = 0; r < kKu; ++r)
+                    if (r < bb) Bw[(long long)r * n + c] -= acc[r];
+            }
             __syncthreads();
         }
     }
