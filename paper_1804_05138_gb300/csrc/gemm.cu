@@ -301,6 +301,87 @@ __global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_
     }
 }
 
+// reduce_y for the FP32 form: the same Y = op(T) W, W = sum_sp P[sp], with FP32 arithmetic of
+// FP64-class accuracy.  T and the FP64 sums W are split into two floats each (x = hi + lo); every
+// term op(T)(r,q) W(q,c) enters as an error-free product hi*hi' (FMA residual) plus the cross
+// terms, summed with TwoSum and a carried compensation (Ogita, Rump, Oishi, Dot2).  One block per
+// 64 columns; every thread owns a 4 x 4 register tile (rows tm + 16 a, columns tn + 16 b) and runs
+// the full contraction over q, the zeros of the triangle taking the rest.
+__global__ void __launch_bounds__(256) reduce_y_f32c_kernel(const double* __restrict__ P, int nsplit, int64_t ncols,
+                                                            int64_t c0, int bb, const double* __restrict__ Tm,
+                                                            int transT, double* __restrict__ Y, int64_t nc,
+                                                            const Status* st)
+{
+    if (status_error(st)) return;
+    extern __shared__ __align__(16) float smf[];
+    const int ld = 65;
+    float* Th = smf;               // [q][r] = op(T)(r, q), bb x ld
+    float* Tl = Th + 64 * ld;
+    float* Wh = Tl + 64 * ld;      // [q][c] = W(q, c), bb x ld
+    float* Wl = Wh + 64 * ld;
+    const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
+    const int64_t cb = (int64_t)blockIdx.x * 64;
+    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+        const int r = e & 63, q = e >> 6;  // T column-major: T(a, b) = Tm[b * bb + a]
+        double tv = 0.0;
+        if (r < bb && q < bb) tv = transT ? Tm[r * bb + q] : Tm[q * bb + r];
+        const float h = (float)tv;
+        Th[q * ld + r] = h;
+        Tl[q * ld + r] = (float)(tv - (double)h);
+    }
+    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+        const int q = e & 63, c = e >> 6;  // P[sp][col][q]: q fastest, coalesced
+        double w = 0.0;
+        if (q < bb && cb + c < nc) {
+            const int64_t col = c0 + cb + c;
+            for (int sp = 0; sp < nsplit; ++sp) w += P[((int64_t)sp * ncols + col) * bb + q];
+        }
+        const float h = (float)w;
+        Wh[q * ld + c] = h;
+        Wl[q * ld + c] = (float)(w - (double)h);
+    }
+    __syncthreads();
+    float sh[4][4], cp[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) sh[a][b] = cp[a][b] = 0.f;
+    for (int q = 0; q < bb; ++q) {
+        float th[4], tl[4], wh[4], wl[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            th[a] = Th[q * ld + tm + 16 * a];
+            tl[a] = Tl[q * ld + tm + 16 * a];
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            wh[b] = Wh[q * ld + tn + 16 * b];
+            wl[b] = Wl[q * ld + tn + 16 * b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float pr = th[a] * wh[b];
+                const float pe = fmaf(th[a], wh[b], -pr);
+                const float t = sh[a][b] + pr;
+                const float z = t - sh[a][b];
+                const float er = (sh[a][b] - (t - z)) + (pr - z);
+                sh[a][b] = t;
+                cp[a][b] += er + pe + fmaf(th[a], wl[b], tl[a] * wh[b]);
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = tm + 16 * a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t c = cb + tn + 16 * b;
+            if (r < bb && c < nc) Y[c * bb + r] = (double)sh[a][b] + (double)cp[a][b];
+        }
+    }
+}
+
 }  // namespace
 
 int gemm_tn_blocks_per_sm(int elem_bytes)
@@ -368,7 +449,7 @@ cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, con
 }
 
 cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t c0, int bb, const double* Tm,
-                            int transT, double* Y, int64_t nc, const Status* st, cudaStream_t s)
+                            int transT, double* Y, int64_t nc, const Status* st, cudaStream_t s, int fp32c)
 {
     if (nc <= 0) return cudaSuccess;
     const int threads = 256, nw = threads / 32;
@@ -377,6 +458,17 @@ cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t 
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(reduce_y_kernel)) return e;
         attr_set = true;
+    }
+    if (fp32c && bb <= 64) {
+        static bool set_c = false;
+        if (!set_c) {
+            if (cudaError_t e = allow_max_dynamic_smem(reduce_y_f32c_kernel)) return e;
+            set_c = true;
+        }
+        const size_t smem_c = sizeof(float) * 4 * 64 * 65;
+        reduce_y_f32c_kernel<<<(unsigned)((nc + 63) / 64), 256, smem_c, s>>>(P, nsplit, ncols, c0, bb, Tm, transT, Y,
+                                                                            nc, st);
+        return cudaGetLastError();
     }
     int64_t grid = (nc + nw - 1) / nw;
     const int64_t cap = (int64_t)dev_info().sms * 4;

@@ -162,9 +162,11 @@ cudaError_t launch_sketch_reduce(const double* P, int nsplit, int64_t l, int64_t
 cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, const double* tau,
                          double* Tm, const Status* st, cudaStream_t s);
 
-// Y(:, c) = op(T) * sum_sp P[sp][c0 + c][0:bb], c < nc, op(T) = T^T if transT else T.
+// Y(:, c) = op(T) * sum_sp P[sp][c0 + c][0:bb], c < nc, op(T) = T^T if transT else T.  fp32c:
+// FP32 arithmetic with FP64-class accuracy (two-float operands, compensated sums) for the FP32
+// form; otherwise IEEE double.
 cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t c0, int bb, const double* Tm,
-                            int transT, double* Y, int64_t nc, const Status* st, cudaStream_t s);
+                            int transT, double* Y, int64_t nc, const Status* st, cudaStream_t s, int fp32c = 0);
 
 // Cooperative pivot search on B(:, i:n) (bb steps of QRCP on the sketch).  `cand` is
 // pivot_cand_bytes(l) of candidate buffers followed by the swap map (1 + 4*bb int64).

@@ -240,7 +240,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         RQ_LAUNCH(K_TFORM, (double)bb * bb * bb / 3.0, (double)ns * bb * bb * 8,
                   launch_tform(P, ns, n - i, bb, tau + i, Tm, st, s));
         RQ_LAUNCH(K_REDUCE_Y, (double)bb * bb * nt, ((double)ns + 1.0) * bb * nt * 8,
-                  launch_reduce_y(P, ns, n - i, bb, bb, Tm, 1, Y, nt, st, s));
+                  launch_reduce_y(P, ns, n - i, bb, bb, Tm, 1, Y, nt, st, s, sizeof(T) == 4 ? 1 : 0));
         if (sizeof(T) == 4 && tensor_cores_enabled() && tc_update_supported(bb, lda, Vp + (int64_t)bb * lda))
             RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
                       launch_gemm_update_tc((float*)(Vp + (int64_t)bb * lda), lda, (const float*)Vp, lda, Y, bb, mr, nt,
