@@ -189,15 +189,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const unsigned char* xt = stage_ptr(s) + tileC;
                 const uint32_t td = tmem + (uint32_t)(b * dcols);
                 const uint32_t ta = tA + (uint32_t)(b * ACOLS);
+                // k-step k starts 32 bytes further into the 128-byte swizzle rows: the descriptor's
+                // address field (bytes >> 4, 14 bits, tile below 256 KB) advances by 2 without carry
+                const uint64_t dx = umma_desc(xt);
                 if (BF) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_bf16_ts(td, ta + 8 * k, umma_desc(xt + k * 32), idesc, k > 0 ? 1 : 0);
+                    for (int k = 0; k < 4; ++k) mma_bf16_ts(td, ta + 8 * k, dx + 2 * k, idesc, k > 0 ? 1 : 0);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < TC_KC / 8; ++k)
-                        mma_tf32_ts(td, ta + 32 + 8 * k, umma_desc(xt + k * 32), idesc, k > 0 ? 1 : 0);
+                    for (int k = 0; k < TC_KC / 8; ++k) mma_tf32_ts(td, ta + 32 + 8 * k, dx + 2 * k, idesc, k > 0 ? 1 : 0);
 #pragma unroll
-                    for (int k = 0; k < TC_KC / 8; ++k) mma_tf32_ts(td, ta + 8 * k, umma_desc(xt + k * 32), idesc, 1);
+                    for (int k = 0; k < TC_KC / 8; ++k) mma_tf32_ts(td, ta + 8 * k, dx + 2 * k, idesc, 1);
                 }
                 mma_commit(&empty[s]);
                 mma_commit(&accfull[b]);
