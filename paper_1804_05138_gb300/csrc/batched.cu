@@ -34,11 +34,12 @@ constexpr int kKu = 64;          // largest K of the update contraction (b <= 64
 constexpr int kLdT = kTile + 1;  // padded shared-memory tile stride
 
 struct Smem {
+    float* G;       // union: the panel's sub-panel S, or the contractions' ring / tiles
     float* S;       // SW x m_max sub-panel
     double* nu;     // n_max sketch norms
     double* Tm;     // b_max x b_max: T, then Omega_hat_11
-    float* Xs;      // kKu x kLdT GEMM tile
-    float* Cs;      // kKu x kLdT GEMM tile
+    float* Xs;      // kKu x kLdT GEMM tile (inside G)
+    float* Cs;      // kKu x kLdT GEMM tile (inside G)
     float* vs;      // l_max reflector of the pivot search
     double* red;    // NW x SW block-reduction scratch
     double* sc;     // scalars: tau, beta, scal, guard, ...
@@ -81,13 +82,31 @@ __device__ void block_sum(double (&v)[NV], double* red, double* out)
     __syncthreads();
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async), grouped per K-slice.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Ring of K-slices for the contractions: kRing stages, the largest stage being the 32 x 32
+// X slice plus the 32 x 128 C slice with their padded strides.
+constexpr int kRing = 4;
+constexpr int kStageFloats = 32 * (32 + 1) + 32 * (128 + 1);
+constexpr int kGemmFloats = kRing * kStageFloats;
+
 // Out(M x N) = X^T C; X is K x M (ldx), C is K x N (ldc), column-major.  maskX / maskC: unit-
 // lower reflector structure of X / of the first maskC columns of C.  out_rowmajor stores
 // Out(r, c) at r*ldo + c, else at c*ldo + r.  Output tiles are RT x CT (RT * CT = 4096: 16 x 256,
 // 32 x 128 or 64 x 64, the smallest RT >= M when M <= 32, so a short X wastes no rows); every
-// thread owns 4 rows x 2 columns.  K is consumed in KS-deep slices; the next slice is fetched into
-// registers while the current one is multiplied out of shared memory.  Up to 64 terms are summed
-// in FP32 and folded into a compensated (TwoSum) total.
+// thread owns 4 rows x 2 columns.  K is consumed in KS-deep slices that stream through a ring of
+// kRing shared-memory stages by cp.async, kRing - 1 slices in flight while one is multiplied (a
+// single block per SM has to keep that many bytes moving on its own).  Entries the unit-lower
+// structure fixes (0 or 1) are stored directly instead of copied.  Up to 64 terms are summed in
+// FP32 and folded into a compensated (TwoSum) total.
 template <int RT>
 __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
                                long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
@@ -96,58 +115,58 @@ __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const f
     constexpr int CT = 4096 / RT;
     constexpr int KS = RT == 16 ? 16 : 32;
     constexpr int LX = RT + 1, LC = CT + 1;
+    constexpr int SX = KS * LX, STG = KS * (LX + LC);
     constexpr int PX = (KS * RT + BT - 1) / BT, PC = (KS * CT) / BT;
     constexpr int FOLD = 64 / KS;  // slices per FP32 partial sum
-    static_assert(KS * (LX + LC) <= 2 * kKu * kLdT, "tiles exceed the shared-memory GEMM region");
-    float* Xs = sm.Xs;            // KS x LX
-    float* Cs = sm.Xs + KS * LX;  // KS x LC (the Xs/Cs region is contiguous)
+    static_assert(STG <= kStageFloats, "stage exceeds the ring's stage size");
+    float* ring = sm.G;
     const int tid = threadIdx.x, tm = tid % (RT / 4), tn = tid / (RT / 4);
+    const long long nsl = (K + KS - 1) / KS;
     for (long long m0 = 0; m0 < M; m0 += RT)
         for (long long n0 = 0; n0 < N; n0 += CT) {
-            float acc[4][2], hi[4][2], lo[4][2], xr[PX], cr[PC];
+            // copy slice j into stage j % kRing (one commit group per slice, possibly empty)
+            auto issue = [&](long long j) {
+                if (j < nsl) {
+                    float* Xs = ring + (j % kRing) * STG;
+                    float* Cs = Xs + SX;
+                    const long long k0 = j * KS;
+#pragma unroll
+                    for (int it = 0; it < PX; ++it) {
+                        const int e = tid + it * BT, kk = e % KS, mm = e / KS;
+                        if (e < KS * RT) {
+                            const long long q = k0 + kk, r = m0 + mm;
+                            float* dst = Xs + kk * LX + mm;
+                            if (q >= K || r >= M) *dst = 0.f;
+                            else if (maskX && q <= r) *dst = q == r ? 1.f : 0.f;
+                            else cp_async4(dst, X + r * ldx + q);
+                        }
+                    }
+#pragma unroll
+                    for (int it = 0; it < PC; ++it) {
+                        const int e = tid + it * BT, kk = e % KS, mm = e / KS;
+                        const long long q = k0 + kk, c = n0 + mm;
+                        float* dst = Cs + kk * LC + mm;
+                        if (q >= K || c >= N) *dst = 0.f;
+                        else if (c < maskC && q <= c) *dst = q == c ? 1.f : 0.f;
+                        else cp_async4(dst, C + c * ldc + q);
+                    }
+                }
+                cp_async_commit();
+            };
+            float acc[4][2], hi[4][2], lo[4][2];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
-            auto fetch = [&](long long k0) {
 #pragma unroll
-                for (int it = 0; it < PX; ++it) {
-                    const int e = tid + it * BT, kk = e % KS, mm = e / KS;
-                    const long long q = k0 + kk, r = m0 + mm;
-                    float xv = 0.f;
-                    if (e < KS * RT && q < K && r < M) {
-                        xv = X[r * ldx + q];
-                        if (maskX) xv = vmask_f(xv, q, r);
-                    }
-                    xr[it] = xv;
-                }
-#pragma unroll
-                for (int it = 0; it < PC; ++it) {
-                    const int e = tid + it * BT, kk = e % KS, mm = e / KS;
-                    const long long q = k0 + kk, c = n0 + mm;
-                    float cv = 0.f;
-                    if (q < K && c < N) {
-                        cv = C[c * ldc + q];
-                        if (c < maskC) cv = vmask_f(cv, q, c);
-                    }
-                    cr[it] = cv;
-                }
-            };
-            fetch(0);
+            for (int j = 0; j < kRing - 1; ++j) issue(j);
             int slice = 0;
-            for (long long k0 = 0; k0 < K; k0 += KS) {
-#pragma unroll
-                for (int it = 0; it < PX; ++it) {
-                    const int e = tid + it * BT;
-                    if (e < KS * RT) Xs[(e % KS) * LX + e / KS] = xr[it];
-                }
-#pragma unroll
-                for (int it = 0; it < PC; ++it) {
-                    const int e = tid + it * BT;
-                    Cs[(e % KS) * LC + e / KS] = cr[it];
-                }
-                __syncthreads();
-                if (k0 + KS < K) fetch(k0 + KS);
+            for (long long j = 0; j < nsl; ++j) {
+                cp_async_wait<kRing - 2>();  // this thread's copies of slice j have landed
+                __syncthreads();             // everyone's have; stage (j - 1) % kRing is free
+                issue(j + kRing - 1);
+                const float* Xs = ring + (j % kRing) * STG;
+                const float* Cs = Xs + SX;
 #pragma unroll 8
                 for (int kk = 0; kk < KS; ++kk) {
                     float xa[4], cb[2];
@@ -160,7 +179,6 @@ __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const f
 #pragma unroll
                         for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(xa[a], cb[b], acc[a][b]);
                 }
-                __syncthreads();
                 if (++slice == FOLD) {
                     slice = 0;
 #pragma unroll
@@ -172,6 +190,8 @@ __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const f
                         }
                 }
             }
+            cp_async_wait<0>();
+            __syncthreads();  // the ring is reused by the next tile
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -197,72 +217,80 @@ __device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const floa
 }
 
 // C(M x N) -= V(M x K) Y(K x N), column-major, K <= 64; V with the optional unit-lower
-// structure.  64 x 64 tiles, rows of tiles outermost: V's 64-row band stays in shared memory for
-// a whole row of tiles; the next tile's C values and Y tile (and the next band of V) are fetched
-// into registers while the current tile is multiplied, so the loads of one tile overlap the
-// arithmetic of the previous one.
+// structure.  64 x 64 tiles, rows of tiles outermost; each tile's C block, Y block and V band
+// stream through a ring of kURing shared-memory stages by cp.async (V and Y come from L2), so
+// kURing - 1 tiles are in flight while one is multiplied; every thread owns 4 rows x 2 columns
+// and writes its C entries straight back.
+constexpr int kURing = 3;
+constexpr int kUStage = 3 * kKu * kLdT;  // C (64 x 64, [col][row]), Y ([k][col]), V ([k][row])
+
 __device__ void blk_gemm_update(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
                                 long long ldy, long long M, long long N, long long K, const Smem& sm)
 {
-    constexpr int PV = (kKu * kTile) / BT;  // 8 elements of V and of Y per thread
+    constexpr int PE = (kTile * kTile) / BT;  // 8 copies per operand per thread
     const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
     const long long nrt = (M + kTile - 1) / kTile, nct = (N + kTile - 1) / kTile;
     const long long ntile = nrt * nct;
     if (ntile == 0) return;
-    float cv[4][2], vr[PV], yr[PV];
-    auto fetch = [&](long long t, bool band) {
-        const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
+    float* ring = sm.G;
+    auto issue = [&](long long t) {
+        if (t < ntile) {
+            float* Cs = ring + (t % kURing) * kUStage;
+            float* Ys = Cs + kKu * kLdT;
+            float* Vs = Ys + kKu * kLdT;
+            const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
-                cv[a][b] = (r < M && c < N) ? C[c * ldc + r] : 0.f;
-            }
-#pragma unroll
-        for (int it = 0; it < PV; ++it) {
-            const int e = tid + it * BT;
-            if (band) {
-                const int rr = e & (kTile - 1), kk = e / kTile;  // V band, rows fastest
-                const long long r = r0 + rr;
-                float vv = 0.f;
-                if (r < M && kk < K) {
-                    vv = V[(long long)kk * ldv + r];
-                    if (maskV) vv = vmask_f(vv, r, kk);
+            for (int it = 0; it < PE; ++it) {
+                const int e = tid + it * BT;
+                {  // C block, rows fastest
+                    const int rr = e & (kTile - 1), cc = e / kTile;
+                    const long long r = r0 + rr, c = c0 + cc;
+                    float* dst = Cs + cc * kLdT + rr;
+                    if (r < M && c < N) cp_async4(dst, C + c * ldc + r);
+                    else *dst = 0.f;
                 }
-                vr[it] = vv;
+                {  // V band, rows fastest
+                    const int rr = e & (kTile - 1), kk = e / kTile;
+                    if (kk < K) {
+                        const long long r = r0 + rr;
+                        float* dst = Vs + kk * kLdT + rr;
+                        if (r >= M) *dst = 0.f;
+                        else if (maskV && r <= kk) *dst = r == kk ? 1.f : 0.f;
+                        else cp_async4(dst, V + (long long)kk * ldv + r);
+                    }
+                }
+                {  // Y block, K fastest
+                    const int kk = e & (kKu - 1), cc = e / kKu;
+                    if (kk < K) {
+                        const long long c = c0 + cc;
+                        float* dst = Ys + kk * kLdT + cc;
+                        if (c < N) cp_async4(dst, Y + c * ldy + kk);
+                        else *dst = 0.f;
+                    }
+                }
             }
-            const int kk2 = e & (kKu - 1), cc = e / kKu;  // Y tile, K fastest
-            const long long c = c0 + cc;
-            yr[it] = (kk2 < K && c < N) ? Y[c * ldy + kk2] : 0.f;
         }
+        cp_async_commit();
     };
-    fetch(0, true);
+#pragma unroll
+    for (int j = 0; j < kURing - 1; ++j) issue(j);
     for (long long t = 0; t < ntile; ++t) {
-        const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
-        const bool new_band = (t % nct) == 0;
-#pragma unroll
-        for (int it = 0; it < PV; ++it) {
-            const int e = tid + it * BT;
-            if (new_band) sm.Xs[(e / kTile) * kLdT + (e & (kTile - 1))] = vr[it];
-            sm.Cs[(e & (kKu - 1)) * kLdT + e / kKu] = yr[it];
-        }
-        float cur[4][2];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) cur[a][b] = cv[a][b];
+        cp_async_wait<kURing - 2>();
         __syncthreads();
-        if (t + 1 < ntile) fetch(t + 1, ((t + 1) % nct) == 0);
+        issue(t + kURing - 1);
+        const float* Cs = ring + (t % kURing) * kUStage;
+        const float* Ys = Cs + kKu * kLdT;
+        const float* Vs = Ys + kKu * kLdT;
+        const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
         float acc[4][2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.f;
         for (int kk = 0; kk < K; ++kk) {
             float va[4], yb[2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) va[a] = sm.Xs[kk * kLdT + tm + 16 * a];
+            for (int a = 0; a < 4; ++a) va[a] = Vs[kk * kLdT + tm + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 2; ++b) yb[b] = sm.Cs[kk * kLdT + tn + 32 * b];
+            for (int b = 0; b < 2; ++b) yb[b] = Ys[kk * kLdT + tn + 32 * b];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -272,11 +300,13 @@ __device__ void blk_gemm_update(float* C, long long ldc, const float* V, long lo
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                const long long r = r0 + tm + 16 * a, c = c0 + tn + 32 * b;
-                if (r < M && c < N) C[c * ldc + r] = cur[a][b] - acc[a][b];
+                const int rr = tm + 16 * a, cc = tn + 32 * b;
+                const long long r = r0 + rr, c = c0 + cc;
+                if (r < M && c < N) C[c * ldc + r] = Cs[cc * kLdT + rr] - acc[a][b];
             }
-        __syncthreads();
     }
+    cp_async_wait<0>();
+    __syncthreads();  // the ring is reused by whatever follows
 }
 
 // Order key of a squared norm: non-negative doubles order as their bit patterns read as signed
@@ -669,6 +699,16 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
     __syncthreads();
 }
 
+// The panel's sub-panel and the contractions' shared-memory buffers are never live at the
+// same time, so they share one region.
+__host__ __device__ inline size_t union_floats(long long m_max)
+{
+    size_t f = (size_t)SW * (size_t)m_max;
+    if (f < (size_t)kGemmFloats) f = kGemmFloats;
+    if (f < (size_t)kURing * kUStage) f = (size_t)kURing * kUStage;
+    return f;
+}
+
 __global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restrict__ descs, const int* __restrict__ order,
                                                         int count, const float* __restrict__ Om, long long ldo, int p,
                                                         long long m_max, long long n_max, int b_max, char* ws,
@@ -683,11 +723,12 @@ __global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restr
         return ptr;
     };
     const int l_max = b_max + p;
-    sm.S = reinterpret_cast<float*>(carve(sizeof(float) * SW * (size_t)m_max));
+    sm.G = reinterpret_cast<float*>(carve(sizeof(float) * union_floats(m_max)));
+    sm.S = sm.G;
+    sm.Xs = sm.G;
+    sm.Cs = sm.G + kKu * kLdT;
     sm.nu = reinterpret_cast<double*>(carve(sizeof(double) * (size_t)n_max));
     sm.Tm = reinterpret_cast<double*>(carve(sizeof(double) * (size_t)b_max * b_max));
-    sm.Xs = reinterpret_cast<float*>(carve(sizeof(float) * kKu * kLdT));
-    sm.Cs = reinterpret_cast<float*>(carve(sizeof(float) * kKu * kLdT));
     sm.vs = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)l_max));
     sm.red = reinterpret_cast<double*>(carve(sizeof(double) * NW * SW));
     sm.sc = reinterpret_cast<double*>(carve(sizeof(double) * 40));
@@ -714,11 +755,9 @@ size_t batched_smem_bytes(long long m_max, long long n_max, int b_max, int p)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~(size_t)15; };
-    take(sizeof(float) * SW * (size_t)m_max);
+    take(sizeof(float) * union_floats(m_max));
     take(sizeof(double) * (size_t)n_max);
     take(sizeof(double) * (size_t)b_max * b_max);
-    take(sizeof(float) * kKu * kLdT);
-    take(sizeof(float) * kKu * kLdT);
     take(sizeof(float) * (size_t)(b_max + p));
     take(sizeof(double) * NW * SW);
     take(sizeof(double) * 40);
