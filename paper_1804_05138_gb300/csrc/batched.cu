@@ -92,72 +92,95 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Ring of K-slices for the contractions: kRing stages, the largest stage being the 32 x 32
-// X slice plus the 32 x 128 C slice with their padded strides.
+// Ring of K-slices for the contractions: kRing stages, the largest being the 32 x 32 X slice
+// plus the 32 x 256 C slice.
 constexpr int kRing = 4;
-constexpr int kStageFloats = 32 * (32 + 1) + 32 * (128 + 1);
+constexpr int kStageFloats = 32 * (32 + 256);
 constexpr int kGemmFloats = kRing * kStageFloats;
 
 // Out(M x N) = X^T C; X is K x M (ldx), C is K x N (ldc), column-major.  maskX / maskC: unit-
 // lower reflector structure of X / of the first maskC columns of C.  out_rowmajor stores
-// Out(r, c) at r*ldo + c, else at c*ldo + r.  Output tiles are RT x CT (RT * CT = 4096: 16 x 256,
-// 32 x 128 or 64 x 64, the smallest RT >= M when M <= 32, so a short X wastes no rows); every
-// thread owns 4 rows x 2 columns.  K is consumed in KS-deep slices that stream through a ring of
-// kRing shared-memory stages by cp.async, kRing - 1 slices in flight while one is multiplied (a
-// single block per SM has to keep that many bytes moving on its own).  Entries the unit-lower
-// structure fixes (0 or 1) are stored directly instead of copied.  Up to 64 terms are summed in
-// FP32 and folded into a compensated (TwoSum) total.
+// Out(r, c) at r*ldo + c, else at c*ldo + r.  Output tiles are RT x CT (RT * CT = 8192: 16 x 512,
+// 32 x 256 or 64 x 128, the smallest RT >= M when M <= 32, so a short X wastes no rows); every
+// thread owns a 4 x 4 block of them.  K is consumed in KS-deep slices that stream through a ring
+// of kRing shared-memory stages by cp.async, kRing - 1 slices in flight while one is multiplied
+// (a single block per SM has to keep that many bytes moving on its own).  A slice is stored
+// k-major with the element (k, j) of row k at j ^ k: the copies (lanes along k) then hit distinct
+// banks, and a thread reads its 4 rows and its 4 columns as two 16-byte words whose lanes are
+// permuted by the low bits of k.  Interior slices copy from per-thread base pointers; slices that
+// touch an edge or the unit-lower structure take the checked path, which stores the entries that
+// structure fixes (0 or 1) directly.  Up to 64 terms are summed in FP32 and folded into a
+// compensated (TwoSum) total.
 template <int RT>
 __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
                                long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
                                const Smem& sm)
 {
-    constexpr int CT = 4096 / RT;
+    constexpr int CT = 8192 / RT;
     constexpr int KS = RT == 16 ? 16 : 32;
-    constexpr int LX = RT + 1, LC = CT + 1;
-    constexpr int SX = KS * LX, STG = KS * (LX + LC);
+    constexpr int SX = KS * RT, STG = KS * (RT + CT);
     constexpr int PX = (KS * RT + BT - 1) / BT, PC = (KS * CT) / BT;
+    constexpr int CPI = BT / KS;  // rows / columns one pass of the block copies
     constexpr int FOLD = 64 / KS;  // slices per FP32 partial sum
     static_assert(STG <= kStageFloats, "stage exceeds the ring's stage size");
+    static_assert(KS <= RT && KS <= CT, "the k-swizzle must stay inside a row");
     float* ring = sm.G;
     const int tid = threadIdx.x, tm = tid % (RT / 4), tn = tid / (RT / 4);
+    const int ck = tid % KS, cm = tid / KS;  // this thread's copy coordinates in a slice
     const long long nsl = (K + KS - 1) / KS;
+    const long long xstep = (long long)CPI * ldx, cstep = (long long)CPI * ldc;
     for (long long m0 = 0; m0 < M; m0 += RT)
         for (long long n0 = 0; n0 < N; n0 += CT) {
+            const float* xsrc = X + (m0 + cm) * ldx + ck;
+            const float* csrc = C + (n0 + cm) * ldc + ck;
+            const bool inner = m0 + RT <= M && n0 + CT <= N;
             // copy slice j into stage j % kRing (one commit group per slice, possibly empty)
             auto issue = [&](long long j) {
                 if (j < nsl) {
                     float* Xs = ring + (j % kRing) * STG;
                     float* Cs = Xs + SX;
                     const long long k0 = j * KS;
+                    if (inner && k0 + KS <= K && (!maskX || k0 >= m0 + RT) && (n0 >= maskC || k0 >= maskC)) {
 #pragma unroll
-                    for (int it = 0; it < PX; ++it) {
-                        const int e = tid + it * BT, kk = e % KS, mm = e / KS;
-                        if (e < KS * RT) {
-                            const long long q = k0 + kk, r = m0 + mm;
-                            float* dst = Xs + kk * LX + mm;
-                            if (q >= K || r >= M) *dst = 0.f;
-                            else if (maskX && q <= r) *dst = q == r ? 1.f : 0.f;
-                            else cp_async4(dst, X + r * ldx + q);
+                        for (int it = 0; it < PX; ++it) {
+                            const int mm = cm + it * CPI;
+                            if (PX * BT == KS * RT || mm < RT) cp_async4(Xs + ck * RT + (mm ^ ck), xsrc + it * xstep + k0);
                         }
-                    }
 #pragma unroll
-                    for (int it = 0; it < PC; ++it) {
-                        const int e = tid + it * BT, kk = e % KS, mm = e / KS;
-                        const long long q = k0 + kk, c = n0 + mm;
-                        float* dst = Cs + kk * LC + mm;
-                        if (q >= K || c >= N) *dst = 0.f;
-                        else if (c < maskC && q <= c) *dst = q == c ? 1.f : 0.f;
-                        else cp_async4(dst, C + c * ldc + q);
+                        for (int it = 0; it < PC; ++it) {
+                            const int mm = cm + it * CPI;
+                            cp_async4(Cs + ck * CT + (mm ^ ck), csrc + it * cstep + k0);
+                        }
+                    } else {
+#pragma unroll
+                        for (int it = 0; it < PX; ++it) {
+                            const int mm = cm + it * CPI;
+                            if (mm < RT) {
+                                const long long q = k0 + ck, r = m0 + mm;
+                                float* dst = Xs + ck * RT + (mm ^ ck);
+                                if (q >= K || r >= M) *dst = 0.f;
+                                else if (maskX && q <= r) *dst = q == r ? 1.f : 0.f;
+                                else cp_async4(dst, X + r * ldx + q);
+                            }
+                        }
+#pragma unroll
+                        for (int it = 0; it < PC; ++it) {
+                            const int mm = cm + it * CPI;
+                            const long long q = k0 + ck, c = n0 + mm;
+                            float* dst = Cs + ck * CT + (mm ^ ck);
+                            if (q >= K || c >= N) *dst = 0.f;
+                            else if (c < maskC && q <= c) *dst = q == c ? 1.f : 0.f;
+                            else cp_async4(dst, C + c * ldc + q);
+                        }
                     }
                 }
                 cp_async_commit();
             };
-            float acc[4][2], hi[4][2], lo[4][2];
+            float acc[4][4], hi[4][4], lo[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
+                for (int b = 0; b < 4; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
 #pragma unroll
             for (int j = 0; j < kRing - 1; ++j) issue(j);
             int slice = 0;
@@ -167,24 +190,23 @@ __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const f
                 issue(j + kRing - 1);
                 const float* Xs = ring + (j % kRing) * STG;
                 const float* Cs = Xs + SX;
-#pragma unroll 8
+#pragma unroll
                 for (int kk = 0; kk < KS; ++kk) {
-                    float xa[4], cb[2];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) xa[a] = Xs[kk * LX + tm + (RT / 4) * a];
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) cb[b] = Cs[kk * LC + tn + (CT / 2) * b];
+                    const float4 xv = *reinterpret_cast<const float4*>(Xs + kk * RT + ((4 * tm) ^ (kk & ~3)));
+                    const float4 cv = *reinterpret_cast<const float4*>(Cs + kk * CT + ((4 * tn) ^ (kk & ~3)));
+                    const float xr[4] = {xv.x, xv.y, xv.z, xv.w}, cr[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(xa[a], cb[b], acc[a][b]);
+                        for (int b = 0; b < 4; ++b)
+                            acc[a][b] = fmaf(xr[a ^ (kk & 3)], cr[b ^ (kk & 3)], acc[a][b]);
                 }
                 if (++slice == FOLD) {
                     slice = 0;
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int b = 0; b < 2; ++b) {
+                        for (int b = 0; b < 4; ++b) {
                             two_sum_acc(hi[a][b], lo[a][b], acc[a][b]);
                             acc[a][b] = 0.f;
                         }
@@ -195,9 +217,9 @@ __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const f
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
+                for (int b = 0; b < 4; ++b) {
                     two_sum_acc(hi[a][b], lo[a][b], acc[a][b]);
-                    const long long r = m0 + tm + (RT / 4) * a, c = n0 + tn + (CT / 2) * b;
+                    const long long r = m0 + 4 * tm + a, c = n0 + 4 * tn + b;
                     if (r < M && c < N) {
                         const float v = hi[a][b] + lo[a][b];
                         if (out_rowmajor) Out[r * ldo + c] = v;
@@ -217,96 +239,128 @@ __device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const floa
 }
 
 // C(M x N) -= V(M x K) Y(K x N), column-major, K <= 64; V with the optional unit-lower
-// structure.  64 x 64 tiles, rows of tiles outermost; each tile's C block, Y block and V band
-// stream through a ring of kURing shared-memory stages by cp.async (V and Y come from L2), so
-// kURing - 1 tiles are in flight while one is multiplied; every thread owns 4 rows x 2 columns
-// and writes its C entries straight back.
-constexpr int kURing = 3;
-constexpr int kUStage = 3 * kKu * kLdT;  // C (64 x 64, [col][row]), Y ([k][col]), V ([k][row])
+// structure.  64 x 128 tiles, rows of tiles outermost; each tile's C block, Y block and V band
+// stream through a ring of NST shared-memory stages by cp.async (V and Y come from L2), so
+// NST - 1 tiles are in flight while one is multiplied.  Lane l of warp w owns rows l, l + 32 and
+// columns 8w..8w+7 of the tile, so its C entries are written back 128 bytes per warp store.
+// C is kept [col][row], V [k][row], Y [k][col] with the element (k, c) at c ^ k, which spreads
+// the copies (lanes along k) over the banks and lets a warp read its eight columns as two
+// 16-byte words, permuted by the low bits of k.  K is zero-padded to K4, a multiple of 4; a stage
+// holds 8192 + 192 K4 floats, three of them when they fit in kURingFloats, else two.
+constexpr int kUR = 64, kUC = 128;
+constexpr int kURingFloats = 3 * (kUR * kUC + 32 * (kUR + kUC));
 
-__device__ void blk_gemm_update(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
-                                long long ldy, long long M, long long N, long long K, const Smem& sm)
+template <int NST>
+__device__ void blk_gemm_update_n(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
+                                  long long ldy, long long M, long long N, long long K, int K4, const Smem& sm)
 {
-    constexpr int PE = (kTile * kTile) / BT;  // 8 copies per operand per thread
-    const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
-    const long long nrt = (M + kTile - 1) / kTile, nct = (N + kTile - 1) / kTile;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long nrt = (M + kUR - 1) / kUR, nct = (N + kUC - 1) / kUC;
     const long long ntile = nrt * nct;
-    if (ntile == 0) return;
+    const int SF = kUR * kUC + K4 * (kUR + kUC);
+    int klog = 2;
+    while ((1 << klog) < K4) ++klog;
+    const int kmask = (1 << klog) - 1;  // K slots of the Y copy (a power of two >= K4)
     float* ring = sm.G;
+    const int rr = tid & (kUR - 1), cc0 = tid / kUR;
     auto issue = [&](long long t) {
         if (t < ntile) {
-            float* Cs = ring + (t % kURing) * kUStage;
-            float* Ys = Cs + kKu * kLdT;
-            float* Vs = Ys + kKu * kLdT;
-            const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
+            float* Cs = ring + (t % NST) * SF;
+            float* Ys = Cs + kUR * kUC;
+            float* Vs = Ys + K4 * kUC;
+            const long long r0 = (t / nct) * kUR, c0 = (t % nct) * kUC;
+            // C block, rows fastest
+            if (r0 + kUR <= M && c0 + kUC <= N) {
+                const float* src = C + (c0 + cc0) * ldc + r0 + rr;
+                const long long step = (long long)(BT / kUR) * ldc;
 #pragma unroll
-            for (int it = 0; it < PE; ++it) {
-                const int e = tid + it * BT;
-                {  // C block, rows fastest
-                    const int rr = e & (kTile - 1), cc = e / kTile;
+                for (int it = 0; it < kUR * kUC / BT; ++it)
+                    cp_async4(Cs + (cc0 + it * (BT / kUR)) * kUR + rr, src + it * step);
+            } else {
+#pragma unroll
+                for (int it = 0; it < kUR * kUC / BT; ++it) {
+                    const int cc = cc0 + it * (BT / kUR);
                     const long long r = r0 + rr, c = c0 + cc;
-                    float* dst = Cs + cc * kLdT + rr;
+                    float* dst = Cs + cc * kUR + rr;
                     if (r < M && c < N) cp_async4(dst, C + c * ldc + r);
                     else *dst = 0.f;
                 }
-                {  // V band, rows fastest
-                    const int rr = e & (kTile - 1), kk = e / kTile;
-                    if (kk < K) {
-                        const long long r = r0 + rr;
-                        float* dst = Vs + kk * kLdT + rr;
-                        if (r >= M) *dst = 0.f;
-                        else if (maskV && r <= kk) *dst = r == kk ? 1.f : 0.f;
-                        else cp_async4(dst, V + (long long)kk * ldv + r);
-                    }
-                }
-                {  // Y block, K fastest
-                    const int kk = e & (kKu - 1), cc = e / kKu;
-                    if (kk < K) {
+            }
+            // V band, rows fastest
+            for (int kk = cc0; kk < K4; kk += BT / kUR) {
+                const long long r = r0 + rr;
+                float* dst = Vs + kk * kUR + rr;
+                if (kk >= K || r >= M) *dst = 0.f;
+                else if (maskV && r <= kk) *dst = r == kk ? 1.f : 0.f;
+                else cp_async4(dst, V + (long long)kk * ldv + r);
+            }
+            // Y block, K fastest
+            {
+                const int kk = tid & kmask;
+                if (kk < K4)
+                    for (int cc = tid >> klog; cc < kUC; cc += BT >> klog) {
                         const long long c = c0 + cc;
-                        float* dst = Ys + kk * kLdT + cc;
-                        if (c < N) cp_async4(dst, Y + c * ldy + kk);
+                        float* dst = Ys + kk * kUC + (cc ^ kk);
+                        if (kk < K && c < N) cp_async4(dst, Y + c * ldy + kk);
                         else *dst = 0.f;
                     }
-                }
             }
         }
         cp_async_commit();
     };
 #pragma unroll
-    for (int j = 0; j < kURing - 1; ++j) issue(j);
+    for (int j = 0; j < NST - 1; ++j) issue(j);
     for (long long t = 0; t < ntile; ++t) {
-        cp_async_wait<kURing - 2>();
+        cp_async_wait<NST - 2>();
         __syncthreads();
-        issue(t + kURing - 1);
-        const float* Cs = ring + (t % kURing) * kUStage;
-        const float* Ys = Cs + kKu * kLdT;
-        const float* Vs = Ys + kKu * kLdT;
-        const long long r0 = (t / nct) * kTile, c0 = (t % nct) * kTile;
-        float acc[4][2];
+        issue(t + NST - 1);
+        const float* Cs = ring + (t % NST) * SF;
+        const float* Ys = Cs + kUR * kUC;
+        const float* Vs = Ys + K4 * kUC;
+        const long long r0 = (t / nct) * kUR, c0 = (t % nct) * kUC;
+        float acc[2][8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.f;
-        for (int kk = 0; kk < K; ++kk) {
-            float va[4], yb[2];
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) va[a] = Vs[kk * kLdT + tm + 16 * a];
+            for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+        for (int k0 = 0; k0 < K4; k0 += 4) {
 #pragma unroll
-            for (int b = 0; b < 2; ++b) yb[b] = Ys[kk * kLdT + tn + 32 * b];
+            for (int u = 0; u < 4; ++u) {
+                const int kk = k0 + u;
+                const float va[2] = {Vs[kk * kUR + lane], Vs[kk * kUR + lane + 32]};
+                const float4 y0 = *reinterpret_cast<const float4*>(Ys + kk * kUC + ((8 * w) ^ k0));
+                const float4 y1 = *reinterpret_cast<const float4*>(Ys + kk * kUC + ((8 * w + 4) ^ k0));
+                const float yr[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(va[a], yb[b], acc[a][b]);
+                    for (int b = 0; b < 4; ++b) {
+                        acc[a][b] = fmaf(va[a], yr[b ^ u], acc[a][b]);
+                        acc[a][4 + b] = fmaf(va[a], yr[4 + (b ^ u)], acc[a][4 + b]);
+                    }
+            }
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 8; ++b)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int rr = tm + 16 * a, cc = tn + 32 * b;
-                const long long r = r0 + rr, c = c0 + cc;
-                if (r < M && c < N) C[c * ldc + r] = Cs[cc * kLdT + rr] - acc[a][b];
+            for (int a = 0; a < 2; ++a) {
+                const int r_ = lane + 32 * a, cc = 8 * w + b;
+                const long long r = r0 + r_, c = c0 + cc;
+                if (r < M && c < N) C[c * ldc + r] = Cs[cc * kUR + r_] - acc[a][b];
             }
     }
     cp_async_wait<0>();
     __syncthreads();  // the ring is reused by whatever follows
+}
+
+__device__ void blk_gemm_update(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
+                                long long ldy, long long M, long long N, long long K, const Smem& sm)
+{
+    if (M <= 0 || N <= 0) return;
+    const int K4 = (int)((K + 3) & ~3LL);
+    const int SF = kUR * kUC + K4 * (kUR + kUC);
+    if (3 * SF <= kURingFloats) blk_gemm_update_n<3>(C, ldc, V, ldv, maskV, Y, ldy, M, N, K, K4, sm);
+    else blk_gemm_update_n<2>(C, ldc, V, ldv, maskV, Y, ldy, M, N, K, K4, sm);
 }
 
 // Order key of a squared norm: non-negative doubles order as their bit patterns read as signed
@@ -705,7 +759,7 @@ __host__ __device__ inline size_t union_floats(long long m_max)
 {
     size_t f = (size_t)SW * (size_t)m_max;
     if (f < (size_t)kGemmFloats) f = kGemmFloats;
-    if (f < (size_t)kURing * kUStage) f = (size_t)kURing * kUStage;
+    if (f < (size_t)kURingFloats) f = (size_t)kURingFloats;
     return f;
 }
 
