@@ -7,6 +7,10 @@
 //               of rows t..l-1 recomputed while the reflector is applied, FP64 reflector;
 //   panel       left-looking in sub-panels of 8 columns held in shared memory, every
 //               reflector (norm, beta, tau) formed in FP64;
+//   sums        the per-term sums feeding norms and reflectors (column norms of B, the panel's
+//               dot products) are Dot2 sums of exact FP32 products carried as float pairs, then
+//               combined across the block in FP64: FP64-class results without a per-term FP64
+//               operation, which runs at a small fraction of the FP32 rate on this part;
 //   update      W = V^T [V C] (Gram and V^T C in one pass), T (xLARFT order, FP64),
 //               Y = T^T W, C -= V Y, tiled FP32 with compensated accumulation;
 //   Eq. (4)     Omega_hat_11 = R_hat11 R11^{-1} row by row, B(0:bb, trail) -= Omega_hat_11 R12.
@@ -43,14 +47,10 @@ struct Smem {
     float* vs;      // l_max reflector of the pivot search
     double* red;    // NW x SW block-reduction scratch
     double* sc;     // scalars: tau, beta, scal, guard, ...
+    float* scf;     // FP32 coefficients of the panel's rank-1 steps
     int* piv;       // b_max pivot targets
     long long* lpos;
 };
-
-__device__ __forceinline__ float vmask_f(float stored, long long q, long long r)
-{
-    return q > r ? stored : (q == r ? 1.f : 0.f);
-}
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
@@ -60,24 +60,49 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
     hi = t;
 }
 
-// Sum of NV doubles over the block; result in out[0..NV) for every thread (fixed order).
+// Dot2 step (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): the product's
+// rounding error (by FMA) and the sum's (TwoSum) go into lo, so hi + lo carries a sum of exact
+// FP32 products to about twice FP32 precision, with no FP64 arithmetic per term.
+__device__ __forceinline__ void dot2_acc(float& hi, float& lo, float x, float y)
+{
+    const float p = x * y;
+    const float pe = fmaf(x, y, -p);
+    const float t = hi + p;
+    const float z = t - hi;
+    lo += ((hi - (t - z)) + (p - z)) + pe;
+    hi = t;
+}
+
+// Sum of NV float-pair (hi + lo) values over the block, in fixed order: pairs are combined
+// across each warp with TwoSum (no FP64 instruction on 32 lanes), the NV warp totals by NV
+// threads in FP64.  out[i] (FP64) and, scaled by scale[i] when scale is given, outf[i] = (float)
+// (scale_i * out[i]) are visible to every thread on return.
 template <int NV>
-__device__ void block_sum(double (&v)[NV], double* red, double* out)
+__device__ void block_sum2(float (&h)[NV], float (&l)[NV], double* red, double* out, const double* scale = nullptr,
+                           float* outf = nullptr)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h[i], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, l[i], o);
+            const float t = h[i] + oh;
+            const float z = t - h[i];
+            l[i] += ol + ((h[i] - (t - z)) + (oh - z));
+            h[i] = t;
+        }
     }
     if (lane == 0)
 #pragma unroll
-        for (int i = 0; i < NV; ++i) red[w * NV + i] = v[i];
+        for (int i = 0; i < NV; ++i) red[w * NV + i] = (double)h[i] + (double)l[i];
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
         for (int ww = 0; ww < NW; ++ww) s += red[ww * NV + threadIdx.x];
         out[threadIdx.x] = s;
+        if (outf) outf[threadIdx.x] = (float)(scale[threadIdx.x] * s);
     }
     __syncthreads();
 }
@@ -409,12 +434,12 @@ __device__ int blk_pivot(float* B, long long n, int l, long long i, int bb, int3
 {
     const int tid = threadIdx.x;
     for (long long c = i + tid; c < n; c += BT) {
-        double s = 0.0;
+        float h = 0.f, lo = 0.f;
         for (int r = 0; r < l; ++r) {
-            const double x = B[(long long)r * n + c];
-            s += x * x;
+            const float x = B[(long long)r * n + c];
+            dot2_acc(h, lo, x, x);
         }
-        sm.nu[c] = s;
+        sm.nu[c] = (double)h + (double)lo;
     }
     __syncthreads();
     for (int t = 0; t < bb; ++t) {
@@ -474,21 +499,22 @@ __device__ int blk_pivot(float* B, long long n, int l, long long i, int bb, int3
         __syncthreads();
         for (int r = t + tid; r < l; r += BT) B[(long long)r * n + c0] = (r == t) ? (float)sm.sc[1] : 0.f;
         const float tauf = (float)tau;
+        const bool refl = tau != 0.0;
         for (long long c = c0 + 1 + tid; c < n; c += BT) {
             float w = 0.f;
-            if (tau != 0.0)
+            if (refl)
                 for (int r = t; r < l; ++r) w = fmaf(sm.vs[r], B[(long long)r * n + c], w);
             const float wt = w * tauf;
-            double nu = 0.0;
+            float h = 0.f, lo = 0.f;
             for (int r = t; r < l; ++r) {
                 float x = B[(long long)r * n + c];
-                if (tau != 0.0) {
+                if (refl) {
                     x = fmaf(-wt, sm.vs[r], x);
                     B[(long long)r * n + c] = x;
                 }
-                if (r > t) nu += (double)x * (double)x;
+                if (r > t) dot2_acc(h, lo, x, x);
             }
-            sm.nu[c] = nu;
+            sm.nu[c] = (double)h + (double)lo;
         }
         __syncthreads();
     }
@@ -507,37 +533,43 @@ __device__ void blk_panel(float* P, long long ldp, long long m1, int bb, double*
         __syncthreads();
         // earlier reflectors of this panel, in order
         for (int h = 0; h < s0; ++h) {
-            double v[SW];
+            float sh[SW], sl[SW];
 #pragma unroll
-            for (int cc = 0; cc < SW; ++cc) v[cc] = 0.0;
+            for (int cc = 0; cc < SW; ++cc) sh[cc] = sl[cc] = 0.f;
             const float* vh = P + (long long)h * ldp;
             for (long long r = h + tid; r < m1; r += BT) {
                 const float x = (r == h) ? 1.f : vh[r];
 #pragma unroll
                 for (int cc = 0; cc < SW; ++cc)
-                    if (cc < sw) v[cc] += (double)(x * sm.S[cc * m1 + r]);
+                    if (cc < sw) dot2_acc(sh[cc], sl[cc], x, sm.S[cc * m1 + r]);
             }
-            block_sum<SW>(v, sm.red, sm.sc + 16);
-            const double th = tau[h];
+            // coefficients tau_h * (v_h^T S(:, cc)), rounded to FP32 once
+            if (tid < SW) sm.sc[32 + tid] = tau[h];
+            block_sum2<SW>(sh, sl, sm.red, sm.sc + 16, sm.sc + 32, sm.scf);
+            float cf[SW];
+#pragma unroll
+            for (int cc = 0; cc < SW; ++cc) cf[cc] = sm.scf[cc];
             for (long long r = h + tid; r < m1; r += BT) {
                 const float x = (r == h) ? 1.f : vh[r];
-                for (int cc = 0; cc < sw; ++cc) sm.S[cc * m1 + r] -= (float)(th * sm.sc[16 + cc]) * x;
+#pragma unroll
+                for (int cc = 0; cc < SW; ++cc)
+                    if (cc < sw) sm.S[cc * m1 + r] -= cf[cc] * x;
             }
             __syncthreads();
         }
         // factor the sub-panel columns
         for (int jj = 0; jj < sw; ++jj) {
             const long long j = s0 + jj;  // panel row/column index of the diagonal
-            double v[SW];
+            float sh[SW], sl[SW];
 #pragma unroll
-            for (int cc = 0; cc < SW; ++cc) v[cc] = 0.0;
+            for (int cc = 0; cc < SW; ++cc) sh[cc] = sl[cc] = 0.f;
             for (long long r = j + 1 + tid; r < m1; r += BT) {
                 const float x = sm.S[jj * m1 + r];
 #pragma unroll
                 for (int cc = 0; cc < SW; ++cc)
-                    if (cc >= jj && cc < sw) v[cc] += (double)(x * sm.S[cc * m1 + r]);
+                    if (cc >= jj && cc < sw) dot2_acc(sh[cc], sl[cc], x, sm.S[cc * m1 + r]);
             }
-            block_sum<SW>(v, sm.red, sm.sc + 16);
+            block_sum2<SW>(sh, sl, sm.red, sm.sc + 16);
             if (tid == 0) {
                 const double alpha = sm.S[jj * m1 + j];
                 const double ss = sm.sc[16 + jj];
@@ -552,19 +584,26 @@ __device__ void blk_panel(float* P, long long ldp, long long m1, int bb, double*
                 sm.sc[1] = beta;
                 sm.sc[2] = scal;
                 tau[j] = tj;
-                for (int cc = jj + 1; cc < sw; ++cc)
-                    sm.sc[24 + cc] = tj * ((double)sm.S[cc * m1 + j] + scal * sm.sc[16 + cc]);
+                sm.scf[SW] = (float)scal;
+                for (int cc = 0; cc < SW; ++cc)
+                    sm.scf[cc] = (cc > jj && cc < sw)
+                                     ? (float)(tj * ((double)sm.S[cc * m1 + j] + scal * sm.sc[16 + cc])) : 0.f;
             }
             __syncthreads();
-            const double tj = sm.sc[0], scal = sm.sc[2];
-            if (tj != 0.0) {
+            if (sm.sc[0] != 0.0) {
+                const float scalf = sm.scf[SW];
+                float cf[SW];
+#pragma unroll
+                for (int cc = 0; cc < SW; ++cc) cf[cc] = sm.scf[cc];
                 for (long long r = j + 1 + tid; r < m1; r += BT) {
-                    const float vr = (float)((double)sm.S[jj * m1 + r] * scal);
+                    const float vr = sm.S[jj * m1 + r] * scalf;
                     sm.S[jj * m1 + r] = vr;
-                    for (int cc = jj + 1; cc < sw; ++cc) sm.S[cc * m1 + r] -= (float)sm.sc[24 + cc] * vr;
+#pragma unroll
+                    for (int cc = 0; cc < SW; ++cc)
+                        if (cc > jj && cc < sw) sm.S[cc * m1 + r] -= cf[cc] * vr;
                 }
                 if (tid == 0)
-                    for (int cc = jj + 1; cc < sw; ++cc) sm.S[cc * m1 + j] -= (float)sm.sc[24 + cc];
+                    for (int cc = jj + 1; cc < sw; ++cc) sm.S[cc * m1 + j] -= cf[cc];
             }
             __syncthreads();
             if (tid == 0) sm.S[jj * m1 + j] = (float)sm.sc[1];
@@ -636,11 +675,12 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
     double mx = 0.0;
     bool finite = true;
     for (long long c = tid; c < n; c += BT) {
-        double s = 0.0;
+        float h = 0.f, lo = 0.f;
         for (int r = 0; r < l; ++r) {
-            const double x = Bw[(long long)r * n + c];
-            s += x * x;
+            const float x = Bw[(long long)r * n + c];
+            dot2_acc(h, lo, x, x);
         }
+        const double s = (double)h + (double)lo;
         finite = finite && isfinite(s);
         mx = fmax(mx, s);
     }
@@ -786,6 +826,7 @@ __global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restr
     sm.vs = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)l_max));
     sm.red = reinterpret_cast<double*>(carve(sizeof(double) * NW * SW));
     sm.sc = reinterpret_cast<double*>(carve(sizeof(double) * 40));
+    sm.scf = reinterpret_cast<float*>(carve(sizeof(float) * (SW + 1)));
     sm.piv = reinterpret_cast<int*>(carve(sizeof(int) * (size_t)b_max));
     sm.lpos = reinterpret_cast<long long*>(carve(sizeof(long long) * (NW + 1)));
 
@@ -815,6 +856,7 @@ size_t batched_smem_bytes(long long m_max, long long n_max, int b_max, int p)
     take(sizeof(float) * (size_t)(b_max + p));
     take(sizeof(double) * NW * SW);
     take(sizeof(double) * 40);
+    take(sizeof(float) * (SW + 1));
     take(sizeof(int) * (size_t)b_max);
     take(sizeof(long long) * (NW + 1));
     return off;
