@@ -492,7 +492,7 @@ def run_batched(args, w, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     p = w["p"]
-    shapes = inputs.batched_shapes(512, seed=0)
+    shapes = inputs.batched_shapes(args.count, seed=0)
     table = autotune.load_or_tune(shapes, p=p)
     bs = [autotune.choose(table, m, n, k) for (m, n, k) in shapes]
     mats = []
@@ -575,7 +575,9 @@ def run_batched(args, w, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["desc"], "count": len(shapes), "p": p, "b_histogram":
+        "config": {"workload": w["desc"] if args.count == 512 else
+                   w["desc"].replace("512 FP32 matrices", f"the first {args.count} of the 512 FP32 matrices"),
+                   "count": len(shapes), "p": p, "b_histogram":
                    {str(b): int(c) for b, c in zip(*np.unique(bs, return_counts=True))},
                    "counted_gflop_per_step": round(F / 1e9, 3), "bytes_per_step": nbytes,
                    "l2": "inputs larger than L2: 2.6 GB of matrices restored before every step",
@@ -600,6 +602,9 @@ def main():
     ap.add_argument("--workload", default="fp64_8192_iid", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=512,
+                    help="batched workload only: factor the first COUNT matrices of the 512-matrix draw "
+                         "(a smaller case for profiling; the workload is 512)")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other form (mixed / plain FP64) on the same matrix")
     args = ap.parse_args()
