@@ -2,7 +2,8 @@
 // launch.  Every block (one per SM) repeatedly takes the next matrix from a work queue (an
 // atomic counter over a caller-given order, largest first) and factors that matrix alone,
 // with block-level synchronisation only:
-//   sketch      B = Omega(0:l, 0:m) A, tiled FP32 contraction, B kept row-major (ld = n);
+//   sketch      B = Omega(0:l, 0:m) A on the tensor cores (tcgen05, 3xTF32, accumulator in
+//               tensor memory, per-chunk read-back with compensated sums), B row-major (ld = n);
 //   pivots      Alg. 1 on B with physical column swaps (ties to the smallest position), norms
 //               of rows t..l-1 recomputed while the reflector is applied, FP64 reflector;
 //   panel       left-looking in sub-panels of 8 columns held in shared memory, every
@@ -12,10 +13,10 @@
 //               combined across the block in FP64: FP64-class results without a per-term FP64
 //               operation, which runs at a small fraction of the FP32 rate on this part;
 //   update      W = V^T [V C] (Gram and V^T C in one pass), T (xLARFT order, FP64),
-//               Y = T^T W, C -= V Y, tiled FP32 with compensated accumulation;
+//               Y = T^T W, C -= V Y, tiled FP32 SIMT with compensated accumulation;
 //   Eq. (4)     Omega_hat_11 = R_hat11 R11^{-1} row by row, B(0:bb, trail) -= Omega_hat_11 R12.
 // FP32 storage (the mixed form); the rank guard of the single-matrix path applies per matrix.
-#include "internal.cuh"
+#include "tc_common.cuh"
 
 namespace rq {
 
@@ -39,6 +40,9 @@ constexpr int kLdT = kTile + 1;  // padded shared-memory tile stride
 
 struct Smem {
     float* G;       // union: the panel's sub-panel S, or the contractions' ring / tiles
+    uint64_t* mbar; // two mbarriers: tensor-core MMA completion per accumulator buffer
+    int* mph;       // completed phases of the two mbarriers
+    uint32_t tmem;  // tensor memory of the block (kTmemCols columns)
     float* S;       // SW x m_max sub-panel
     double* nu;     // n_max sketch norms
     double* Tm;     // b_max x b_max: T, then Omega_hat_11
@@ -254,13 +258,212 @@ __device__ void blk_gemm_tn_rt(const float* X, long long ldx, int maskX, const f
         }
 }
 
-__device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
-                            long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
-                            const Smem& sm)
+// ---- tensor-core form of the contraction (tcgen05, 3xTF32) ----
+// Out(M x N) = X^T C as D = C^T X on the tensor cores, one 128-column tile of C at a time: the
+// MMA's A operand is a 128 x 32 chunk of C (lane = column c, K = 32 rows), its B operand the
+// NB x 32 chunk of X (NB = M rounded up to 16), both K-major with the 128-byte swizzle in shared
+// memory.  cp.async writes each chunk's raw FP32 values straight into their swizzled places (the
+// unit-lower structure and the edges by direct stores); a pass over the stage then splits every
+// value in place into x_hi = tf32(x) and, next to it, x_lo = tf32(x - x_hi).  B is [X_hi; X_lo]
+// (2 NB lines), so a chunk is eight MMAs of N = 2 NB: A_lo first, then A_hi, against both halves
+// (all four products; lo lo is below the others' rounding).  The accumulator (double-buffered in
+// tensor memory) only ever holds one chunk's products; each is read back by all 16 warps (warp w:
+// lane quarter w % 4, column quarter w / 4) and summed in FP32 registers, with a compensated fold
+// every 16 chunks, as in the single-matrix 3xTF32 contraction.  Every wait is bounded.
+constexpr int kTmemCols = 512;
+constexpr int kTcA = 128 * 32 * 4;  // one 128-line x 32-element TF32 tile (16 KB)
+constexpr int kTcNbMax = 96;
+constexpr int kTcRing = 3;
+__host__ __device__ constexpr int tc_stage_bytes(int nb) { return 2 * kTcA + 2 * nb * 128; }
+
+// Byte offset of element (line, k) of a K-major tile of 32-element (128-byte) lines with the
+// 128-byte swizzle: 16-byte piece k / 4 of line `line` sits at piece (k / 4) ^ (line % 8).
+__device__ __forceinline__ int sw128(int line, int k)
 {
+    return line * 128 + ((((k >> 2) ^ line) & 7) << 4) + ((k & 3) << 2);
+}
+
+template <int CQ>
+__device__ bool blk_gemm_tn_tc(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
+                               long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
+                               const Smem& sm)
+{
+    using namespace tc;
+    constexpr int NB = 4 * CQ;
+    constexpr int SB = tc_stage_bytes(NB);
+    constexpr int XO = 2 * kTcA;  // offset of [X_hi; X_lo] in a stage
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the ring starts at the first 1024-byte boundary of the region (the swizzle atoms)
+    unsigned char* ring = reinterpret_cast<unsigned char*>(sm.G) + ((1024u - (su32(sm.G) & 1023u)) & 1023u);
+    const long long nsl = (K + 31) / 32;
+    uint32_t ph[2] = {(uint32_t)sm.mph[0], (uint32_t)sm.mph[1]};
+    const uint32_t idesc = idesc_tf32(128, 2 * NB);
+    const int qd = warp & 3, hd = warp >> 2;  // drain: lane quarter, column quarter
+    const int kk = tid & 31, l0 = tid >> 5;   // copies: k of the chunk, first line
+    bool ok = true;
+    uint32_t g = 0;  // chunks issued in this call: accumulator buffer g & 1
+    for (long long n0 = 0; n0 < N && ok; n0 += 128) {
+        auto issue = [&](long long j) {
+            if (j < nsl) {
+                unsigned char* st = ring + (j % kTcRing) * SB;
+                const long long q = j * 32 + kk;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int cl = l0 + 16 * it;
+                    const long long c = n0 + cl;
+                    float* dst = reinterpret_cast<float*>(st + sw128(cl, kk));
+                    if (q >= K || c >= N) *dst = 0.f;
+                    else if (c < maskC && q <= c) *dst = q == c ? 1.f : 0.f;
+                    else cp_async4(dst, C + c * ldc + q);
+                }
+#pragma unroll
+                for (int it = 0; it < NB / 16; ++it) {
+                    const int r = l0 + 16 * it;
+                    float* dst = reinterpret_cast<float*>(st + XO + sw128(r, kk));
+                    if (q >= K || r >= M) *dst = 0.f;
+                    else if (maskX && q <= r) *dst = q == r ? 1.f : 0.f;
+                    else cp_async4(dst, X + (long long)r * ldx + q);
+                }
+            }
+            cp_async_commit();
+        };
+        float acc[CQ], sum[CQ];
+#pragma unroll
+        for (int j = 0; j < CQ; ++j) acc[j] = sum[j] = 0.f;
+        // read back chunk gg's products (both halves) and add them to acc
+        auto drain = [&](uint32_t gg) -> bool {
+            const int b = (int)(gg & 1u);
+            const bool w_ok = mbar_wait(&sm.mbar[b], ph[b] & 1u, nullptr);
+            ++ph[b];
+            if (__syncthreads_or(w_ok ? 0 : 1)) return false;
+            fence_after();
+            const uint32_t tb = sm.tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * 2 * NB + hd * CQ);
+            // groups of up to 8 columns: both halves' loads in flight, one wait per group
+#pragma unroll
+            for (int g0 = 0; g0 < CQ; g0 += 8) {
+                uint32_t rh[8], rl[8];
+#pragma unroll
+                for (int c0 = 0; c0 < 8; c0 += 4) {
+                    if (g0 + c0 < CQ) {
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                     : "=r"(rh[c0]), "=r"(rh[c0 + 1]), "=r"(rh[c0 + 2]), "=r"(rh[c0 + 3])
+                                     : "r"(tb + (uint32_t)(g0 + c0)));
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                     : "=r"(rl[c0]), "=r"(rl[c0 + 1]), "=r"(rl[c0 + 2]), "=r"(rl[c0 + 3])
+                                     : "r"(tb + (uint32_t)(NB + g0 + c0)));
+                    }
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (g0 + u < CQ) acc[g0 + u] += __uint_as_float(rl[u]) + __uint_as_float(rh[u]);
+            }
+            fence_before();
+            return true;
+        };
+        auto fold = [&]() {  // (sum, acc) = TwoSum(sum, acc)
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) {
+                const float t = sum[j] + acc[j];
+                const float z = t - sum[j];
+                acc[j] = (sum[j] - (t - z)) + (acc[j] - z);
+                sum[j] = t;
+            }
+        };
+        issue(0);
+        issue(1);
+        long long j = 0;
+        for (; j < nsl; ++j) {
+            cp_async_wait<1>();  // this thread's copies of chunk j have landed
+            __syncthreads();
+            unsigned char* st = ring + (j % kTcRing) * SB;
+            for (int e = tid; e < 1024 + NB * 8; e += BT) {
+                float4* p = e < 1024 ? reinterpret_cast<float4*>(st) + e : reinterpret_cast<float4*>(st + XO) + (e - 1024);
+                float4* pl = e < 1024 ? p + 1024 : p + NB * 8;
+                const float4 v = *p;
+                float4 hv, lv;
+                hv.x = tf32_rn(v.x);
+                hv.y = tf32_rn(v.y);
+                hv.z = tf32_rn(v.z);
+                hv.w = tf32_rn(v.w);
+                lv.x = tf32_rn(v.x - hv.x);
+                lv.y = tf32_rn(v.y - hv.y);
+                lv.z = tf32_rn(v.z - hv.z);
+                lv.w = tf32_rn(v.w - hv.w);
+                *p = hv;
+                *pl = lv;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                fence_after();
+                const int b = (int)(g & 1u);
+                const uint64_t da = umma_desc(st), dal = umma_desc(st + kTcA), dx = umma_desc(st + XO);
+                const uint32_t td = sm.tmem + (uint32_t)(b * 2 * NB);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mma_tf32_ss(td, dal + 2 * k, dx + 2 * k, idesc, k > 0 ? 1 : 0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mma_tf32_ss(td, da + 2 * k, dx + 2 * k, idesc, 1);
+                mma_commit(&sm.mbar[b]);
+            }
+            ++g;
+            if (j > 0) {
+                if (!drain(g - 2)) {
+                    ok = false;
+                    break;
+                }
+                if (j % 16 == 0) fold();
+            }
+            issue(j + 2);  // into the stage chunk j - 1 used; its MMAs have completed
+        }
+        if (ok && nsl > 0 && !drain(g - 1)) ok = false;
+        cp_async_wait<0>();
+        __syncthreads();
+        if (!ok) break;
+        fold();
+        const long long c = n0 + 32 * qd + lane;
+#pragma unroll
+        for (int jj = 0; jj < CQ; ++jj) {
+            const long long r = hd * CQ + jj;
+            if (r < M && c < N) {
+                const float v = sum[jj] + acc[jj];
+                if (out_rowmajor) Out[r * ldo + c] = v;
+                else Out[c * ldo + r] = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        sm.mph[0] = (int)ph[0];
+        sm.mph[1] = (int)ph[1];
+    }
+    __syncthreads();
+    return ok;
+}
+
+// tensor == 1 and M <= kTcNbMax: the tensor-core form; false only if a tensor-core wait timed
+// out.  The sketch (Omega shared by all blocks, resident in L2; M = b + p rows would waste up to
+// half of a SIMT tile) runs on the tensor cores; the Gram V^T [V C] stays on the SIMT form, which
+// keeps more bytes in flight per block than the tensor-core stages (raw, hi and lo parts) allow.
+__device__ bool blk_gemm_tn(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
+                            long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
+                            const Smem& sm, int tensor)
+{
+    if (M <= 0 || N <= 0) return true;
+    if (tensor && M <= kTcNbMax) {
+        switch ((int)((M + 15) / 16)) {
+        case 1: return blk_gemm_tn_tc<4>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+        case 2: return blk_gemm_tn_tc<8>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+        case 3: return blk_gemm_tn_tc<12>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+        case 4: return blk_gemm_tn_tc<16>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+        case 5: return blk_gemm_tn_tc<20>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+        default: return blk_gemm_tn_tc<24>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+        }
+    }
     if (M <= 16) blk_gemm_tn_rt<16>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
     else if (M <= 32) blk_gemm_tn_rt<32>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
     else blk_gemm_tn_rt<64>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+    return true;
 }
 
 // C(M x N) -= V(M x K) Y(K x N), column-major, K <= 64; V with the optional unit-lower
@@ -274,6 +477,7 @@ __device__ void blk_gemm_tn(const float* X, long long ldx, int maskX, const floa
 // holds 8192 + 192 K4 floats, three of them when they fit in kURingFloats, else two.
 constexpr int kUR = 64, kUC = 128;
 constexpr int kURingFloats = 3 * (kUR * kUC + 32 * (kUR + kUC));
+static_assert(kTcRing * tc_stage_bytes(kTcNbMax) <= kURingFloats * 4, "tensor-core ring exceeds the shared region");
 
 template <int NST>
 __device__ void blk_gemm_update_n(float* C, long long ldc, const float* V, long long ldv, int maskV, const float* Y,
@@ -659,7 +863,8 @@ __device__ void blk_bsolve(const float* B, long long n, const float* A, long lon
     __syncthreads();
 }
 
-__device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, int p, float* Bw, float* Ww, float* Yw,
+// Factors one matrix; false if a tensor-core wait timed out (the matrix's rank is then -2).
+__device__ bool factor_one(const BatchDesc& d, const float* Om, long long ldo, int p, float* Bw, float* Ww, float* Yw,
                            const Smem& sm)
 {
     const int tid = threadIdx.x;
@@ -669,7 +874,11 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
     float* A = d.A;
     for (long long c = tid; c < n; c += BT) d.jpvt[c] = (int32_t)c;
     // sketch B = Omega(0:l, 0:m) A, row-major l x n
-    blk_gemm_tn(Om, ldo, 0, A, lda, 0, l, n, m, Bw, n, 1, sm);
+    if (!blk_gemm_tn(Om, ldo, 0, A, lda, 0, l, n, m, Bw, n, 1, sm, 1)) {
+        if (tid == 0) *d.rank = -2;
+        __syncthreads();
+        return false;
+    }
     __syncthreads();
     // largest initial sketch column norm^2 and finiteness
     double mx = 0.0;
@@ -691,7 +900,7 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
     if (!all_finite) {
         if (tid == 0) *d.rank = -1;
         __syncthreads();
-        return;
+        return true;
     }
     const double gtol = 10.0 * sqrt((double)(m > n ? m : n)) * 5.9604644775390625e-08;
     const double guard = gtol * gtol * bv;
@@ -724,7 +933,11 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
         const long long nt = n - i - bb;
         if (nt <= 0) continue;
         // W = V^T [V C] (bb x (n-i), column-major ld bb), T, Y = T^T W(:, bb:), C -= V Y
-        blk_gemm_tn(Vp, lda, 1, Vp, lda, bb, bb, n - i, m1, Ww, bb, 0, sm);
+        if (!blk_gemm_tn(Vp, lda, 1, Vp, lda, bb, bb, n - i, m1, Ww, bb, 0, sm, 0)) {
+            if (tid == 0) *d.rank = -2;
+            __syncthreads();
+            return false;
+        }
         __syncthreads();
         blk_tform(Ww, bb, d.tau + i, sm);
         {
@@ -791,6 +1004,7 @@ __device__ void factor_one(const BatchDesc& d, const float* Om, long long ldo, i
     }
     if (tid == 0) *d.rank = rank;
     __syncthreads();
+    return true;
 }
 
 // The panel's sub-panel and the contractions' shared-memory buffers are never live at the
@@ -817,7 +1031,7 @@ __global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restr
         return ptr;
     };
     const int l_max = b_max + p;
-    sm.G = reinterpret_cast<float*>(carve(sizeof(float) * union_floats(m_max)));
+    sm.G = reinterpret_cast<float*>(carve(sizeof(float) * union_floats(m_max) + 1024));  // + room to align the tensor-core ring
     sm.S = sm.G;
     sm.Xs = sm.G;
     sm.Cs = sm.G + kKu * kLdT;
@@ -834,6 +1048,24 @@ __global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restr
     float* Bw = reinterpret_cast<float*>(mine);
     float* Ww = Bw + (size_t)l_max * n_max;
     float* Yw = Ww + (size_t)b_max * (n_max + b_max);
+    // tensor memory (the whole of it: one block per SM) and the two MMA-completion barriers
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ int s_mph[2];
+    __shared__ uint32_t s_tmem;
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&s_tmem, kTmemCols);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_mbar[0], 1);
+        tc::mbar_init(&s_mbar[1], 1);
+        s_mph[0] = s_mph[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    sm.mbar = s_mbar;
+    sm.mph = s_mph;
+    sm.tmem = s_tmem;
+
     __shared__ int s_next;
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
@@ -842,15 +1074,19 @@ __global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchDesc* __restr
         __syncthreads();
         if (idx >= count) break;
         const BatchDesc d = descs[order[idx]];
-        factor_one(d, Om, ldo, p, Bw, Ww, Yw, sm);
+        if (!factor_one(d, Om, ldo, p, Bw, Ww, Yw, sm)) break;  // a tensor-core wait timed out
     }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(sm.tmem, kTmemCols);
 }
 
 size_t batched_smem_bytes(long long m_max, long long n_max, int b_max, int p)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~(size_t)15; };
-    take(sizeof(float) * union_floats(m_max));
+    take(sizeof(float) * union_floats(m_max) + 1024);
     take(sizeof(double) * (size_t)n_max);
     take(sizeof(double) * (size_t)b_max * b_max);
     take(sizeof(float) * (size_t)(b_max + p));
