@@ -215,11 +215,14 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  * matrix from an atomic counter and factors it alone.  All matrices share one FP32 sketching
  * matrix Omega (l_max x m_max, l_max = b_max + p, drawn from `seed` as rqrcp_generate_omega_f32);
  * matrix i uses its leading (b_i + p) x m_i block.  Per-matrix results as rqrcp_factor_mixed;
- * rank is -1 when the sketch of that matrix is not finite.  The call is two kernels and a
- * memset on `stream` and allocates nothing (graph-capturable).  `work` needs
- * rqrcp_batched_workspace_size(m_max, n_max, b_max, p) bytes.  Limits: SW * m_max floats
- * (SW = 8) and n_max doubles must fit in one block's shared memory (m_max <= ~5000 for
- * n_max = 2048), else RQRCP_ERR_UNSUPPORTED.
+ * rank is -1 when the sketch of that matrix is not finite, and -2 when a tensor-core wait of
+ * the block factoring it gave up after 2 s (that block then stops taking matrices; the others
+ * finish the batch; matrices never taken keep rank 0).  The call is two kernels and a memset on
+ * `stream` and allocates nothing (graph-capturable).  Each block holds all of its SM's tensor
+ * memory for the launch.  `work` needs rqrcp_batched_workspace_size(m_max, n_max, b_max, p)
+ * bytes.  Limits: the block's shared memory (max(8 m_max floats, 168 KB) + n_max doubles +
+ * b_max^2 doubles + ~3 KB) must fit, else RQRCP_ERR_UNSUPPORTED (m_max <= ~5600 with
+ * n_max = 2048, b_max = 64).
  */
 size_t rqrcp_batched_workspace_size(int64_t m_max, int64_t n_max, int64_t b_max, int64_t p);
 int rqrcp_factor_batched(int64_t count, const void* descs, const int* order, int64_t m_max, int64_t n_max,
