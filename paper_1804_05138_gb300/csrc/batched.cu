@@ -682,15 +682,9 @@ __device__ int blk_pivot(float* B, long long n, int l, long long i, int bb, int3
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            double tau, beta, scal;
+            warp_larfg((double)B[(long long)t * n + c0], ss, tau, beta, scal);
             if (tid == 0) {
-                const double alpha = B[(long long)t * n + c0];
-                double tau = 0.0, beta = alpha, scal = 0.0;
-                if (ss != 0.0) {
-                    const double nrm = sqrt(alpha * alpha + ss);
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    tau = (beta - alpha) / beta;
-                    scal = 1.0 / (alpha - beta);
-                }
                 sm.sc[0] = tau;
                 sm.sc[1] = beta;
                 sm.sc[2] = scal;
@@ -774,24 +768,20 @@ __device__ void blk_panel(float* P, long long ldp, long long m1, int bb, double*
                     if (cc >= jj && cc < sw) dot2_acc(sh[cc], sl[cc], x, sm.S[cc * m1 + r]);
             }
             block_sum2<SW>(sh, sl, sm.red, sm.sc + 16);
-            if (tid == 0) {
-                const double alpha = sm.S[jj * m1 + j];
-                const double ss = sm.sc[16 + jj];
-                double tj = 0.0, beta = alpha, scal = 0.0;
-                if (ss != 0.0) {
-                    const double nrm = sqrt(alpha * alpha + ss);
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    tj = (beta - alpha) / beta;
-                    scal = 1.0 / (alpha - beta);
+            if (tid < 32) {
+                double tj, beta, scal;
+                warp_larfg((double)sm.S[jj * m1 + j], sm.sc[16 + jj], tj, beta, scal);
+                // lane cc: the FP32 coefficient tau * v^T a_cc of the update of column cc
+                if (tid < SW)
+                    sm.scf[tid] = (tid > jj && tid < sw)
+                                      ? (float)(tj * ((double)sm.S[tid * m1 + j] + scal * sm.sc[16 + tid])) : 0.f;
+                if (tid == 0) {
+                    sm.sc[0] = tj;
+                    sm.sc[1] = beta;
+                    sm.sc[2] = scal;
+                    tau[j] = tj;
+                    sm.scf[SW] = (float)scal;
                 }
-                sm.sc[0] = tj;
-                sm.sc[1] = beta;
-                sm.sc[2] = scal;
-                tau[j] = tj;
-                sm.scf[SW] = (float)scal;
-                for (int cc = 0; cc < SW; ++cc)
-                    sm.scf[cc] = (cc > jj && cc < sw)
-                                     ? (float)(tj * ((double)sm.S[cc * m1 + j] + scal * sm.sc[16 + cc])) : 0.f;
             }
             __syncthreads();
             if (sm.sc[0] != 0.0) {

@@ -12,8 +12,7 @@ struct Status {
     int error;                     // RQRCP_OK or an RQRCP_ERR_* code set by a kernel
     int guard;                     // 1 once the rank guard fired
     long long rank;                // pivots chosen before the guard fired
-    unsigned int bar_count;        // grid barrier arrival counter
-    unsigned int bar_gen;          // grid barrier generation
+    unsigned long long bar;        // grid barrier: arrivals (low 32 bits), generation (high 32 bits)
     unsigned long long nu0bits;    // bits of the largest initial sketch column norm^2 (>= 0)
     long long pad[12];
 };
@@ -38,46 +37,78 @@ __device__ __forceinline__ void set_error(Status* st, int code)
     atomicCAS(&st->error, 0, code);
 }
 
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p)
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p)
 {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Grid-wide barrier for cooperatively launched kernels: one arrival counter and a generation
-// word polled with acquire loads.  Every wait is bounded: after kWaitLimitNs the block records
-// RQRCP_ERR_TIMEOUT and the barrier returns false, as it does when any block has recorded an
-// error; callers then leave the kernel.
+// Waits longer than this also watch the status word (a block that met an error has left).
+constexpr unsigned long long kErrorWatchNs = 20000;
+
+// Grid-wide barrier for cooperatively launched kernels.  One 64-bit word holds the arrivals of
+// the current barrier (low half) and its generation (high half).  A block arrives with one
+// acquire-release add, which also tells it the generation; the last arrival resets the count
+// and opens the next generation with a single release add of 2^32 - G; the others poll the word
+// with acquire loads.  The count is back at 0 after every barrier, so launches of any grid size
+// can share the word.  Every wait is bounded: a wait longer than kErrorWatchNs returns false as
+// soon as any block has recorded an error, and after kWaitLimitNs the block records
+// RQRCP_ERR_TIMEOUT and returns false; callers then leave the kernel.
 __device__ __forceinline__ bool grid_barrier(Status* st)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int gen = ld_acquire_gpu(&st->bar_gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        const unsigned long long G = gridDim.x;
+        unsigned long long old;
+        asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(&st->bar), "l"(1ull) : "memory");
+        const unsigned int gen = (unsigned int)(old >> 32);
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
+        if ((old & 0xffffffffull) == G - 1) {
+            asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&st->bar), "l"((1ull << 32) - G) : "memory");
         } else {
             const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_gpu(&st->bar_gen) == gen) {
-                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            while ((unsigned int)(ld_acquire_gpu(&st->bar) >> 32) == gen) {
+                const unsigned long long dt = globaltimer_ns() - t0;
+                if (dt > kErrorWatchNs && status_error(st)) {
+                    ok = 0;
+                    break;
+                }
+                if (dt > kWaitLimitNs) {
                     set_error(st, RQRCP_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
             }
         }
-        __threadfence();
-        if (status_error(st)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Householder scalars (xLARFG convention) from alpha = x(1) and ss = ||x(2:)||^2, in FP64,
+// computed by a whole warp: beta = -sign(alpha) sqrt(alpha^2 + ss), and the two divisions
+// tau = (beta - alpha) / beta and scal = 1 / (alpha - beta) run on lanes 0 and 1 at once (FP64
+// division and square root are long dependent chains on this part).  ss = 0 gives tau = scal = 0
+// and beta = alpha.  All 32 lanes must call it with the same alpha and ss; every lane gets the
+// results.
+__device__ __forceinline__ void warp_larfg(double alpha, double ss, double& tau, double& beta, double& scal)
+{
+    beta = alpha;
+    tau = 0.0;
+    scal = 0.0;
+    if (ss != 0.0) {
+        const int lane = threadIdx.x & 31;
+        const double nrm = sqrt(alpha * alpha + ss);
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        const double num = lane == 0 ? beta - alpha : 1.0;
+        const double den = lane == 0 ? beta : alpha - beta;
+        const double q = num / den;
+        tau = __shfl_sync(0xffffffffu, q, 0);
+        scal = __shfl_sync(0xffffffffu, q, 1);
+    }
 }
 
 template <typename T>

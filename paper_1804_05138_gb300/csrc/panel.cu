@@ -12,6 +12,8 @@
 //      a_k -= (tau * v^T a_k) v, with v^T a_k = a_k(j) + scal * (x^T a_k) from the partials.
 // Partials and the diagonal row are double-buffered by the parity of j, so one barrier per
 // column suffices.
+#include <cstdlib>
+
 #include "internal.cuh"
 
 namespace rq {
@@ -45,8 +47,24 @@ __device__ __forceinline__ double sum_partials(const double* p, int G, int start
     return s;
 }
 
+// Sum of red[c * bbp + k] over c < nchunk, even and odd c in two chains, fixed order.
+__device__ __forceinline__ double sum_chunks(const double* red, int nchunk, int bbp, int k)
+{
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c + 1 < nchunk; c += 2) {
+        a += red[c * bbp + k];
+        b += red[(c + 1) * bbp + k];
+    }
+    if (nchunk & 1) a += red[(nchunk - 1) * bbp + k];
+    return a + b;
+}
+
+// 256 threads: measured faster per column than 512 (the cross-block sums dominate, not the
+// per-row work).
+constexpr int kPanelThreads = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t lda, int64_t m1, int bb,
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(T* __restrict__ A, int64_t lda, int64_t m1, int bb,
                                                     int64_t rpb, double* __restrict__ tau,
                                                     double* __restrict__ part, Status* st)
 {
@@ -55,7 +73,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
     extern __shared__ __align__(16) double S[];
     const int ldS = (int)(rpb | 1);
     const int bbp = pow2_at_least(bb);   // threads per row-chunk group
-    const int nchunk = NTH / bbp;        // >= 1 because bb <= 256 and NTH == 256
+    const int nchunk = NTH / bbp;        // >= 1 because bb <= 256 < NTH
     double* red = S + (size_t)ldS * bb;  // nchunk x bbp
     double* wk = red + (size_t)nchunk * bbp;
     double* sums = wk + bbp;
@@ -83,11 +101,7 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
             red[chunk * bbp + kidx] = s;
         }
         __syncthreads();
-        if (tid < nk) {
-            double s = 0.0;
-            for (int c = 0; c < nchunk; ++c) s += red[c * bbp + tid];
-            part[((size_t)buf * G + g) * bb + tid] = s;
-        }
+        if (tid < nk) part[((size_t)buf * G + g) * bb + tid] = sum_chunks(red, nchunk, bbp, tid);
         if (r0 <= j && j < r0 + nrow) {
             const int rj = (int)(j - r0);
             for (int kk = tid; kk < nk; kk += NTH) diag[(size_t)buf * bb + kk] = S[(size_t)(j + kk) * ldS + rj];
@@ -103,26 +117,17 @@ __global__ void __launch_bounds__(256) panel_kernel(T* __restrict__ A, int64_t l
             if (tid < nk) dg[tid] = ld_cg(&diag[(size_t)buf * bb + tid]);
         }
         __syncthreads();
-        if (tid < nk) {
-            double s = 0.0;
-            for (int c = 0; c < nchunk; ++c) s += red[c * bbp + tid];
-            sums[tid] = s;
-        }
+        if (tid < nk) sums[tid] = sum_chunks(red, nchunk, bbp, tid);
         __syncthreads();
-        if (tid == 0) {
-            const double alpha = dg[0];
-            const double ss = sums[0];
-            double tj = 0.0, beta = alpha, scal = 0.0;
-            if (ss != 0.0) {
-                const double nrm = sqrt(alpha * alpha + ss);
-                beta = (alpha >= 0.0) ? -nrm : nrm;
-                tj = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
+        if (tid < 32) {
+            double tj, beta, scal;
+            warp_larfg(dg[0], sums[0], tj, beta, scal);
+            if (tid == 0) {
+                sh_tau = tj;
+                sh_beta = beta;
+                sh_scal = scal;
+                if (g == 0) tau[j] = tj;
             }
-            sh_tau = tj;
-            sh_beta = beta;
-            sh_scal = scal;
-            if (g == 0) tau[j] = tj;
         }
         __syncthreads();
         if (tid > 0 && tid < nk) wk[tid] = sh_tau * (dg[tid] + sh_scal * sums[tid]);
@@ -164,7 +169,7 @@ __device__ __forceinline__ void dot2_acc(float x, float y, float& s, float& c)
     c += q + e;
 }
 
-__global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, int64_t lda, int64_t m1, int bb,
+__global__ void __launch_bounds__(kPanelThreads) panel_f32_kernel(float* __restrict__ A, int64_t lda, int64_t m1, int bb,
                                                         int64_t rpb, double* __restrict__ tau,
                                                         double* __restrict__ part, Status* st)
 {
@@ -201,11 +206,7 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
             red[chunk * bbp + kidx] = (double)sacc + (double)cacc;
         }
         __syncthreads();
-        if (tid < nk) {
-            double sv = 0.0;
-            for (int c = 0; c < nchunk; ++c) sv += red[c * bbp + tid];
-            part[((size_t)buf * G + g) * bb + tid] = sv;
-        }
+        if (tid < nk) part[((size_t)buf * G + g) * bb + tid] = sum_chunks(red, nchunk, bbp, tid);
         if (r0 <= j && j < r0 + nrow) {
             const int rj = (int)(j - r0);
             for (int kk = tid; kk < nk; kk += NTH) diag[(size_t)buf * bb + kk] = (double)S[(size_t)(j + kk) * ldS + rj];
@@ -218,26 +219,17 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
             if (tid < nk) dg[tid] = ld_cg(&diag[(size_t)buf * bb + tid]);
         }
         __syncthreads();
-        if (tid < nk) {
-            double sv = 0.0;
-            for (int c = 0; c < nchunk; ++c) sv += red[c * bbp + tid];
-            sums[tid] = sv;
-        }
+        if (tid < nk) sums[tid] = sum_chunks(red, nchunk, bbp, tid);
         __syncthreads();
-        if (tid == 0) {
-            const double alpha = dg[0];
-            const double ss = sums[0];
-            double tj = 0.0, beta = alpha, scal = 0.0;
-            if (ss != 0.0) {
-                const double nrm = sqrt(alpha * alpha + ss);
-                beta = (alpha >= 0.0) ? -nrm : nrm;
-                tj = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
+        if (tid < 32) {
+            double tj, beta, scal;
+            warp_larfg(dg[0], sums[0], tj, beta, scal);
+            if (tid == 0) {
+                sh_tau = tj;
+                sh_beta = beta;
+                sh_scal = scal;
+                if (g == 0) tau[j] = tj;
             }
-            sh_tau = tj;
-            sh_beta = beta;
-            sh_scal = scal;
-            if (g == 0) tau[j] = tj;
         }
         __syncthreads();
         if (tid > 0 && tid < nk)
@@ -266,22 +258,44 @@ __global__ void __launch_bounds__(256) panel_f32_kernel(float* __restrict__ A, i
 size_t panel_f32_smem(int64_t rpb, int bb)
 {
     const int bbp = pow2_at_least(bb);
-    const int nchunk = 256 / bbp;
+    const int nchunk = kPanelThreads / bbp;
     return sizeof(double) * ((size_t)nchunk * bbp + 2 * (size_t)bbp) + sizeof(float) * ((size_t)bbp + (size_t)(rpb | 1) * bb);
 }
 
 size_t panel_smem(int64_t rpb, int bb)
 {
     const int bbp = pow2_at_least(bb);
-    const int nchunk = 256 / bbp;
+    const int nchunk = kPanelThreads / bbp;
     return sizeof(double) * ((size_t)(rpb | 1) * bb + (size_t)nchunk * bbp + 3 * (size_t)bbp);
 }
 
-int64_t panel_blocks(int64_t m1)
+// Rows per block at least RQRCP_PANEL_MIN_ROWS (default 64), at most one block per SM.
+int64_t panel_min_rows()
 {
-    int64_t G = (m1 + 63) / 64;
-    if (G > dev_info().sms) G = dev_info().sms;
-    return G < 1 ? 1 : G;
+    static int64_t v = -1;
+    if (v < 0) {
+        const char* e = getenv("RQRCP_PANEL_MIN_ROWS");
+        v = (e != nullptr && atoll(e) > 0) ? atoll(e) : 64;
+    }
+    return v;
+}
+
+// Blocks of the panel kernel: rows per block at least RQRCP_PANEL_MIN_ROWS, at most one block
+// per SM, and enough blocks for each block's rows to fit in shared memory.
+int64_t panel_blocks(int64_t m1, int bb, int elem_bytes)
+{
+    const int64_t rows = panel_min_rows();
+    int64_t G = (m1 + rows - 1) / rows;
+    const int64_t sms = dev_info().sms;
+    if (G > sms) G = sms;
+    if (G < 1) G = 1;
+    const size_t lim = (size_t)dev_info().max_smem_optin - 1024;
+    auto fits = [&](int64_t g) {
+        const int64_t rpb = (m1 + g - 1) / g;
+        return (elem_bytes == 4 ? panel_f32_smem(rpb, bb) : panel_smem(rpb, bb)) <= lim;
+    };
+    while (G < sms && !fits(G)) ++G;
+    return G;
 }
 
 }  // namespace
@@ -292,12 +306,13 @@ size_t panel_part_bytes(int bb)
     return sizeof(double) * (2 * (size_t)1024 * bb + 2 * (size_t)bb);
 }
 
-bool panel_fits(int64_t m1, int bb, int /*elem_bytes*/)
+bool panel_fits(int64_t m1, int bb, int elem_bytes)
 {
     if (bb > 256) return false;
-    const int64_t G = panel_blocks(m1);
+    const int64_t G = panel_blocks(m1, bb, elem_bytes);
     const int64_t rpb = (m1 + G - 1) / G;
-    return panel_smem(rpb, bb) <= (size_t)dev_info().max_smem_optin - 1024;
+    const size_t smem = elem_bytes == 4 ? panel_f32_smem(rpb, bb) : panel_smem(rpb, bb);
+    return smem <= (size_t)dev_info().max_smem_optin - 1024;
 }
 
 template <typename T>
@@ -312,10 +327,10 @@ cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, dou
             return e;
         attr_set = true;
     }
-    const int64_t G = panel_blocks(m1);
+    const int64_t G = panel_blocks(m1, bb, (int)sizeof(T));
     const int64_t rpb = (m1 + G - 1) / G;
     const size_t smem = f32 ? panel_f32_smem(rpb, bb) : panel_smem(rpb, bb);
-    const int threads = 256;
+    const int threads = kPanelThreads;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;

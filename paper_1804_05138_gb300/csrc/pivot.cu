@@ -213,15 +213,9 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
             for (int r = t + 1 + tid; r < l; r += 32) ss += xs[r] * xs[r];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            double tau, beta, scal;
+            warp_larfg(xs[t], ss, tau, beta, scal);
             if (tid == 0) {
-                const double alpha = xs[t];
-                double tau = 0.0, beta = alpha, scal = 0.0;
-                if (ss != 0.0) {
-                    const double nrm = sqrt(alpha * alpha + ss);
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    tau = (beta - alpha) / beta;
-                    scal = 1.0 / (alpha - beta);
-                }
                 sh_tau = tau;
                 sh_beta = beta;
                 sh_scal = scal;

@@ -16,8 +16,7 @@ __global__ void init_kernel(Status* st, int64_t k, int32_t* jpvt, int64_t n)
         st->error = 0;
         st->guard = 0;
         st->rank = k;
-        st->bar_count = 0;
-        st->bar_gen = 0;
+        st->bar = 0;
         st->nu0bits = 0;
     }
     for (int64_t j = t; j < n; j += (int64_t)gridDim.x * blockDim.x) jpvt[j] = (int32_t)j;
