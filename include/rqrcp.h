@@ -104,7 +104,10 @@ int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_
  * reflector (column norm, beta, tau) of the panel is generated in FP64 and tau is returned in
  * FP64.  Arguments and output layout as in rqrcp_factor; the rank guard uses 2^-6 in place of
  * 10*max(m,n)*2^-53 (about five times the relative noise BF16 rounding leaves in a sketch column:
- * rank below that level is not resolved by this sketch).
+ * rank below that level is not resolved by this sketch).  RQRCP_TENSOR_CORES=0 in the environment
+ * (read once per process) runs the FP32 form's contractions, and the batched kernel's sketch and
+ * trailing update, as FP32 SIMT code instead of on the tensor cores, for A/B timing; the
+ * accuracy class is the same.
  */
 int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
                        uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
