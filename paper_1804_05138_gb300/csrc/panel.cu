@@ -26,11 +26,32 @@ __host__ __device__ inline int pow2_at_least(int x)
     return p;
 }
 
-// Sum of p[h * stride] for h = start, start + step, ... < G in increasing h, with up to 40 loads
-// in flight before their additions (the partials sit in L2 and every block reads all of them:
-// one round trip instead of one per few loads).  Same order, so the same value, in every block.
+// Sum of p[h * stride] for h = start, start + step, ... < G, in a fixed order, so the same value
+// in every block.  Few terms (n <= 16, e.g. up to 64 blocks): batches of 8 loads at clamped (always
+// valid) addresses, summed in two chains with the out-of-range slots as exact zeros; the step is
+// then one or two L2 round trips.  More terms: up to 40 loads in flight, one chain (with 100+
+// blocks the all-to-all read of the partials is bound by L2 bandwidth, and this form measured
+// faster there).
 __device__ __forceinline__ double sum_partials(const double* p, int G, int start, int step, size_t stride)
 {
+    const int n = start < G ? (G - 1 - start) / step + 1 : 0;
+    if (n <= 16) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int u = 0; u < n; u += 8) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int uu = u + q < n ? u + q : n - 1;
+                v[q] = ld_cg(p + (size_t)(start + uu * step) * stride);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                s0 += u + q < n ? v[q] : 0.0;
+                s1 += u + q + 1 < n ? v[q + 1] : 0.0;
+            }
+        }
+        return s0 + s1;
+    }
     constexpr int U = 40;
     double s = 0.0;
     for (int h0 = start; h0 < G; h0 += U * step) {
