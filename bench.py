@@ -247,6 +247,58 @@ def gpu_smi_id(dev_index):
 
 
 # ------------------------------------------------------------------------------ our arm
+def gpu_local_cpus(dev):
+    """CPUs local to the GPU (the sysfs local_cpulist of its PCI function, within this process's
+    affinity), or None when that is not available."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (pr.pci_domain_id, pr.pci_bus_id,
+                                                                         pr.pci_device_id)
+        with open(path) as f:
+            txt = f.read().strip()
+        cpus = set()
+        for part in txt.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
+class NearGpu:
+    """Context in which the process runs on the GPU's local CPUs, so that pinned host buffers
+    allocated in it land on the GPU's NUMA node; the previous affinity comes back on exit.
+    `placement` says what happened ("gpu-local" or "default")."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.old = None
+        self.placement = "default"
+
+    def __enter__(self):
+        cpus = gpu_local_cpus(self.dev)
+        self.old = os.sched_getaffinity(0)
+        if cpus:
+            try:
+                os.sched_setaffinity(0, cpus)
+                self.placement = "gpu-local"
+            except OSError:
+                pass
+        return self
+
+    def __exit__(self, *exc):
+        try:
+            os.sched_setaffinity(0, self.old)
+        except OSError:
+            pass
+        return False
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -365,10 +417,11 @@ def run_ours(args, w, rank, world, local_rank):
 
     # end to end through the public API with host buffers
     # host buffers hold the column-major matrix as a contiguous (n, m) row-major array
-    host_A = A0.t().contiguous().cpu().pin_memory()
-    host_out = torch.empty_like(host_A).pin_memory()
-    host_jpvt = torch.empty(n, dtype=torch.int32).pin_memory()
-    host_tau = torch.empty(k, dtype=torch.float64).pin_memory()
+    with NearGpu(dev) as near:
+        host_A = A0.t().contiguous().cpu().pin_memory()
+        host_out = torch.empty_like(host_A).pin_memory()
+        host_jpvt = torch.empty(n, dtype=torch.int32).pin_memory()
+        host_tau = torch.empty(k, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     if world > 1:
@@ -403,7 +456,7 @@ def run_ours(args, w, rank, world, local_rank):
     esz = A.element_size()
     e2e = {"value": round(world * F / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
            "h2d_bytes_per_step": m * n * esz, "d2h_bytes_per_step": m * n * esz + n * 4 + k * 8,
-           "ms_per_step": round(e2e_ms, 3)}
+           "ms_per_step": round(e2e_ms, 3), "host_buffers": "pinned, " + near.placement}
 
     extra = {}
     if not diff and not args.no_other_form:
@@ -495,19 +548,25 @@ def run_batched(args, w, rank, world, local_rank):
     shapes = inputs.batched_shapes(args.count, seed=0)
     table = autotune.load_or_tune(shapes, p=p)
     bs = [autotune.choose(table, m, n, k) for (m, n, k) in shapes]
+    # the matrices are column-major views (ld = m) into one device pool, so the end-to-end run
+    # moves the batch with one copy each way and the restore between steps is one copy
+    pool = torch.empty(sum(m * n for m, n, _ in shapes), dtype=torch.float32, device=dev)
     mats = []
+    off = 0
     for i, (m, n, _) in enumerate(shapes):
         sig = inputs.sigma_exp_decay(min(m, n), 0.1 * n)
-        mats.append(inputs.spectrum_matrix_torch(m, n, sig, seed_u=1000 + 2 * i + 4096 * rank,
-                                                 seed_v=1001 + 2 * i + 4096 * rank, device=dev, dtype=torch.float32))
-    pristine = [A.clone() for A in mats]
+        view = pool[off:off + m * n].view(n, m).t()
+        view.copy_(inputs.spectrum_matrix_torch(m, n, sig, seed_u=1000 + 2 * i + 4096 * rank,
+                                                seed_v=1001 + 2 * i + 4096 * rank, device=dev, dtype=torch.float32))
+        mats.append(view)
+        off += m * n
+    pristine_pool = pool.clone()
     batch = binding.Batch(mats, [k for _, _, k in shapes], bs, p=p, seed=0)
     F = batch.flops
     stream = torch.cuda.Stream(device=dev)
 
     def restore():
-        for A, O in zip(batch.mats, pristine):
-            A.copy_(O)
+        pool.copy_(pristine_pool)
 
     # capture the batched call in a CUDA graph
     restore()
@@ -556,17 +615,17 @@ def run_batched(args, w, rank, world, local_rank):
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = F / (ms_per_step * 1e-3) / 1e12
     # end to end: H2D of every matrix from pinned host memory, the batched call, D2H of every result
-    host_in = [A.t().contiguous().cpu().pin_memory() for A in pristine]
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    with NearGpu(dev) as near:
+        host_in = pristine_pool.cpu().pin_memory()  # the batch as stored on the device, one buffer
+        host_out = torch.empty_like(host_in).pin_memory()
+        host_jall = torch.empty(sum(j.numel() for j in batch.jpvts), dtype=torch.int32).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(cur)
-    for A, h in zip(batch.mats, host_in):
-        A.t().copy_(h, non_blocking=True)
+    pool.copy_(host_in, non_blocking=True)
     code = batch.run(stream=cur)
-    for A, h in zip(batch.mats, host_out):
-        h.copy_(A.t(), non_blocking=True)
-    host_j = [j.cpu() for j in batch.jpvts]
+    host_out.copy_(pool, non_blocking=True)
+    host_jall.copy_(torch.cat(batch.jpvts), non_blocking=True)  # every pivot vector, one copy
     e1.record(cur)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -586,8 +645,8 @@ def run_batched(args, w, rank, world, local_rank):
                      "frac": round(achieved / fp32_peak, 4), "traffic": None, "kernel": "batched_kernel",
                      "peak_source": "FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2070 MHz"},
         "e2e": {"value": round(world * F / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + sum(j.numel() * 4 for j in host_j),
-                "ms_per_step": round(e2e_ms, 3)},
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + host_jall.numel() * 4,
+                "ms_per_step": round(e2e_ms, 3), "host_buffers": "pinned, " + near.placement},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
