@@ -34,7 +34,7 @@ extern "C" {
 #define RQRCP_ERR_NONFINITE 2   /* the sketch of A holds NaN or Inf: A is not finite */
 #define RQRCP_ERR_TIMEOUT 3     /* a grid-wide barrier inside a kernel gave up waiting */
 #define RQRCP_ERR_WORKSPACE 4   /* work is NULL, misaligned or smaller than required */
-#define RQRCP_ERR_UNSUPPORTED 5 /* the shape exceeds what this build keeps on chip */
+#define RQRCP_ERR_UNSUPPORTED 5 /* the shape exceeds what the library keeps on chip */
 
 #define RQRCP_PREC_FP64 0  /* plain form: every step in IEEE double */
 #define RQRCP_PREC_MIXED 1 /* mixed form: FP32 storage, FP64 reflector generation */
@@ -84,7 +84,7 @@ int rqrcp_sketch(int64_t m, int64_t n, const double* A, int64_t lda, const doubl
  * remaining sketch norm^2 falls to (10*max(m,n)*2^-53)^2 times the largest initial one,
  * pivoting stops for good (the remaining columns keep their order, B is no longer
  * updated); rqrcp_read_status reports the pivots taken before that as the rank.
- * Limits of this build: l = b+p <= 1024 and the sketch and panel must fit in shared
+ * Limits of the library: l = b+p <= 1024 and the sketch and panel must fit in shared
  * memory across the GPU (checked; RQRCP_ERR_UNSUPPORTED otherwise).
  */
 int rqrcp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b, int64_t p,

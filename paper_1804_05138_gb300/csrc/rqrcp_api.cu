@@ -360,7 +360,7 @@ __attribute__((visibility("default"))) const char* rqrcp_error_string(int code)
     case RQRCP_ERR_NONFINITE: return "the sketch of A is not finite (A holds NaN or Inf)";
     case RQRCP_ERR_TIMEOUT: return "a grid-wide barrier timed out inside a kernel";
     case RQRCP_ERR_WORKSPACE: return "workspace missing, misaligned (256 B) or too small";
-    case RQRCP_ERR_UNSUPPORTED: return "shape beyond what this build keeps in shared memory";
+    case RQRCP_ERR_UNSUPPORTED: return "shape beyond what the library keeps in shared memory";
     default: return "unknown error code";
     }
 }
