@@ -247,6 +247,29 @@ def gpu_smi_id(dev_index):
 
 
 # ------------------------------------------------------------------------------ our arm
+# ---- N GPUs: replicas (one process per GPU, each factoring its own matrix; no collective on the
+# data path).  The job's time is its slowest rank's; its throughput counts the work of all ranks.
+def replica_seed(base, rank):
+    """Input seed of a rank's matrix: every replica draws its own matrix of the same recipe."""
+    return base + 4096 * rank
+
+
+def max_over_ranks(x, world, device):
+    """max of x over the ranks (x itself when world == 1); device: where the collective runs."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput per second: the units all ranks processed over the job's time (ms)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def gpu_local_cpus(dev):
     """CPUs local to the GPU (the sysfs local_cpulist of its PCI function, within this process's
     affinity), or None when that is not available."""
@@ -315,7 +338,7 @@ def run_ours(args, w, rank, world, local_rank):
     F = counted_flops(m, n, k, l)
     if diff:  # forward (factor + Q1) and backward (thin-QR adjoint with the wide block)
         F += 4.0 * m * k * k + 4.0 * m * (n - k) * k + 5.0 * m * k * k
-    A0 = binding.colmajor(make_input_torch(w, dev, seed=1 + rank))
+    A0 = binding.colmajor(make_input_torch(w, dev, seed=replica_seed(1, rank)))
     A = torch.empty_like(A0.t()).t()
     jpvt = torch.empty(n, dtype=torch.int32, device=dev)
     tau = torch.empty(k, dtype=torch.float64, device=dev)
@@ -374,13 +397,9 @@ def run_ours(args, w, rank, world, local_rank):
         code, rank_out = binding.rqrcp_read_status(work)
         if code != 0:
             raise binding.RQRCPError(code, "device status (timed)")
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * F / (ms_per_step * 1e-3) / 1e9
+    value = job_rate(F, world, ms_per_step) / 1e9
 
     # dominant kernel and its roofline (alu: FP64 DFMA pipe; mixed: FP32 SIMT)
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -448,13 +467,9 @@ def run_ours(args, w, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         t_e2e.append(e0.elapsed_time(e1))
-    e2e_ms = sum(t_e2e) / len(t_e2e)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(sum(t_e2e) / len(t_e2e), world, dev)
     esz = A.element_size()
-    e2e = {"value": round(world * F / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+    e2e = {"value": round(job_rate(F, world, e2e_ms) / 1e9, 3), "unit": "GFLOP/s",
            "h2d_bytes_per_step": m * n * esz, "d2h_bytes_per_step": m * n * esz + n * 4 + k * 8,
            "ms_per_step": round(e2e_ms, 3), "host_buffers": "pinned, " + near.placement}
 
@@ -556,8 +571,9 @@ def run_batched(args, w, rank, world, local_rank):
     for i, (m, n, _) in enumerate(shapes):
         sig = inputs.sigma_exp_decay(min(m, n), 0.1 * n)
         view = pool[off:off + m * n].view(n, m).t()
-        view.copy_(inputs.spectrum_matrix_torch(m, n, sig, seed_u=1000 + 2 * i + 4096 * rank,
-                                                seed_v=1001 + 2 * i + 4096 * rank, device=dev, dtype=torch.float32))
+        view.copy_(inputs.spectrum_matrix_torch(m, n, sig, seed_u=replica_seed(1000 + 2 * i, rank),
+                                                seed_v=replica_seed(1001 + 2 * i, rank), device=dev,
+                                                dtype=torch.float32))
         mats.append(view)
         off += m * n
     pristine_pool = pool.clone()
@@ -605,13 +621,9 @@ def run_batched(args, w, rank, world, local_rank):
     clocks = sampler.stop()
     ranks = batch.ranks.cpu().numpy()
     bad = int(np.sum(ranks != np.array([k for _, _, k in shapes])))
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * F / (ms_per_step * 1e-3) / 1e9
+    value = job_rate(F, world, ms_per_step) / 1e9
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = F / (ms_per_step * 1e-3) / 1e12
     # end to end: H2D of every matrix from pinned host memory, the batched call, D2H of every result
@@ -628,7 +640,7 @@ def run_batched(args, w, rank, world, local_rank):
     host_jall.copy_(torch.cat(batch.jpvts), non_blocking=True)  # every pivot vector, one copy
     e1.record(cur)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     nbytes = sum(A.numel() * 4 for A in batch.mats)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -644,7 +656,7 @@ def run_batched(args, w, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / fp32_peak, 4), "traffic": None, "kernel": "batched_kernel",
                      "peak_source": "FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2070 MHz"},
-        "e2e": {"value": round(world * F / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+        "e2e": {"value": round(job_rate(F, world, e2e_ms) / 1e9, 3), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + host_jall.numel() * 4,
                 "ms_per_step": round(e2e_ms, 3), "host_buffers": "pinned, " + near.placement},
         "gpu_launches": 2 * args.steps,
