@@ -65,7 +65,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) divided
 # by the launch's algorithmic bytes, on the 4096^2 FP64 capture summarised in
 # profiles/gemm_fp64_4096_wy_kernels.md; scaled to a full launch by the algorithmic bytes.
-MEASURED_TRAFFIC_RATIO = {"fp64": {"wy_gemm_tn": 1.028, "wy_update": 0.604}}
+MEASURED_TRAFFIC_RATIO = {"fp64": {"wy_gemm_tn": 1.011, "wy_update": 0.609}}
 
 
 # Roofline of each kernel class.  FP64 form: the SIMT contractions run on the DFMA pipe; the
