@@ -346,6 +346,12 @@ def run_ours(args, w, rank, world, local_rank):
     work = binding.workspace(need, dev)
     stream = torch.cuda.current_stream(dev)
     call = binding.rqrcp_factor_mixed if mixed else binding.rqrcp_factor
+    if args.formula == 5:
+        if mixed:
+            raise SystemExit("--formula 5 applies to the plain FP64 workloads")
+
+        def call(A, k, b, p, seed, jpvt, tau, work):
+            return binding.rqrcp_factor_ex(A, k, b, p, seed, None, binding.RQRCP_UPDATE_EQ5, jpvt, tau, work)
 
     if diff:
         from paper_1804_05138_gb300 import autograd as rq_autograd
@@ -534,6 +540,7 @@ def run_ours(args, w, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "b": b, "p": p,
+                   "sketch_update": "Eq. (5)" if args.formula == 5 else "Eq. (4)",
                    "counted_gflop_per_step": round(F / 1e9, 3),
                    "l2": "inputs larger than L2: the 512 MB+ input is rewritten from a pristine copy before every step",
                    "parallelism": "replicas" if world > 1 else "single", "rank_out": rank_out},
@@ -676,6 +683,9 @@ def main():
     ap.add_argument("--count", type=int, default=512,
                     help="batched workload only: factor the first COUNT matrices of the 512-matrix draw "
                          "(a smaller case for profiling; the workload is 512)")
+    ap.add_argument("--formula", type=int, default=4, choices=[4, 5],
+                    help="plain FP64 workloads: update the sketch between blocks with Eq. (4) (default) "
+                         "or Eq. (5)")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other form (mixed / plain FP64) on the same matrix")
     args = ap.parse_args()

@@ -96,6 +96,29 @@ int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_
                             int64_t p, const double* Omega, int64_t ldo, int32_t* jpvt, double* tau,
                             void* work, size_t work_bytes, void* stream);
 
+#define RQRCP_UPDATE_EQ4 4 /* sketch update of Eq. (4) (Duersch-Gu): the default */
+#define RQRCP_UPDATE_EQ5 5 /* sketch update of Eq. (5) (Martinsson et al.) */
+
+/*
+ * Plain FP64 form of Alg. 2 with the choice of the sketch update between pivot blocks.
+ * Omega: the l x m sketching matrix (row-major, ldo >= m) or NULL to draw it from `seed` as in
+ * rqrcp_generate_omega (ldo is then ignored).  formula:
+ *   RQRCP_UPDATE_EQ4  Eq. (4): the QRCP of each block runs on B in place and the top bb rows of
+ *                     the trailing sketch become R_hat12 - R_hat11 R11^{-1} R12 (rqrcp_factor);
+ *   RQRCP_UPDATE_EQ5  Eq. (5): the QRCP runs on a copy of B; B is only permuted, Omega_bar =
+ *                     Omega Q is kept up to date (the block's reflectors applied from the right,
+ *                     as a compact-WY update of the m x l matrix Omega_bar^T) and the trailing
+ *                     sketch becomes B2 - Omega_bar_1 R12 (all l rows).  The caller's Omega is
+ *                     copied into the workspace, never written.
+ * Both give the same pivots in exact arithmetic (Sec. 3.2 and 3.3.1); Eq. (5) reads and writes the m x l
+ * Omega_bar once more per block.  Errors as in rqrcp_factor, with argument numbers in this list:
+ * -10 ldo < m with Omega given, -11 formula not one of RQRCP_UPDATE_*, -12 jpvt NULL, -13 tau
+ * NULL.  Workspace: rqrcp_workspace_size(..., RQRCP_PREC_FP64).
+ */
+int rqrcp_factor_ex(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                    uint64_t seed, const double* Omega, int64_t ldo, int formula, int32_t* jpvt, double* tau,
+                    void* work, size_t work_bytes, void* stream);
+
 /*
  * Mixed form of Alg. 2: A is FP32 (lda >= m).  The sketch B = Omega A (Alg. 2, the sketch
  * step) is formed from Omega and A rounded to BF16 (round to nearest even) with FP32

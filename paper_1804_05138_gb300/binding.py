@@ -26,6 +26,8 @@ RQRCP_PREC_FP64 = 0
 RQRCP_PREC_MIXED = 1
 RQRCP_SKETCH_BF16 = 0
 RQRCP_SKETCH_FP32 = 1
+RQRCP_UPDATE_EQ4 = 4
+RQRCP_UPDATE_EQ5 = 5
 
 # Every symbol include/rqrcp.h declares.
 ABI_SYMBOLS = (
@@ -35,7 +37,7 @@ ABI_SYMBOLS = (
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
     "rqrcp_backward_f32", "rqrcp_reorth_workspace_size", "rqrcp_lowrank_reorth",
-    "rqrcp_batched_workspace_size", "rqrcp_factor_batched",
+    "rqrcp_batched_workspace_size", "rqrcp_factor_batched", "rqrcp_factor_ex",
 )
 RQRCP_PROFILE_CLASSES = 14
 
@@ -69,6 +71,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "rqrcp_factor": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp, _sz, _vp]),
             "rqrcp_factor_with_omega": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _vp, _i64, _vp,
                                                        _vp, _vp, _sz, _vp]),
+            "rqrcp_factor_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, ctypes.c_int,
+                                               _vp, _vp, _vp, _sz, _vp]),
             "rqrcp_factor_mixed": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp,
                                                   _sz, _vp]),
             "rqrcp_factor_mixed_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, ctypes.c_int, _vp,
@@ -188,6 +192,13 @@ def rqrcp_factor_with_omega(A, k, b, p, Omega, jpvt, tau, work, stream=None) -> 
     m, n = A.shape
     return load().rqrcp_factor_with_omega(m, n, _ptr(A), _ld(A), k, b, p, _ptr(Omega), _ld_rowmajor(Omega),
                                           _ptr(jpvt), _ptr(tau), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_factor_ex(A, k, b, p, seed, Omega, formula, jpvt, tau, work, stream=None) -> int:
+    m, n = A.shape
+    om, ldo = (None, 0) if Omega is None else (_ptr(Omega), _ld_rowmajor(Omega))
+    return load().rqrcp_factor_ex(m, n, _ptr(A), _ld(A), k, b, p, seed, om, ldo, formula, _ptr(jpvt), _ptr(tau),
+                                  _ptr(work), work.numel(), _stream(stream))
 
 
 def rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
@@ -331,7 +342,7 @@ class Factorization:
     k: int
 
 
-def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETCH_BF16):
+def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETCH_BF16, formula=RQRCP_UPDATE_EQ4):
     import torch
     m, n = A.shape
     dev = A.device
@@ -344,6 +355,8 @@ def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETC
         work = workspace(need, dev)
     if mixed:
         code = rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream)
+    elif formula != RQRCP_UPDATE_EQ4:
+        code = rqrcp_factor_ex(A, k, b, p, seed, omega, formula, jpvt, tau, work, stream)
     elif omega is None:
         code = rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream)
     else:
@@ -355,16 +368,19 @@ def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETC
 
 
 def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=None, stream=None,
-           overwrite: bool = False) -> Factorization:
+           overwrite: bool = False, formula: int = 4) -> Factorization:
     """Randomized QRCP of a float64 CUDA matrix (plain FP64 form).  ``omega`` (row-major
-    (b+p) x m float64 CUDA tensor) replaces the seeded sketch when given."""
+    (b+p) x m float64 CUDA tensor) replaces the seeded sketch when given.  ``formula``: 4 updates
+    the sketch between blocks with Eq. (4) (Duersch-Gu), 5 with Eq. (5) (Martinsson et al.)."""
     import torch
     if A.dtype != torch.float64:
         raise TypeError("factor expects float64; use factor_mixed for float32")
     Acm = colmajor(A)
     if not overwrite:
         Acm = Acm.t().clone().t()
-    return _run_factor(Acm, k, b, p, seed, omega, False, work, stream)
+    if formula not in (RQRCP_UPDATE_EQ4, RQRCP_UPDATE_EQ5):
+        raise ValueError("formula must be 4 or 5")
+    return _run_factor(Acm, k, b, p, seed, omega, False, work, stream, formula=formula)
 
 
 def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,

@@ -228,6 +228,12 @@ template <typename T>
 cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i, int bb, int64_t n,
                            double* What, const Status* st, cudaStream_t s);
 
+// Eq. (5), last step: B(:, c0:c0+nt) = Bc(:, c0:c0+nt) - sum_sp P[sp][c][0:l] (ld l for B and
+// Bc), written to both B and Bc.  Skipped once the rank guard has fired.
+template <typename T>
+cudaError_t launch_bfinish(T* B, T* Bc, int l, int64_t c0, int64_t nt, const double* P, int nsplit,
+                           const Status* st, cudaStream_t s);
+
 // Opt-in kernel timing (prof.cu): classes in the order of rqrcp_profile_class_name.
 enum ProfClass {
     K_OMEGA = 0, K_SKETCH_GEMM, K_SKETCH_REDUCE, K_PIVOT, K_SWAP, K_PANEL,

@@ -58,7 +58,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t status, omega, B, P, Y, Tm, What, piv, cand, part, tmp, xs, total;
+    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
@@ -74,14 +74,17 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     L.status = take(sizeof(Status));
     L.omega = take((size_t)l * m * esz);
     L.B = take((size_t)l * n * esz);
+    // FP64 form: the untransformed copy of the sketch that Eq. (5) updates
+    L.Bc = take(esz == sizeof(double) ? (size_t)l * n * esz : 0);
     L.P = take((size_t)kMaxSplit * n * (size_t)(l > b ? l : b) * sizeof(double));
-    L.Y = take((size_t)b * n * sizeof(double));
+    // Y holds T^T W for the trailing columns, and for the l columns of Omega_bar^T under Eq. (5)
+    L.Y = take((size_t)b * (size_t)(n > l ? n : l) * sizeof(double));
     L.Tm = take((size_t)b * b * sizeof(double));
     L.What = take((size_t)b * b * sizeof(double));
     L.piv = take((size_t)b * sizeof(int32_t));
     L.cand = take(pivot_cand_bytes((int)l) + sizeof(long long) * (1 + 4 * (size_t)b));
     L.part = take(panel_part_bytes((int)b));
-    L.tmp = take((size_t)2 * b * m * esz);
+    L.tmp = take((size_t)2 * b * (size_t)(m > l ? m : l) * esz);  // 2b columns of A, or of the sketch
     {
         // TF32 parts of Omega / V (contraction) and of Y (update); used one after the other
         const size_t xs = tc_xsplit_bytes(l > b ? l : b, m), ys = tc_update_ws_bytes(n);
@@ -154,7 +157,7 @@ int check_work(void* work, size_t work_bytes, size_t need)
 template <typename T>
 int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, int64_t p, uint64_t seed,
                 const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
-                cudaStream_t s, int sketch_bf16 = 0)
+                cudaStream_t s, int sketch_bf16 = 0, int formula = RQRCP_UPDATE_EQ4)
 {
     const int64_t l = b + p;
     const Layout L = make_layout(m, n, b, p, sizeof(T));
@@ -174,12 +177,20 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     const long long* swapmap = reinterpret_cast<const long long*>(w + L.cand + pivot_cand_bytes((int)l));
     double* part = reinterpret_cast<double*>(w + L.part);
     T* tmp = reinterpret_cast<T*>(w + L.tmp);
+    T* Bc = reinterpret_cast<T*>(w + L.Bc);
+    const bool eq5 = formula == RQRCP_UPDATE_EQ5;
+    if (eq5 && sizeof(T) != sizeof(double)) return RQRCP_ERR_UNSUPPORTED;
 
     RQ_CHECK(launch_init(st, k, jpvt, n, s));
     const double es = (double)sizeof(T);
     const T* Omega = Omega_user;
     if (Omega == nullptr) {
         RQ_LAUNCH(K_OMEGA, 0, l * m * es, launch_omega<T>(l, m, seed, Om, m, s));
+        Omega = Om;
+        ldo = m;
+    } else if (eq5) {  // Eq. (5) updates Omega_bar = Omega Q in place: work on a copy
+        RQ_CHECK(cudaMemcpy2DAsync(Om, (size_t)m * sizeof(T), Omega_user, (size_t)ldo * sizeof(T),
+                                   (size_t)m * sizeof(T), (size_t)l, cudaMemcpyDeviceToDevice, s));
         Omega = Om;
         ldo = m;
     }
@@ -203,6 +214,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         }
         RQ_LAUNCH(K_SKETCH_REDUCE, 0, (double)ns * l * n * 8 + (double)l * n * es,
                   launch_sketch_reduce<T>(P, ns, l, n, B, l, st, s));
+        if (eq5) RQ_CHECK(cudaMemcpyAsync(Bc, B, (size_t)l * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
     // guard tolerance: 10 max(m,n) u for FP64 (the oracle's reading); FP32 storage uses
     // 10 sqrt(max(m,n)) u, about ten times the rounding noise of an FP32 sketch column; the BF16
@@ -218,6 +230,8 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         RQ_LAUNCH(K_PIVOT, 4.0 * l * np * bb, 2.0 * l * np * es,
                   launch_pivot<T>(B, l, (int)l, n, i, bb, jpvt, piv, cand, guard_rel2, st, s));
         RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * m * es, launch_swaps<T>(A, lda, m, bb, swapmap, tmp, st, s));
+        if (eq5 && i + bb < k)  // the same column moves on the untransformed sketch
+            RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * l * es, launch_swaps<T>(Bc, l, l, bb, swapmap, tmp, st, s));
         T* Vp = A + i * lda + i;
         const int64_t mr = m - i;
         RQ_LAUNCH(K_PANEL, 2.0 * mr * bb * bb - 2.0 * bb * bb * bb / 3.0, 2.0 * mr * bb * es,
@@ -248,9 +262,29 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         else
             RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
                       launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st, s));
-        if (i + bb < k)
+        if (i + bb < k && !eq5)
             RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
                       launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));
+        if (i + bb < k && eq5) {
+            // Eq. (5): Omega_bar <- Omega_bar Q_tilde, i.e. Omega_bar^T(i:m, :) <- Q_tilde^T
+            // Omega_bar^T(i:m, :), the compact-WY update of the trailing matrix with C the m x l
+            // column-major view of the row-major Omega_bar; then B2 <- B2 - Omega_bar_1 R12.
+            T* OmT = Om + i;
+            int ns2;
+            int64_t kc2;
+            choose_split(bb, l, mr, ns2, kc2, (int)sizeof(T));
+            RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, (double)mr * l * es,
+                      launch_gemm_tn<T>(Vp, lda, OmT, m, bb, l, mr, kc2, P, 1, 0, st, s));
+            RQ_LAUNCH(K_BUPDATE, (double)bb * bb * l, ((double)ns2 + 1.0) * bb * l * 8,
+                      launch_reduce_y(P, ns2, l, 0, bb, Tm, 1, Y, l, st, s));
+            RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, 2.0 * mr * l * es,
+                      launch_gemm_update<T>(OmT, m, Vp, lda, Y, bb, mr, l, bb, 1, nullptr, st, s));
+            choose_split(l, nt, bb, ns2, kc2, (int)sizeof(T));
+            RQ_LAUNCH(K_BUPDATE, 2.0 * l * bb * nt, (double)bb * nt * es + (double)l * bb * es,
+                      launch_gemm_tn<T>(OmT, m, Vp + (int64_t)bb * lda, lda, l, nt, bb, kc2, P, 0, 0, st, s));
+            RQ_LAUNCH(K_BUPDATE, 0, (double)ns2 * l * nt * 8 + 3.0 * l * nt * es,
+                      launch_bfinish<T>(B, Bc, (int)l, i + bb, nt, P, ns2, st, s));
+        }
     }
     return RQRCP_OK;
 }
@@ -443,6 +477,18 @@ __attribute__((visibility("default"))) int rqrcp_factor_with_omega(int64_t m, in
     if (ldo < m) return -9;
     return factor_impl<double>(m, n, A, lda, k, b, p, 0, Omega, ldo, jpvt, tau, work, work_bytes,
                                (cudaStream_t)stream);
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_ex(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
+                                                           int64_t b, int64_t p, uint64_t seed, const double* Omega,
+                                                           int64_t ldo, int formula, int32_t* jpvt, double* tau,
+                                                           void* work, size_t work_bytes, void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 3 : e;
+    if (Omega != nullptr && ldo < m) return -10;
+    if (formula != RQRCP_UPDATE_EQ4 && formula != RQRCP_UPDATE_EQ5) return -11;
+    return factor_impl<double>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, work,
+                               work_bytes, (cudaStream_t)stream, 0, formula);
 }
 
 __attribute__((visibility("default"))) int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k,

@@ -3,7 +3,9 @@
 //  * "Swap (j_1..j_b) and (i:i+b-1) columns in A": gather the moved columns into scratch,
 //    then scatter them to their new positions (whole columns, all m rows, coalesced);
 //  * Eq. (4): B(0:bb, i+bb:n) <- R_hat12 - Omega_hat_11 R12 with Omega_hat_11 = R_hat11 R11^{-1}
-//    from the forward substitution Omega_hat_11 R11 = R_hat11 (both upper triangular).
+//    from the forward substitution Omega_hat_11 R11 = R_hat11 (both upper triangular);
+//  * the last step of Eq. (5): B(:, i+bb:n) <- B2 - Omega_bar_1 R12 from the split-K partials of
+//    Omega_bar_1 R12.
 #include "internal.cuh"
 
 namespace rq {
@@ -151,6 +153,28 @@ __global__ void __launch_bounds__(256) bapply_kernel(T* __restrict__ B, int64_t 
     }
 }
 
+// Eq. (5), last step: B(:, c0+c) = Bc(:, c0+c) - sum_sp P[sp][c][0:l] for c < nt, the partials
+// holding Omega_bar_1 R12 with Omega_bar_1 the columns i:i+bb of Omega Q_tilde.  Bc is the sketch
+// as permuted by this block's pivots but not transformed by its QRCP; both buffers take the
+// result: B for the next pivot search (which transforms it in place), Bc as its untouched copy.
+template <typename T>
+__global__ void bfinish_kernel(T* __restrict__ B, T* __restrict__ Bc, int l, int64_t c0, int64_t nt,
+                               const double* __restrict__ P, int nsplit, const Status* st)
+{
+    if (status_error(st) || *(volatile const int*)&st->guard) return;
+    const int64_t total = (int64_t)l * nt;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / l;
+        const int r = (int)(e - c * l);
+        double s = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * nt + c) * l + r];
+        const int64_t at = (c0 + c) * l + r;
+        const T v = (T)((double)Bc[at] - s);
+        B[at] = v;
+        Bc[at] = v;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s)
@@ -193,7 +217,22 @@ cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_bfinish(T* B, T* Bc, int l, int64_t c0, int64_t nt, const double* P, int nsplit,
+                           const Status* st, cudaStream_t s)
+{
+    const int64_t total = (int64_t)l * nt;
+    if (total <= 0) return cudaSuccess;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = 8 * (int64_t)dev_info().sms;
+    if (grid > cap) grid = cap;
+    bfinish_kernel<T><<<(unsigned)grid, 256, 0, s>>>(B, Bc, l, c0, nt, P, nsplit, st);
+    return cudaGetLastError();
+}
+
 #define RQ_INST(T)                                                                                    \
+    template cudaError_t launch_bfinish<T>(T*, T*, int, int64_t, int64_t, const double*, int, const Status*, \
+                                           cudaStream_t);                                             \
     template cudaError_t launch_swaps<T>(T*, int64_t, int64_t, int, const long long*, T*, const Status*, \
                                          cudaStream_t);                                               \
     template cudaError_t launch_bupdate<T>(T*, int64_t, const T*, int64_t, int64_t, int, int64_t,     \

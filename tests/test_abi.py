@@ -71,6 +71,15 @@ def test_factor_argument_codes(lib):
     assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, fake, None, None, 0, None) == -11
     h = lib.rqrcp_factor_mixed
     assert h(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, fake, 16, None) == 4     # too small
+    x = lib.rqrcp_factor_ex
+    #            m  n  A    lda k  b  p  seed Omega ldo formula jpvt tau work bytes stream
+    assert x(5, 5, None, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, 0, None) == -3
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 5, fake, fake, None, 0, None) == -10
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 3, fake, fake, None, 0, None) == -11
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, None, fake, None, 0, None) == -12
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, None, None, 0, None) == -13
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, 0, None) == 4  # no workspace
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 5, 4, fake, fake, None, 0, None) == 4
 
 
 def test_other_entry_point_argument_codes(lib):

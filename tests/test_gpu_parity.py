@@ -155,6 +155,47 @@ def test_rank_deficient_guard(gpu, orc, m, n, r, k, b, p):
     assert orc.rel_residual(A0, Ag, f.tau.cpu().numpy(), f.jpvt.cpu().numpy(), k) < 1e-13
 
 
+EQ5_CASES = [  # m, n, k, b, p
+    (1000, 1000, 64, 32, 8),    # the 1000 x 1000 workload
+    (257, 190, 100, 16, 5),     # ragged tails everywhere
+    (300, 500, 250, 64, 8),     # wide
+    (64, 64, 64, 7, 3),         # k = m = n, odd block
+    (33, 17, 17, 5, 40),        # l > m
+]
+
+
+@pytest.mark.parametrize("m,n,k,b,p", EQ5_CASES)
+def test_factor_eq5_matches_oracle(gpu, orc, m, n, k, b, p):
+    """Eq. (5) (Omega_bar = Omega Q kept on the device, B2 - Omega_bar_1 R12) against the
+    oracle's Eq. (5) path, with the bar of the Eq. (4) runs; the caller's Omega is not written."""
+    import torch
+    A0 = inputs.spectrum_matrix(m, n, inputs.sigma_log_decay(min(m, n)))
+    Om = inputs.gaussian_sketch(b + p, m, seed=3)
+    ref = orc.rqrcp(A0, k, b, p, Om, formula=5)
+    Omg = torch.from_numpy(Om).cuda()
+    f = gpu.factor(_to_gpu(A0), k, b, p, omega=Omg, formula=5)
+    torch.cuda.synchronize()
+    _compare(orc, ref, f.A.cpu().numpy(), f.jpvt.cpu().numpy(), f.tau.cpu().numpy(), k, A0)
+    assert f.rank == ref.rank
+    assert np.array_equal(Omg.cpu().numpy(), Om)
+
+
+def test_factor_eq5_seeded_and_rank_guard(gpu, orc):
+    m, n, k, b, p = 400, 300, 200, 32, 8
+    A0 = inputs.spectrum_matrix(m, n, inputs.sigma_log_decay(min(m, n)))
+    ref = orc.rqrcp_seeded(A0, k, b, p, 5, formula=5)
+    f = gpu.factor(_to_gpu(A0), k, b, p, seed=5, formula=5)
+    upto = _compare(orc, ref, f.A.cpu().numpy(), f.jpvt.cpu().numpy(), f.tau.cpu().numpy(), k, A0)
+    assert upto >= 32
+    m, n, r, k, b, p = 600, 500, 50, 200, 32, 8
+    A0 = inputs.rank_r_product(m, n, r)
+    ref = orc.rqrcp_seeded(A0, k, b, p, 0, formula=5)
+    f = gpu.factor(_to_gpu(A0), k, b, p, seed=0, formula=5)
+    assert ref.rank == r and f.rank == r
+    assert np.array_equal(f.jpvt.cpu().numpy()[:r], ref.jpvt[:r])
+    assert orc.rel_residual(A0, f.A.cpu().numpy(), f.tau.cpu().numpy(), f.jpvt.cpu().numpy(), k) < 1e-13
+
+
 def test_nonfinite_input_reports_error(gpu):
     import torch
     A = torch.randn(100, 80, dtype=torch.float64, device="cuda").t().contiguous().t()
