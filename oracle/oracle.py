@@ -14,7 +14,9 @@ Pins (tests/test_oracle_*.py): Philox against numpy's Philox bit generator; Alg.
 against LAPACK dgeqp3; RQRCP with Omega = I against Alg. 1 (special case, Sec. III-B);
 Eq. (4) against Eq. (5) (same permutations, Sec. III-B); the Kahan matrix against
 Tables I and II (Sec. V-B); Lemma 1 and Lemma 3 inequalities; Theorem 1's p bound
-against the worked example in Sec. III-C; the gradient against finite differences.
+against the worked example in Sec. III-C; the gradient against finite differences; Alg. 3
+(SRQR) against Tables I and II's SRQR columns, the factorization identity through forced
+swaps, exact estimates with a scaled identity sketch, the bound of Sec. IV-D and the exact g2.
 """
 from __future__ import annotations
 
@@ -81,6 +83,9 @@ def _load():
         lib.orc_apply_q.restype = None
         lib.orc_lowrank.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i32p, _dp, _i64, _dp]
         lib.orc_lowrank.restype = ctypes.c_int
+        lib.orc_srqr.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _i64, _dp, ctypes.c_double, _i64, _u64, _i64,
+                                 _dp, _i32p, _i64p, _dp, _dp]
+        lib.orc_srqr.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -165,6 +170,37 @@ def rqrcp_seeded(A: np.ndarray, k: int, b: int, p: int, seed: int, formula: int 
                  sketch_bf16: bool = False) -> RQRCPResult:
     """Alg. 2 with Omega drawn from the seed by the oracle's own Philox generator."""
     return rqrcp(A, k, b, p, omega(b + p, A.shape[0], seed), formula, sketch_bf16)
+
+
+# --------------------------------------------------------------------------- Alg. 3
+class SRQRResult:
+    def __init__(self, R, jpvt, swaps, g2, alpha, l):
+        self.R, self.jpvt, self.swaps, self.g2, self.alpha, self.l = R, jpvt, swaps, g2, alpha, l
+
+
+def srqr(A: np.ndarray, l: int, b: int, p: int, Omega: np.ndarray, g: float = 5.0, d: int = 8,
+         seed_g: int = 0, max_swaps: int = 1000) -> SRQRResult:
+    """Alg. 3 (SRQR): RQRCP to rank l with the sketch Omega ((b+p) x m), the extra pivot, the
+    randomized g_2 estimate (d x (l+1) Gaussian matrices from seeds seed_g, seed_g+1, ...) and
+    the swap loop while g_2 > g.  Returns the explicit R (m x n), jpvt, the swap count, the last
+    g_2 estimate and |alpha| = |R(l, l)|."""
+    lib = _load()
+    A64 = _fortran64(A)
+    m, n = A64.shape
+    Om = np.ascontiguousarray(Omega, dtype=np.float64)
+    if Om.shape != (b + p, m):
+        raise ValueError(f"Omega must be {b + p}x{m}, got {Om.shape}")
+    R = np.zeros((m, n), dtype=np.float64, order="F")
+    jpvt = np.zeros(n, dtype=np.int32)
+    swaps = np.zeros(1, dtype=np.int64)
+    g2 = np.zeros(1, dtype=np.float64)
+    alpha = np.zeros(1, dtype=np.float64)
+    rc = lib.orc_srqr(m, n, _ptr(A64, ctypes.c_double), m, l, b, p, _ptr(Om, ctypes.c_double), float(g), d,
+                      seed_g, max_swaps, _ptr(R, ctypes.c_double), _ptr(jpvt, ctypes.c_int32),
+                      _ptr(swaps, ctypes.c_int64), _ptr(g2, ctypes.c_double), _ptr(alpha, ctypes.c_double))
+    if rc != 0:
+        raise ValueError(f"orc_srqr: error {rc}")
+    return SRQRResult(R, jpvt, int(swaps[0]), float(g2[0]), float(alpha[0]), l)
 
 
 def round_bf16(x: np.ndarray) -> np.ndarray:

@@ -33,6 +33,17 @@
  *    element of Omega and of A is first rounded to FP32, then to BF16 (8 significant bits,
  *    round to nearest, ties to even); the products and their sums are then formed exactly
  *    as in the FP64 sketch.  Only the initial sketch sees the rounding.
+ *  - SRQR (Alg. 3, orc_srqr) works on an explicit R.  Its RQRCP stage is Alg. 2 with Eq. (4)
+ *    to rank l; the sketch after the last block's update is the sketch of R22 whose column
+ *    norms / (b+p) start the estimates r_i (Eq. (4) and Eq. (5) give the same norms).  The
+ *    downdated estimates are used as they are, negative or not (only their argmax matters).
+ *    Estimate t of g_2 draws a fresh d x (l+1) Gaussian from orc_omega(d, l+1, seed_g + t).
+ *    A zero diagonal entry of R_hat gives g_2 = +inf with that column as the worst one.  The
+ *    round-robin swap moves the worst column to position l and shifts the columns after it
+ *    left by one; Givens rotations on rows (j, j+1), j = worst..l-1, across all n columns
+ *    restore the upper-trapezoidal form.  "r_{l+1} = R_{l+1,l+1}^2" is the squared norm of
+ *    the column now at position l, whose entries below row l are zero.  The swap loop is
+ *    capped at max_swaps (the paper only states that it ends).
  */
 #include <math.h>
 #include <stdint.h>
@@ -375,6 +386,148 @@ ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t 
     if (Bout) memcpy(Bout, B, sizeof(double) * (size_t)(l * n));
     free(B); free(Bq); free(Wh); free(Ob);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. 3 (SRQR, Sec. IV-E) on an explicit R.                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Alg. 3 "Swap ... One-step QR factorization of A(l+1:m,l+1:n) ... |alpha| = R_{l+1,l+1}  */
+/* ... r_i = r_i - A(l+1,i)^2": move the trailing column with the largest estimate r_i to  */
+/* position l, reduce R(l:m, l) to its first entry with one reflector applied to the       */
+/* trailing columns, and downdate the estimates by the new row l.  Returns |alpha|.         */
+static double srqr_extra_pivot(int64_t m, int64_t n, int64_t l, double* R, int32_t* jpvt, double* r)
+{
+    int64_t best = l;
+    for (int64_t i = l + 1; i < n; ++i)
+        if (r[i] > r[best]) best = i;
+    swap_cols(R, m, m, l, best);
+    int32_t tp = jpvt[l]; jpvt[l] = jpvt[best]; jpvt[best] = tp;
+    double tr = r[l]; r[l] = r[best]; r[best] = tr;
+    double* x = &AT(R, m, l, l);
+    const double t = house_gen(m - l, x);
+    for (int64_t s = l + 1; s < n; ++s) house_apply(m - l, x, t, &AT(R, m, l, s));
+    for (int64_t i = l + 1; i < m; ++i) AT(R, m, i, l) = 0.0;
+    for (int64_t i = l + 1; i < n; ++i) r[i] -= AT(R, m, l, i) * AT(R, m, l, i);
+    return fabs(AT(R, m, l, l));
+}
+
+/* Alg. 3 "g_2 ~ |alpha|/sqrt(d) ||Omega R_hat^{-T}||_{1,2}": X = Omega R_hat^{-T} row by row  */
+/* (row q of X is R_hat^{-1} times row q of Omega, by back substitution on the leading     */
+/* (l+1) x (l+1) block of R); ||X||_{1,2} is its largest column norm.  *imax receives that   */
+/* column.  A zero diagonal entry of R_hat gives g_2 = +inf with *imax at that column.       */
+static double srqr_g2(int64_t m, int64_t l, const double* R, double alpha, int64_t d, const double* Og,
+                      double* X, double* cn, int64_t* imax)
+{
+    const int64_t w = l + 1;
+    for (int64_t j = 0; j < w; ++j)
+        if (AT(R, m, j, j) == 0.0) { *imax = j; return INFINITY; }
+    for (int64_t q = 0; q < d; ++q)
+        for (int64_t j = w - 1; j >= 0; --j) {
+            double acc = Og[q * w + j];
+            for (int64_t c = j + 1; c < w; ++c) acc -= AT(R, m, j, c) * X[q * w + c];
+            X[q * w + j] = acc / AT(R, m, j, j);
+        }
+    int64_t best = 0;
+    for (int64_t j = 0; j < w; ++j) {
+        double ss = 0.0;
+        for (int64_t q = 0; q < d; ++q) ss += X[q * w + j] * X[q * w + j];
+        cn[j] = sqrt(ss);
+        if (cn[j] > cn[best]) best = j;
+    }
+    *imax = best;
+    return alpha / sqrt((double)d) * cn[best];
+}
+
+/*
+ * SRQR: RQRCP to rank l (Alg. 2, Eq. (4), sketch Omega of b+p rows), then the extra pivot
+ * chosen from the final sketch's column norms / (b+p), the randomized estimate of g_2 with a
+ * fresh d x (l+1) Gaussian matrix per estimate (estimate t draws orc_omega(d, l+1, seed_g+t)),
+ * and while g_2 > g: the worst column of R_hat (largest column of Omega R_hat^{-T}) rotated to
+ * position l (round robin: the columns after it move left by one), Givens rotations on rows
+ * (j, j+1) restoring the upper-trapezoidal form, the estimates r updated by row l, and a new
+ * extra pivot.  At most max_swaps swaps.
+ * R (m x n, ld m) receives the explicit factor: R(0:l+1, :) upper trapezoidal and the
+ * trailing block R(l+1:m, l+1:n); A(:, jpvt) = Q R for an orthogonal Q (not formed).
+ * Requires 1 <= l < min(m, n), g > 1, d >= 1.  Outputs: *swaps_out, the last *g2_out and
+ * *alpha_out = |R(l, l)|.  Returns 0, a negative argument position, or 1 on allocation failure.
+ */
+ORC_EXPORT int orc_srqr(int64_t m, int64_t n, const double* A, int64_t lda, int64_t l, int64_t b, int64_t p,
+                        const double* Omega, double g, int64_t d, uint64_t seed_g, int64_t max_swaps,
+                        double* R, int32_t* jpvt, int64_t* swaps_out, double* g2_out, double* alpha_out)
+{
+    if (m < 2) return -1;
+    if (n < 2) return -2;
+    if (lda < m) return -4;
+    if (l < 1 || l >= (m < n ? m : n)) return -5;
+    if (b < 1) return -6;
+    if (p < 0) return -7;
+    if (!(g > 1.0)) return -9;
+    if (d < 1) return -10;
+    if (max_swaps < 0) return -12;
+    const int64_t ls = b + p, w = l + 1;
+    double* W = (double*)malloc(sizeof(double) * (size_t)(m * n));
+    double* tau = (double*)malloc(sizeof(double) * (size_t)l);
+    double* Bs = (double*)malloc(sizeof(double) * (size_t)(ls * n));
+    double* r = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Og = (double*)malloc(sizeof(double) * (size_t)(d * w));
+    double* X = (double*)malloc(sizeof(double) * (size_t)(d * w));
+    double* cn = (double*)malloc(sizeof(double) * (size_t)w);
+    int rc = 1;
+    if (!W || !tau || !Bs || !r || !Og || !X || !cn) goto done;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) AT(W, m, i, j) = AT(A, lda, i, j);
+    int64_t rank;
+    rc = orc_rqrcp2(m, n, W, m, l, b, p, Omega, 4, 0, jpvt, tau, &rank, NULL, Bs);
+    if (rc != 0) goto done;
+    /* explicit R: upper trapezoid of the first l rows, and the trailing block W(l:m, l:n) */
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i)
+            AT(R, m, i, j) = (i < l) ? (i <= j ? AT(W, m, i, j) : 0.0) : (j >= l ? AT(W, m, i, j) : 0.0);
+    /* Alg. 3 "r_i = r_hat_i / (b+p)": squared column norms of the final sketch of R22 */
+    for (int64_t i = l; i < n; ++i) {
+        double ss = 0.0;
+        for (int64_t q = 0; q < ls; ++q) ss += AT(Bs, ls, q, i) * AT(Bs, ls, q, i);
+        r[i] = ss / (double)ls;
+    }
+    double alpha = srqr_extra_pivot(m, n, l, R, jpvt, r);
+    int64_t imax, swaps = 0;
+    orc_omega(d, w, seed_g, Og);
+    double g2 = srqr_g2(m, l, R, alpha, d, Og, X, cn, &imax);
+    while (g2 > g && swaps < max_swaps) {
+        /* round robin: column imax goes to position l, columns imax+1..l move left by one */
+        for (int64_t j = imax; j < l; ++j) {
+            swap_cols(R, m, m, j, j + 1);
+            int32_t tp = jpvt[j]; jpvt[j] = jpvt[j + 1]; jpvt[j + 1] = tp;
+        }
+        /* Givens rotations on rows (j, j+1) zero the subdiagonal of R(0:l+1, imax:l) */
+        for (int64_t j = imax; j < l; ++j) {
+            const double a = AT(R, m, j, j), bsub = AT(R, m, j + 1, j);
+            if (bsub != 0.0) {
+                const double h = hypot(a, bsub), c = a / h, sn = bsub / h;
+                for (int64_t col = j; col < n; ++col) {
+                    const double x = AT(R, m, j, col), y = AT(R, m, j + 1, col);
+                    AT(R, m, j, col) = c * x + sn * y;
+                    AT(R, m, j + 1, col) = -sn * x + c * y;
+                }
+            }
+            AT(R, m, j + 1, j) = 0.0;
+        }
+        /* Alg. 3 "r_{l+1} = R_{l+1,l+1}^2; r_i = r_i + A(l+1,i)^2": row l rejoins the trailing rows */
+        r[l] = AT(R, m, l, l) * AT(R, m, l, l);
+        for (int64_t i = l + 1; i < n; ++i) r[i] += AT(R, m, l, i) * AT(R, m, l, i);
+        alpha = srqr_extra_pivot(m, n, l, R, jpvt, r);
+        ++swaps;
+        orc_omega(d, w, seed_g + (uint64_t)swaps, Og);
+        g2 = srqr_g2(m, l, R, alpha, d, Og, X, cn, &imax);
+    }
+    if (swaps_out) *swaps_out = swaps;
+    if (g2_out) *g2_out = g2;
+    if (alpha_out) *alpha_out = alpha;
+    rc = 0;
+done:
+    free(W); free(tau); free(Bs); free(r); free(Og); free(X); free(cn);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------- */
