@@ -535,6 +535,32 @@ def run_ours(args, w, rank, world, local_rank):
         extra["lowrank_reorth"] = {"ms": round(min(t_re), 3), "orth_before": float(orth.item()),
                                    "orth_after": float(torch.linalg.norm(G - torch.eye(k, dtype=G.dtype, device=dev)))}
 
+    if args.srqr and not mixed and not diff:
+        # Alg. 3 (SRQR) on the same matrix: RQRCP to rank L, the extra pivot, the g2 estimate and
+        # any swaps; beside it the RQRCP stage alone to k = L
+        L = args.srqr
+        Aw = torch.empty_like(A0.t()).t()
+        ws = binding.workspace(binding.load().rqrcp_srqr_workspace_size(m, n, L, b, p, 8), dev)
+        t_sr, t_rq = [], []
+        for it in range(3):
+            for which in ("srqr", "rqrcp"):
+                Aw.copy_(A0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if which == "srqr":
+                    f = binding.srqr(Aw, L, b, p, seed=0, g=5.0, d=8, max_swaps=50, work=ws, stream=stream,
+                                     overwrite=True)
+                else:
+                    code = binding.rqrcp_factor(Aw, L, b, p, 0, jpvt, tau, work, stream)
+                    if code != 0:
+                        raise binding.RQRCPError(code, "factor (rank l)")
+                e1.record(stream)
+                torch.cuda.synchronize()
+                (t_sr if which == "srqr" else t_rq).append(e0.elapsed_time(e1))
+        extra["srqr"] = {"l": L, "g": 5.0, "d": 8, "max_swaps": 50, "ms": round(min(t_sr[1:]), 3),
+                         "rqrcp_to_l_ms": round(min(t_rq[1:]), 3), "swaps": f.swaps, "g2": f.g2}
+        del Aw, ws
+
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
@@ -686,6 +712,8 @@ def main():
     ap.add_argument("--formula", type=int, default=4, choices=[4, 5],
                     help="plain FP64 workloads: update the sketch between blocks with Eq. (4) (default) "
                          "or Eq. (5)")
+    ap.add_argument("--srqr", type=int, default=0, metavar="L",
+                    help="plain FP64 workloads: also time SRQR (Alg. 3) to rank L on the same matrix")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other form (mixed / plain FP64) on the same matrix")
     args = ap.parse_args()

@@ -120,6 +120,33 @@ int rqrcp_factor_ex(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int
                     void* work, size_t work_bytes, void* stream);
 
 /*
+ * Spectrum-revealing QR, Alg. 3 (Sec. IV-E), plain FP64.  Steps:
+ *   1. RQRCP to rank l (Alg. 2 with Eq. (4), block size b, oversampling p, sketch from `seed` or
+ *      the caller's Omega as in rqrcp_factor_ex; the sketch is updated after the last block too).
+ *   2. The extra pivot: the trailing column with the largest r_i = ||B(:, i)||^2 / (b+p) moves to
+ *      position l, one Householder step reduces A(l:m, l), and r_i -= R(l, i)^2.
+ *   3. g_2 ~ |alpha|/sqrt(d) ||Omega_g R_hat^{-T}||_{1,2}, with R_hat the leading (l+1) x (l+1)
+ *      block of R and alpha = R(l, l).  Omega_g is a fresh d x (l+1) Gaussian per estimate:
+ *      estimate t uses rqrcp_generate_omega(d, l+1, seed_g + t).
+ *   4. While g_2 > g and fewer than max_swaps swaps: the worst column of R_hat (the largest
+ *      column of Omega_g R_hat^{-T}) moves to position l by a round-robin rotation.  Givens
+ *      rotations restore the upper-trapezoidal form, r_l = R(l,l)^2, r_i += R(l,i)^2, then
+ *      steps 2 and 3 again.
+ * Output: A is overwritten with the explicit R of A(:, jpvt) = Q R.  R(0:l+1, :) is upper
+ * trapezoidal, the trailing block R22 = A(l+1:m, l+1:n), and every entry below the diagonal of
+ * columns 0..l is zero.  Q is not formed.  jpvt (n, device) is 0-based.  info (host, 3
+ * doubles, may be NULL) receives the swap count, the last g_2 estimate and |alpha|.  The call
+ * synchronises `stream` once per g_2 estimate.  Requires 1 <= l < min(m, n), g > 1, 1 <= d <=
+ * 65535, (l+1)*8 bytes of shared memory per block.  Errors: -1 m, -2 n, -3 A, -4 lda, -5 l, -6 b,
+ * -7 p, -10 ldo < m with Omega given, -11 g, -12 d, -14 max_swaps, -15 jpvt; RQRCP_ERR_*
+ * otherwise.  Workspace: rqrcp_srqr_workspace_size(m, n, l, b, p, d) bytes (0 if invalid).
+ */
+size_t rqrcp_srqr_workspace_size(int64_t m, int64_t n, int64_t l, int64_t b, int64_t p, int64_t d);
+int rqrcp_srqr(int64_t m, int64_t n, double* A, int64_t lda, int64_t l, int64_t b, int64_t p, uint64_t seed,
+               const double* Omega, int64_t ldo, double g, int64_t d, uint64_t seed_g, int64_t max_swaps,
+               int32_t* jpvt, double* info, void* work, size_t work_bytes, void* stream);
+
+/*
  * Mixed form of Alg. 2: A is FP32 (lda >= m).  The sketch B = Omega A (Alg. 2, the sketch
  * step) is formed from Omega and A rounded to BF16 (round to nearest even) with FP32
  * accumulation; the pivot search, the compact-WY trailing updates (TF32 hi/lo parts on the

@@ -38,6 +38,7 @@ ABI_SYMBOLS = (
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
     "rqrcp_backward_f32", "rqrcp_reorth_workspace_size", "rqrcp_lowrank_reorth",
     "rqrcp_batched_workspace_size", "rqrcp_factor_batched", "rqrcp_factor_ex",
+    "rqrcp_srqr_workspace_size", "rqrcp_srqr",
 )
 RQRCP_PROFILE_CLASSES = 14
 
@@ -73,6 +74,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                        _vp, _vp, _sz, _vp]),
             "rqrcp_factor_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, ctypes.c_int,
                                                _vp, _vp, _vp, _sz, _vp]),
+            "rqrcp_srqr_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i64, _i64]),
+            "rqrcp_srqr": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, ctypes.c_double,
+                                          _i64, _u64, _i64, _vp, ctypes.POINTER(ctypes.c_double), _vp, _sz, _vp]),
             "rqrcp_factor_mixed": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp,
                                                   _sz, _vp]),
             "rqrcp_factor_mixed_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, ctypes.c_int, _vp,
@@ -381,6 +385,39 @@ def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=N
     if formula not in (RQRCP_UPDATE_EQ4, RQRCP_UPDATE_EQ5):
         raise ValueError("formula must be 4 or 5")
     return _run_factor(Acm, k, b, p, seed, omega, False, work, stream, formula=formula)
+
+
+class SRQRFactorization:
+    """Output of srqr: R (the overwritten A: explicit, upper trapezoidal in rows 0..l, trailing
+    block R22 below), jpvt, the swap count, the last g2 estimate and |alpha| = |R(l, l)|."""
+
+    def __init__(self, R, jpvt, l, swaps, g2, alpha):
+        self.R, self.jpvt, self.l, self.swaps, self.g2, self.alpha = R, jpvt, l, swaps, g2, alpha
+
+
+def srqr(A, l: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, g: float = 5.0, d: int = 8,
+         seed_g: int = 0, max_swaps: int = 1000, work=None, stream=None, overwrite: bool = False) -> SRQRFactorization:
+    """Spectrum-revealing QR (Alg. 3) of a float64 CUDA matrix: RQRCP to rank l, the extra pivot,
+    the randomized g2 estimate and the swap loop while g2 > g (rqrcp_srqr)."""
+    import torch
+    if A.dtype != torch.float64:
+        raise TypeError("srqr expects float64")
+    Acm = colmajor(A)
+    if not overwrite:
+        Acm = Acm.t().clone().t()
+    m, n = Acm.shape
+    need = load().rqrcp_srqr_workspace_size(m, n, l, b, p, d)
+    if need == 0:
+        raise ValueError("invalid srqr arguments")
+    if work is None or work.numel() < need:
+        work = workspace(need, Acm.device)
+    jpvt = torch.empty(n, dtype=torch.int32, device=Acm.device)
+    info = (ctypes.c_double * 3)()
+    om, ldo = (None, 0) if omega is None else (_ptr(omega), _ld_rowmajor(omega))
+    code = load().rqrcp_srqr(m, n, _ptr(Acm), _ld(Acm), l, b, p, seed, om, ldo, float(g), d, seed_g, max_swaps,
+                             _ptr(jpvt), info, _ptr(work), work.numel(), _stream(stream))
+    _check(code, "rqrcp_srqr")
+    return SRQRFactorization(Acm, jpvt, l, int(info[0]), float(info[1]), float(info[2]))
 
 
 def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,

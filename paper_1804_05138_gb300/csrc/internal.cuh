@@ -234,6 +234,23 @@ template <typename T>
 cudaError_t launch_bfinish(T* B, T* Bc, int l, int64_t c0, int64_t nt, const double* P, int nsplit,
                            const Status* st, cudaStream_t s);
 
+// Alg. 3 (SRQR) on the explicit R in A (srqr.cu).  info (device, 4 doubles): g_2 estimate,
+// its worst column, |alpha|, and the tau of the latest one-step reflector.
+// prepare: zero the reflector tails of columns 0..l-1; r_i = ||B(:, i)||^2 / ls for i >= l.
+cudaError_t launch_srqr_prepare(double* A, int64_t lda, int64_t m, int64_t l, int64_t n, const double* B, int ls,
+                                double* r, const Status* st, cudaStream_t s);
+// extra pivot: argmax r -> column l, one Householder step on A(l:m, l:n), r_i -= A(l,i)^2.
+cudaError_t launch_srqr_extra_pivot(double* A, int64_t lda, int64_t m, int64_t l, int64_t n, double* r,
+                                    int32_t* jpvt, double* info, const Status* st, cudaStream_t s);
+// g_2 estimate with the d x (l+1) Gaussian drawn from `seed` (Og, X: d*(l+1) doubles each).
+cudaError_t launch_srqr_g2(const double* A, int64_t lda, int64_t l, int64_t d, uint64_t seed, double* Og, double* X,
+                           double* info, const Status* st, cudaStream_t s);
+size_t srqr_solve_smem(int64_t l);
+// one swap: round robin of columns imax..l, Givens re-triangularisation (cs: 2*(l+1) doubles),
+// r_l = R(l,l)^2 and r_i += R(l,i)^2.
+cudaError_t launch_srqr_swap(double* A, int64_t lda, int64_t l, int64_t n, int64_t imax, int32_t* jpvt, double* cs,
+                             double* r, const Status* st, cudaStream_t s);
+
 // Opt-in kernel timing (prof.cu): classes in the order of rqrcp_profile_class_name.
 enum ProfClass {
     K_OMEGA = 0, K_SKETCH_GEMM, K_SKETCH_REDUCE, K_PIVOT, K_SWAP, K_PANEL,

@@ -157,7 +157,7 @@ int check_work(void* work, size_t work_bytes, size_t need)
 template <typename T>
 int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, int64_t p, uint64_t seed,
                 const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
-                cudaStream_t s, int sketch_bf16 = 0, int formula = RQRCP_UPDATE_EQ4)
+                cudaStream_t s, int sketch_bf16 = 0, int formula = RQRCP_UPDATE_EQ4, bool final_b = false)
 {
     const int64_t l = b + p;
     const Layout L = make_layout(m, n, b, p, sizeof(T));
@@ -262,7 +262,8 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         else
             RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
                       launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st, s));
-        if (i + bb < k && !eq5)
+        // final_b: also after the last block, so that B sketches R22 (Alg. 3 reads its norms)
+        if ((i + bb < k || final_b) && !eq5)
             RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
                       launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));
         if (i + bb < k && eq5) {
@@ -287,6 +288,33 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         }
     }
     return RQRCP_OK;
+}
+
+// Alg. 3 workspace: the RQRCP layout, then r (n), the Gaussian and X of the g_2 estimate
+// (d*(l+1) each), the Givens pairs (2*(l+1)), info (4) and the RQRCP stage's tau (l).
+struct SrqrLayout {
+    Layout f;
+    size_t r, Og, X, cs, info, tau, total;
+};
+
+SrqrLayout make_srqr_layout(int64_t m, int64_t n, int64_t l, int64_t b, int64_t p, int64_t d)
+{
+    SrqrLayout S{};
+    S.f = make_layout(m, n, b, p, sizeof(double));
+    size_t off = S.f.total;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    S.r = take(sizeof(double) * (size_t)n);
+    S.Og = take(sizeof(double) * (size_t)d * (size_t)(l + 1));
+    S.X = take(sizeof(double) * (size_t)d * (size_t)(l + 1));
+    S.cs = take(sizeof(double) * 2 * (size_t)(l + 1));
+    S.info = take(sizeof(double) * 4);
+    S.tau = take(sizeof(double) * (size_t)l);
+    S.total = off;
+    return S;
 }
 
 int validate_factor(int64_t m, int64_t n, const void* A, int64_t lda, int64_t k, int64_t b, int64_t p,
@@ -489,6 +517,77 @@ __attribute__((visibility("default"))) int rqrcp_factor_ex(int64_t m, int64_t n,
     if (formula != RQRCP_UPDATE_EQ4 && formula != RQRCP_UPDATE_EQ5) return -11;
     return factor_impl<double>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, work,
                                work_bytes, (cudaStream_t)stream, 0, formula);
+}
+
+__attribute__((visibility("default"))) size_t rqrcp_srqr_workspace_size(int64_t m, int64_t n, int64_t l, int64_t b,
+                                                                        int64_t p, int64_t d)
+{
+    if (m < 2 || n < 2 || l < 1 || l >= (m < n ? m : n) || b < 1 || p < 0 || d < 1) return 0;
+    return make_srqr_layout(m, n, l, b, p, d).total;
+}
+
+__attribute__((visibility("default"))) int rqrcp_srqr(int64_t m, int64_t n, double* A, int64_t lda, int64_t l,
+                                                      int64_t b, int64_t p, uint64_t seed, const double* Omega,
+                                                      int64_t ldo, double g, int64_t d, uint64_t seed_g,
+                                                      int64_t max_swaps, int32_t* jpvt, double* info_out, void* work,
+                                                      size_t work_bytes, void* stream)
+{
+    if (m < 2) return -1;
+    if (n < 2) return -2;
+    if (A == nullptr) return -3;
+    if (lda < m) return -4;
+    if (l < 1 || l >= (m < n ? m : n)) return -5;
+    if (b < 1) return -6;
+    if (p < 0) return -7;
+    if (Omega != nullptr && ldo < m) return -10;
+    if (!(g > 1.0)) return -11;
+    if (d < 1 || d > 65535) return -12;
+    if (max_swaps < 0) return -14;
+    if (jpvt == nullptr) return -15;
+    const SrqrLayout S = make_srqr_layout(m, n, l, b, p, d);
+    if (int e = check_work(work, work_bytes, S.total)) return e;
+    if (srqr_solve_smem(l) > (size_t)dev_info().max_smem_optin) return RQRCP_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(work);
+    double* tau = reinterpret_cast<double*>(w + S.tau);
+    // Alg. 3 "Compute Q, R, Pi with Algorithm 2" (to rank l; B updated after the last block too)
+    if (int e = factor_impl<double>(m, n, A, lda, l, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, w,
+                                    S.f.total, s, 0, RQRCP_UPDATE_EQ4, true))
+        return e;
+    Status* st = reinterpret_cast<Status*>(w + S.f.status);
+    const double* B = reinterpret_cast<const double*>(w + S.f.B);
+    double* r = reinterpret_cast<double*>(w + S.r);
+    double* Og = reinterpret_cast<double*>(w + S.Og);
+    double* X = reinterpret_cast<double*>(w + S.X);
+    double* cs = reinterpret_cast<double*>(w + S.cs);
+    double* info = reinterpret_cast<double*>(w + S.info);
+    const int ls = (int)(b + p);
+    RQ_CHECK(launch_srqr_prepare(A, lda, m, l, n, B, ls, r, st, s));
+    RQ_CHECK(launch_srqr_extra_pivot(A, lda, m, l, n, r, jpvt, info, st, s));
+    RQ_CHECK(launch_srqr_g2(A, lda, l, d, seed_g, Og, X, info, st, s));
+    int64_t swaps = 0;
+    double h[4];
+    for (;;) {
+        // the loop test needs g_2 on the host: one synchronisation per estimate (swaps are rare)
+        int err = 0;
+        RQ_CHECK(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+        RQ_CHECK(cudaMemcpyAsync(&err, &st->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RQ_CHECK(cudaStreamSynchronize(s));
+        if (err != 0) return err;
+        if (!(h[0] > g) || swaps >= max_swaps) break;
+        const int64_t imax = (int64_t)h[1];
+        if (imax < 0 || imax > l) return RQRCP_ERR_CUDA;
+        RQ_CHECK(launch_srqr_swap(A, lda, l, n, imax, jpvt, cs, r, st, s));
+        RQ_CHECK(launch_srqr_extra_pivot(A, lda, m, l, n, r, jpvt, info, st, s));
+        ++swaps;
+        RQ_CHECK(launch_srqr_g2(A, lda, l, d, seed_g + (uint64_t)swaps, Og, X, info, st, s));
+    }
+    if (info_out != nullptr) {
+        info_out[0] = (double)swaps;
+        info_out[1] = h[0];
+        info_out[2] = h[2];
+    }
+    return RQRCP_OK;
 }
 
 __attribute__((visibility("default"))) int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k,

@@ -80,6 +80,19 @@ def test_factor_argument_codes(lib):
     assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, None, None, 0, None) == -13
     assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, 0, None) == 4  # no workspace
     assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 5, 4, fake, fake, None, 0, None) == 4
+    sr = lib.rqrcp_srqr
+    #      m  n  A    lda l  b  p  seed Omega ldo g    d  seed_g swaps jpvt info work bytes stream
+    assert sr(1, 5, fake, 5, 1, 1, 0, 0, None, 0, 5.0, 8, 0, 10, fake, None, None, 0, None) == -1
+    assert sr(5, 5, fake, 5, 5, 1, 0, 0, None, 0, 5.0, 8, 0, 10, fake, None, None, 0, None) == -5
+    assert sr(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 5.0, 8, 0, 10, fake, None, None, 0, None) == -10
+    assert sr(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 1.0, 8, 0, 10, fake, None, None, 0, None) == -11
+    assert sr(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5.0, 0, 0, 10, fake, None, None, 0, None) == -12
+    assert sr(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5.0, 8, 0, -1, fake, None, None, 0, None) == -14
+    assert sr(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5.0, 8, 0, 10, None, None, None, 0, None) == -15
+    assert sr(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5.0, 8, 0, 10, fake, None, None, 0, None) == 4  # no workspace
+    ws = lib.rqrcp_srqr_workspace_size
+    assert ws(5, 5, 5, 1, 0, 8) == 0 and ws(5, 5, 2, 1, 0, 0) == 0
+    assert ws(5, 5, 2, 1, 0, 8) > lib.rqrcp_workspace_size(5, 5, 2, 1, 0, 0)
 
 
 def test_other_entry_point_argument_codes(lib):
