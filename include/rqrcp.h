@@ -128,14 +128,16 @@ int rqrcp_factor_ex(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int
  *   3. g_2 ~ |alpha|/sqrt(d) ||Omega_g R_hat^{-T}||_{1,2}, with R_hat the leading (l+1) x (l+1)
  *      block of R and alpha = R(l, l).  Omega_g is a fresh d x (l+1) Gaussian per estimate:
  *      estimate t uses rqrcp_generate_omega(d, l+1, seed_g + t).
- *   4. While g_2 > g and fewer than max_swaps swaps: the worst column of R_hat (the largest
- *      column of Omega_g R_hat^{-T}) moves to position l by a round-robin rotation.  Givens
- *      rotations restore the upper-trapezoidal form, r_l = R(l,l)^2, r_i += R(l,i)^2, then
- *      steps 2 and 3 again.
+ *   4. While g_2 > g, fewer than max_swaps swaps so far, and the RQRCP stage's rank guard did
+ *      not fire before l pivots (R_hat would be singular to working precision): the worst
+ *      column of R_hat (the largest column of Omega_g R_hat^{-T}) moves to position l by a
+ *      round-robin rotation.  Givens rotations restore the upper-trapezoidal form,
+ *      r_l = R(l,l)^2, r_i += R(l,i)^2, then steps 2 and 3 again.
  * Output: A is overwritten with the explicit R of A(:, jpvt) = Q R.  R(0:l+1, :) is upper
  * trapezoidal, the trailing block R22 = A(l+1:m, l+1:n), and every entry below the diagonal of
- * columns 0..l is zero.  Q is not formed.  jpvt (n, device) is 0-based.  info (host, 3
- * doubles, may be NULL) receives the swap count, the last g_2 estimate and |alpha|.  The call
+ * columns 0..l is zero.  Q is not formed.  jpvt (n, device) is 0-based.  info (host, 4
+ * doubles, may be NULL) receives the swap count, the last g_2 estimate, |alpha| and the RQRCP
+ * stage's rank (pivots before its guard fired; l if it never did).  The call
  * synchronises `stream` once per g_2 estimate.  Requires 1 <= l < min(m, n), g > 1, 1 <= d <=
  * 65535, (l+1)*8 bytes of shared memory per block.  Errors: -1 m, -2 n, -3 A, -4 lda, -5 l, -6 b,
  * -7 p, -10 ldo < m with Omega given, -11 g, -12 d, -14 max_swaps, -15 jpvt; RQRCP_ERR_*

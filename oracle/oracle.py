@@ -84,7 +84,7 @@ def _load():
         lib.orc_lowrank.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i32p, _dp, _i64, _dp]
         lib.orc_lowrank.restype = ctypes.c_int
         lib.orc_srqr.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _i64, _dp, ctypes.c_double, _i64, _u64, _i64,
-                                 _dp, _i32p, _i64p, _dp, _dp]
+                                 _dp, _i32p, _i64p, _dp, _dp, _i64p]
         lib.orc_srqr.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -174,8 +174,8 @@ def rqrcp_seeded(A: np.ndarray, k: int, b: int, p: int, seed: int, formula: int 
 
 # --------------------------------------------------------------------------- Alg. 3
 class SRQRResult:
-    def __init__(self, R, jpvt, swaps, g2, alpha, l):
-        self.R, self.jpvt, self.swaps, self.g2, self.alpha, self.l = R, jpvt, swaps, g2, alpha, l
+    def __init__(self, R, jpvt, swaps, g2, alpha, l, rank):
+        self.R, self.jpvt, self.swaps, self.g2, self.alpha, self.l, self.rank = R, jpvt, swaps, g2, alpha, l, rank
 
 
 def srqr(A: np.ndarray, l: int, b: int, p: int, Omega: np.ndarray, g: float = 5.0, d: int = 8,
@@ -183,7 +183,8 @@ def srqr(A: np.ndarray, l: int, b: int, p: int, Omega: np.ndarray, g: float = 5.
     """Alg. 3 (SRQR): RQRCP to rank l with the sketch Omega ((b+p) x m), the extra pivot, the
     randomized g_2 estimate (d x (l+1) Gaussian matrices from seeds seed_g, seed_g+1, ...) and
     the swap loop while g_2 > g.  Returns the explicit R (m x n), jpvt, the swap count, the last
-    g_2 estimate and |alpha| = |R(l, l)|."""
+    g_2 estimate, |alpha| = |R(l, l)| and the RQRCP stage's rank (the swap loop is skipped when
+    its rank guard fired before l pivots)."""
     lib = _load()
     A64 = _fortran64(A)
     m, n = A64.shape
@@ -195,12 +196,14 @@ def srqr(A: np.ndarray, l: int, b: int, p: int, Omega: np.ndarray, g: float = 5.
     swaps = np.zeros(1, dtype=np.int64)
     g2 = np.zeros(1, dtype=np.float64)
     alpha = np.zeros(1, dtype=np.float64)
+    rank = np.zeros(1, dtype=np.int64)
     rc = lib.orc_srqr(m, n, _ptr(A64, ctypes.c_double), m, l, b, p, _ptr(Om, ctypes.c_double), float(g), d,
                       seed_g, max_swaps, _ptr(R, ctypes.c_double), _ptr(jpvt, ctypes.c_int32),
-                      _ptr(swaps, ctypes.c_int64), _ptr(g2, ctypes.c_double), _ptr(alpha, ctypes.c_double))
+                      _ptr(swaps, ctypes.c_int64), _ptr(g2, ctypes.c_double), _ptr(alpha, ctypes.c_double),
+                      _ptr(rank, ctypes.c_int64))
     if rc != 0:
         raise ValueError(f"orc_srqr: error {rc}")
-    return SRQRResult(R, jpvt, int(swaps[0]), float(g2[0]), float(alpha[0]), l)
+    return SRQRResult(R, jpvt, int(swaps[0]), float(g2[0]), float(alpha[0]), l, int(rank[0]))
 
 
 def round_bf16(x: np.ndarray) -> np.ndarray:

@@ -43,7 +43,8 @@
  *    left by one; Givens rotations on rows (j, j+1), j = worst..l-1, across all n columns
  *    restore the upper-trapezoidal form.  "r_{l+1} = R_{l+1,l+1}^2" is the squared norm of
  *    the column now at position l, whose entries below row l are zero.  The swap loop is
- *    capped at max_swaps (the paper only states that it ends).
+ *    capped at max_swaps (the paper only states that it ends), and skipped when the RQRCP
+ *    stage's rank guard fired before l pivots (R_hat is then singular to working precision).
  */
 #include <math.h>
 #include <stdint.h>
@@ -449,12 +450,16 @@ static double srqr_g2(int64_t m, int64_t l, const double* R, double alpha, int64
  * extra pivot.  At most max_swaps swaps.
  * R (m x n, ld m) receives the explicit factor: R(0:l+1, :) upper trapezoidal and the
  * trailing block R(l+1:m, l+1:n); A(:, jpvt) = Q R for an orthogonal Q (not formed).
- * Requires 1 <= l < min(m, n), g > 1, d >= 1.  Outputs: *swaps_out, the last *g2_out and
- * *alpha_out = |R(l, l)|.  Returns 0, a negative argument position, or 1 on allocation failure.
+ * Requires 1 <= l < min(m, n), g > 1, d >= 1.  Outputs: *swaps_out, the last *g2_out,
+ * *alpha_out = |R(l, l)| and *rank_out, the pivots of the RQRCP stage before its rank guard
+ * fired (l if it never did).  With rank < l, R_hat is singular to working precision and the
+ * swap loop is skipped (g_2 is still estimated once).  Returns 0, a negative argument
+ * position, or 1 on allocation failure.
  */
 ORC_EXPORT int orc_srqr(int64_t m, int64_t n, const double* A, int64_t lda, int64_t l, int64_t b, int64_t p,
                         const double* Omega, double g, int64_t d, uint64_t seed_g, int64_t max_swaps,
-                        double* R, int32_t* jpvt, int64_t* swaps_out, double* g2_out, double* alpha_out)
+                        double* R, int32_t* jpvt, int64_t* swaps_out, double* g2_out, double* alpha_out,
+                        int64_t* rank_out)
 {
     if (m < 2) return -1;
     if (n < 2) return -2;
@@ -494,7 +499,7 @@ ORC_EXPORT int orc_srqr(int64_t m, int64_t n, const double* A, int64_t lda, int6
     int64_t imax, swaps = 0;
     orc_omega(d, w, seed_g, Og);
     double g2 = srqr_g2(m, l, R, alpha, d, Og, X, cn, &imax);
-    while (g2 > g && swaps < max_swaps) {
+    while (g2 > g && swaps < max_swaps && rank >= l) {
         /* round robin: column imax goes to position l, columns imax+1..l move left by one */
         for (int64_t j = imax; j < l; ++j) {
             swap_cols(R, m, m, j, j + 1);
@@ -524,6 +529,7 @@ ORC_EXPORT int orc_srqr(int64_t m, int64_t n, const double* A, int64_t lda, int6
     if (swaps_out) *swaps_out = swaps;
     if (g2_out) *g2_out = g2;
     if (alpha_out) *alpha_out = alpha;
+    if (rank_out) *rank_out = rank;
     rc = 0;
 done:
     free(W); free(tau); free(Bs); free(r); free(Og); free(X); free(cn);

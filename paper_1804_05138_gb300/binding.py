@@ -389,10 +389,11 @@ def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=N
 
 class SRQRFactorization:
     """Output of srqr: R (the overwritten A: explicit, upper trapezoidal in rows 0..l, trailing
-    block R22 below), jpvt, the swap count, the last g2 estimate and |alpha| = |R(l, l)|."""
+    block R22 below), jpvt, the swap count, the last g2 estimate, |alpha| = |R(l, l)| and the
+    RQRCP stage's rank."""
 
-    def __init__(self, R, jpvt, l, swaps, g2, alpha):
-        self.R, self.jpvt, self.l, self.swaps, self.g2, self.alpha = R, jpvt, l, swaps, g2, alpha
+    def __init__(self, R, jpvt, l, swaps, g2, alpha, rank):
+        self.R, self.jpvt, self.l, self.swaps, self.g2, self.alpha, self.rank = R, jpvt, l, swaps, g2, alpha, rank
 
 
 def srqr(A, l: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, g: float = 5.0, d: int = 8,
@@ -412,12 +413,12 @@ def srqr(A, l: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, g: float
     if work is None or work.numel() < need:
         work = workspace(need, Acm.device)
     jpvt = torch.empty(n, dtype=torch.int32, device=Acm.device)
-    info = (ctypes.c_double * 3)()
+    info = (ctypes.c_double * 4)()
     om, ldo = (None, 0) if omega is None else (_ptr(omega), _ld_rowmajor(omega))
     code = load().rqrcp_srqr(m, n, _ptr(Acm), _ld(Acm), l, b, p, seed, om, ldo, float(g), d, seed_g, max_swaps,
                              _ptr(jpvt), info, _ptr(work), work.numel(), _stream(stream))
     _check(code, "rqrcp_srqr")
-    return SRQRFactorization(Acm, jpvt, l, int(info[0]), float(info[1]), float(info[2]))
+    return SRQRFactorization(Acm, jpvt, l, int(info[0]), float(info[1]), float(info[2]), int(info[3]))
 
 
 def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,

@@ -567,14 +567,15 @@ __attribute__((visibility("default"))) int rqrcp_srqr(int64_t m, int64_t n, doub
     RQ_CHECK(launch_srqr_g2(A, lda, l, d, seed_g, Og, X, info, st, s));
     int64_t swaps = 0;
     double h[4];
+    Status hs{};
     for (;;) {
         // the loop test needs g_2 on the host: one synchronisation per estimate (swaps are rare)
-        int err = 0;
         RQ_CHECK(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
-        RQ_CHECK(cudaMemcpyAsync(&err, &st->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RQ_CHECK(cudaMemcpyAsync(&hs, st, sizeof(Status), cudaMemcpyDeviceToHost, s));
         RQ_CHECK(cudaStreamSynchronize(s));
-        if (err != 0) return err;
-        if (!(h[0] > g) || swaps >= max_swaps) break;
+        if (hs.error != 0) return hs.error;
+        // a rank guard that fired before l pivots leaves R_hat singular to working precision
+        if (!(h[0] > g) || swaps >= max_swaps || hs.rank < l) break;
         const int64_t imax = (int64_t)h[1];
         if (imax < 0 || imax > l) return RQRCP_ERR_CUDA;
         RQ_CHECK(launch_srqr_swap(A, lda, l, n, imax, jpvt, cs, r, st, s));
@@ -586,6 +587,7 @@ __attribute__((visibility("default"))) int rqrcp_srqr(int64_t m, int64_t n, doub
         info_out[0] = (double)swaps;
         info_out[1] = h[0];
         info_out[2] = h[2];
+        info_out[3] = (double)hs.rank;
     }
     return RQRCP_OK;
 }

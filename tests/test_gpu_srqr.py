@@ -121,3 +121,19 @@ def test_seeded_sketch_matches_oracle(gpu, orc):
     A0 = inputs.spectrum_matrix(m, n, inputs.sigma_log_decay(min(m, n)))
     R, jp, f, ref = _compare(orc, A0, l, b, p, orc.omega(b + p, m, seed), gpu=gpu, seed=seed)
     _check_factor(A0, R, jp, l)
+
+
+def test_rank_below_l_skips_the_swap_loop(gpu, orc):
+    """Ten nonzero columns among forty, l = 15: the RQRCP stage stops at rank 10, R_hat has
+    exact zeros on its diagonal and the loop is skipped, as in the oracle."""
+    rng = np.random.default_rng(3)
+    A0 = np.zeros((60, 40))
+    A0[:, ::4] = rng.standard_normal((60, 10))
+    Om = inputs.gaussian_sketch(14, 60, seed=0)
+    R, jp, f = _run(gpu, A0, 15, 8, 6, Om)
+    ref = orc.srqr(A0, 15, 8, 6, Om, g=5.0, d=8)
+    assert f.rank == ref.rank == 10
+    assert f.swaps == ref.swaps == 0 and f.g2 == np.inf
+    assert np.array_equal(jp[:10], ref.jpvt[:10])
+    assert np.all(R[10:, 10:] == 0.0)
+    _check_factor(A0, R, jp, 15)

@@ -137,6 +137,20 @@ def test_exact_estimates_pick_the_largest_trailing_column(orc):
         _check_factor(A, res)
 
 
+def test_rank_below_l_skips_the_swap_loop(orc):
+    """Ten nonzero columns among forty: the RQRCP stage's rank guard stops at 10 < l, R_hat
+    has exact zeros on its diagonal (g2 = +inf), and the loop is skipped instead of swapping
+    up to the cap; R is still a factorization with R22 exactly zero."""
+    rng = np.random.default_rng(3)
+    A = np.zeros((60, 40))
+    A[:, ::4] = rng.standard_normal((60, 10))
+    res = orc.srqr(A, 15, 8, 6, inputs.gaussian_sketch(14, 60, seed=0), g=5.0, d=8)
+    assert res.rank == 10 and res.swaps == 0 and res.g2 == np.inf
+    assert sorted(res.jpvt[:10].tolist()) == list(range(0, 40, 4))
+    assert np.all(res.R[10:, 10:] == 0.0)
+    _check_factor(A, res)
+
+
 # ------------------------------------------------------------------------------ S4
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_r22_bounds_of_sec4(orc, seed):
