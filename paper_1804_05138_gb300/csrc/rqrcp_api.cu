@@ -95,14 +95,15 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
 }
 
 // Split-K factor for an M x N result contracted over K on the SIMT contraction (64 x 64 tiles):
-// the split count S <= kMaxSplit minimising waves x (rows per split + a fixed cost of 64 rows),
+// the split count S <= max_split minimising waves x (rows per split + a fixed cost of 64 rows),
 // a wave being the blocks resident on the whole GPU at once; splits of at least 64 rows.
-void choose_split(int64_t M, int64_t N, int64_t K, int& nsplit, int64_t& kchunk, int elem_bytes = 8)
+void choose_split(int64_t M, int64_t N, int64_t K, int& nsplit, int64_t& kchunk, int elem_bytes = 8,
+                  int64_t max_split = kMaxSplit)
 {
     const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
     const int64_t wave = (int64_t)gemm_tn_blocks_per_sm(elem_bytes) * dev_info().sms;
     int64_t smax = (K + 63) / 64;
-    if (smax > kMaxSplit) smax = kMaxSplit;
+    if (smax > max_split) smax = max_split;
     if (smax < 1) smax = 1;
     int64_t best = 1, best_cost = -1;
     for (int64_t S = 1; S <= smax; ++S) {
@@ -273,7 +274,10 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
             T* OmT = Om + i;
             int ns2;
             int64_t kc2;
-            choose_split(bb, l, mr, ns2, kc2, (int)sizeof(T));
+            // only bb x l outputs (two 64-wide tiles): more K splits than kMaxSplit, as many as
+            // the partial buffer (kMaxSplit * n * max(l, b) doubles) holds, keep the GPU busy
+            const int64_t pcap = (int64_t)kMaxSplit * n * (l > b ? l : b);
+            choose_split(bb, l, mr, ns2, kc2, (int)sizeof(T), pcap / ((int64_t)bb * l));
             RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, (double)mr * l * es,
                       launch_gemm_tn<T>(Vp, lda, OmT, m, bb, l, mr, kc2, P, 1, 0, st, s));
             RQ_LAUNCH(K_BUPDATE, (double)bb * bb * l, ((double)ns2 + 1.0) * bb * l * 8,
