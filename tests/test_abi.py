@@ -104,3 +104,18 @@ def test_other_entry_point_argument_codes(lib):
     assert lib.rqrcp_lowrank(5, 5, 6, fake, 5, fake, fake, fake, 5, fake, 5, None, 0, None) == -3
     assert lib.rqrcp_lowrank(5, 5, 2, fake, 5, fake, fake, fake, 5, None, 5, None, 0, None) == -10
     assert lib.rqrcp_read_status(None, None, None) == -1
+
+
+def test_binding_rejects_bad_python_arguments(lib):
+    """The Python wrappers check dtype and the sketch-update choice before any device call."""
+    import torch
+    from paper_1804_05138_gb300 import binding
+    A64 = torch.zeros((8, 6), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        binding.factor(A64, 2, 2, 1, formula=3)
+    with pytest.raises(TypeError):
+        binding.factor(A64.float(), 2, 2, 1)
+    with pytest.raises(TypeError):
+        binding.srqr(A64.float(), 2, 2, 1)
+    with pytest.raises(ValueError):
+        binding.srqr(A64, 6, 2, 1)          # l must be below min(m, n): workspace size 0
