@@ -1321,7 +1321,8 @@ __attribute__((visibility("default"))) int rqrcp_factor_batched(int64_t count, c
     int* counter = reinterpret_cast<int*>(w + off);
     off += 256;
     char* scratch = w + off;
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (allow_max_dynamic_smem(batched_kernel) != cudaSuccess) {
             cudaGetLastError();

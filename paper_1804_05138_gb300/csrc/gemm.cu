@@ -439,7 +439,8 @@ cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, con
                          double* Tm, const Status* st, cudaStream_t s)
 {
     const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)bb);
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(tform_kernel)) return e;
         attr_set = true;
@@ -454,13 +455,15 @@ cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t 
     if (nc <= 0) return cudaSuccess;
     const int threads = 256, nw = threads / 32;
     const size_t smem = sizeof(double) * ((size_t)bb * (bb | 1) + (size_t)nw * bb);
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(reduce_y_kernel)) return e;
         attr_set = true;
     }
     if (fp32c && bb <= 64) {
-        static bool set_c = false;
+        static bool set_c_dev[kMaxDevices] = {};
+        bool& set_c = set_c_dev[current_device()];
         if (!set_c) {
             if (cudaError_t e = allow_max_dynamic_smem(reduce_y_f32c_kernel)) return e;
             set_c = true;

@@ -548,7 +548,8 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
         kern<<<grid, TC_THREADS, smem, s>>>(mapC, mapX, a, P, const_cast<Status*>(st));
         return cudaGetLastError();
     };
-    static bool set[6] = {false, false, false, false, false, false};
+    static bool set_dev[kMaxDevices][6] = {};
+    bool(&set)[6] = set_dev[current_device()];
     if (bf) {
         if (Nb <= 32) return run(gemm_tn_tc_kernel<32, true>, set[3]);
         if (Nb <= 64) return run(gemm_tn_tc_kernel<64, true>, set[4]);

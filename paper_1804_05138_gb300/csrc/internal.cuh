@@ -123,6 +123,19 @@ struct DevInfo {
 };
 const DevInfo& dev_info();
 
+// Kernel attributes such as the dynamic shared-memory limit are set per device: the flags that
+// record "already set" are kept per device, indexed by the calling thread's current device.
+constexpr int kMaxDevices = 64;
+inline int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        d = 0;
+    }
+    return (d < 0 || d >= kMaxDevices) ? 0 : d;
+}
+
 // Allow a kernel the largest dynamic shared memory the device grants next to the kernel's
 // own static shared memory.  Returns the runtime error, if any.
 template <typename K>

@@ -342,7 +342,8 @@ cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, dou
 {
     constexpr bool f32 = sizeof(T) == 4;
     const void* kern = f32 ? (const void*)panel_f32_kernel : (const void*)panel_kernel<double>;
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (cudaError_t e = f32 ? allow_max_dynamic_smem(panel_f32_kernel) : allow_max_dynamic_smem(panel_kernel<double>))
             return e;

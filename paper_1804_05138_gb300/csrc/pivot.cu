@@ -342,7 +342,8 @@ template <typename T>
 cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int32_t* jpvt,
                          int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s)
 {
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(pivot_kernel<T>)) return e;
         attr_set = true;

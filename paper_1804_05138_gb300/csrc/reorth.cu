@@ -295,7 +295,8 @@ __attribute__((visibility("default"))) int rqrcp_lowrank_reorth(int64_t m, int64
     }
     // Cholesky (cooperative), gated by the flag
     {
-        static bool attr_set = false;
+        static bool attr_set_dev[kMaxDevices] = {};
+        bool& attr_set = attr_set_dev[current_device()];
         if (!attr_set) {
             if (allow_max_dynamic_smem(chol_kernel) != cudaSuccess) {
                 cudaGetLastError();

@@ -131,6 +131,9 @@ __global__ void __launch_bounds__(kT) srqr_house_kernel(double* A, int64_t lda, 
     __shared__ double sv[32];
     double* x = &at(A, lda, l, l);
     const int64_t len = m - l;
+    // read before the block sum: its barriers order every thread's read before thread 0
+    // overwrites x[0] with beta
+    const double alpha = x[0];
     double ss = 0.0;
     for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) ss = fma(x[i], x[i], ss);
     ss = block_sum(ss, sv);
@@ -138,7 +141,6 @@ __global__ void __launch_bounds__(kT) srqr_house_kernel(double* A, int64_t lda, 
         if (threadIdx.x == 0) info[3] = 0.0;
         return;
     }
-    const double alpha = x[0];
     const double nrm = sqrt(alpha * alpha + ss);
     const double beta = (alpha >= 0.0) ? -nrm : nrm;
     const double scal = 1.0 / (alpha - beta);
@@ -363,7 +365,8 @@ size_t srqr_solve_smem(int64_t l) { return sizeof(double) * (size_t)(l + 1); }
 cudaError_t launch_srqr_g2(const double* A, int64_t lda, int64_t l, int64_t d, uint64_t seed, double* Og, double* X,
                            double* info, const Status* st, cudaStream_t s)
 {
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(srqr_solve_kernel)) return e;
         attr_set = true;

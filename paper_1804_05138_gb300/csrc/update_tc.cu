@@ -327,7 +327,8 @@ cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long 
     a.maskV = maskV;
     a.ntiles = ntiles;
     a.total = ((mr + UT_BM - 1) / UT_BM) * ntiles;
-    static bool attr_set = false;
+    static bool attr_set_dev[kMaxDevices] = {};
+    bool& attr_set = attr_set_dev[current_device()];
     if (!attr_set) {
         if (cudaError_t e = allow_max_dynamic_smem(update_tc_kernel)) return e;
         attr_set = true;
