@@ -51,13 +51,23 @@ size_t rqrcp_workspace_size(int64_t m, int64_t n, int64_t k, int64_t b, int64_t 
 
 /*
  * Gaussian sketching matrix of Alg. 2 ("Generate i.i.d Gaussian matrix Omega in
- * N(0,1)^{(b+p) x m}").  Writes Omega (l x m, row-major, ldo >= m) on the device.
- * Element with flat index q = r*m + c is lane q%4 of Philox4x64-10 (Salmon et al.,
- * SC'11) evaluated at counter (q/4,0,0,0) with key (seed,0); lanes (0,1) and (2,3) are
- * Box-Muller pairs: u1 = ((w0>>11)+1)*2^-53, u2 = (w1>>11)*2^-53,
- * z_even = sqrt(-2 ln u1) cos(2 pi u2), z_odd = sqrt(-2 ln u1) sin(2 pi u2).
- * The _f32 twin rounds the same doubles to float.
+ * N(0,1)^{(b+p) x m}"), drawn on the HOST: rqrcp_generate_omega_host writes Omega (l x m,
+ * row-major, ldo >= m) into host memory.  Element with flat index q = r*m + c is lane q%4 of
+ * Philox4x64-10 (Salmon et al., SC'11) evaluated at counter (q/4,0,0,0) with key (seed,0);
+ * lanes (0,1) and (2,3) are Box-Muller pairs: u1 = ((w0>>11)+1)*2^-53, u2 = (w1>>11)*2^-53,
+ * z_even = sqrt(-2 ln u1) cos(2 pi u2), z_odd = sqrt(-2 ln u1) sin(2 pi u2), evaluated in IEEE
+ * double with the C library's log, sqrt, cos and sin and no fused multiply-add.  The draw runs
+ * on host threads (the bits do not depend on their number).  Every seeded entry point of this
+ * library uses exactly this draw (its FP32 form rounds it to float), so a caller holding the
+ * same C library reproduces the sketch bit for bit.  Errors: -1 l < 1, -2 m < 1, -4 Omega NULL,
+ * -5 ldo < m.
+ *
+ * rqrcp_generate_omega / rqrcp_generate_omega_f32 write the same draw (FP64, or rounded to FP32)
+ * into DEVICE memory on `stream`: one copy from pageable host memory (the last (seed, l, m) draw
+ * is kept on the host for reuse).  Such a copy may synchronise the host with the stream and cannot
+ * be captured in a CUDA graph; the seeded factorizations below use the same path.
  */
+int rqrcp_generate_omega_host(int64_t l, int64_t m, uint64_t seed, double* Omega, int64_t ldo);
 int rqrcp_generate_omega(int64_t l, int64_t m, uint64_t seed, double* Omega, int64_t ldo, void* stream);
 int rqrcp_generate_omega_f32(int64_t l, int64_t m, uint64_t seed, float* Omega, int64_t ldo, void* stream);
 
@@ -83,18 +93,23 @@ int rqrcp_sketch(int64_t m, int64_t n, const double* A, int64_t lda, const doubl
  * Argmax ties go to the smallest current column position.  Rank guard: if the largest
  * remaining sketch norm^2 falls to (10*max(m,n)*2^-53)^2 times the largest initial one,
  * pivoting stops for good (the remaining columns keep their order, B is no longer
- * updated); rqrcp_read_status reports the pivots taken before that as the rank.
+ * updated); the number of pivots taken before that is the rank.  rank_out (DEVICE pointer to
+ * one int64, may be NULL) receives the rank in stream order, when the factorization has run;
+ * rqrcp_read_status reports it too.  The seeded sketch is rqrcp_generate_omega's draw, copied
+ * from pageable host memory at the start of the call (not capturable in a CUDA graph; use
+ * rqrcp_factor_with_omega there).
  * Limits of the library: l = b+p <= 1024 and the sketch and panel must fit in shared
  * memory across the GPU (checked; RQRCP_ERR_UNSUPPORTED otherwise).
  */
 int rqrcp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b, int64_t p,
-                 uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes, void* stream);
+                 uint64_t seed, int32_t* jpvt, double* tau, int64_t* rank_out, void* work, size_t work_bytes,
+                 void* stream);
 
-/* As rqrcp_factor, with the l x m sketching matrix Omega (l = b+p, row-major, ldo >= m)
- * supplied by the caller instead of drawn from a seed. */
+/* As rqrcp_factor, with the l x m sketching matrix Omega (l = b+p, row-major, ldo >= m, device
+ * memory) supplied by the caller instead of drawn from a seed.  Nothing is copied from the host. */
 int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
                             int64_t p, const double* Omega, int64_t ldo, int32_t* jpvt, double* tau,
-                            void* work, size_t work_bytes, void* stream);
+                            int64_t* rank_out, void* work, size_t work_bytes, void* stream);
 
 #define RQRCP_UPDATE_EQ4 4 /* sketch update of Eq. (4) (Duersch-Gu): the default */
 #define RQRCP_UPDATE_EQ5 5 /* sketch update of Eq. (5) (Martinsson et al.) */
@@ -117,7 +132,7 @@ int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda, int64_
  */
 int rqrcp_factor_ex(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b, int64_t p,
                     uint64_t seed, const double* Omega, int64_t ldo, int formula, int32_t* jpvt, double* tau,
-                    void* work, size_t work_bytes, void* stream);
+                    int64_t* rank_out, void* work, size_t work_bytes, void* stream);
 
 /*
  * Spectrum-revealing QR, Alg. 3 (Sec. IV-E), plain FP64.  Steps:
@@ -162,19 +177,22 @@ int rqrcp_srqr(int64_t m, int64_t n, double* A, int64_t lda, int64_t l, int64_t 
  * accuracy class is the same.
  */
 int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
-                       uint64_t seed, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
-                       void* stream);
+                       uint64_t seed, int32_t* jpvt, double* tau, int64_t* rank_out, void* work,
+                       size_t work_bytes, void* stream);
 
 #define RQRCP_SKETCH_BF16 0 /* sketch operands rounded to BF16, FP32 accumulation */
 #define RQRCP_SKETCH_FP32 1 /* sketch with FP32-level accuracy (TF32 hi/lo parts, or FP32 FMA) */
 
-/* rqrcp_factor_mixed with the sketch precision chosen by `sketch` (RQRCP_SKETCH_*; any other
- * value returns -9, later arguments shift by one).  RQRCP_SKETCH_BF16 is rqrcp_factor_mixed;
- * RQRCP_SKETCH_FP32 uses the rank guard 10*sqrt(max(m,n))*2^-24 (about ten times the rounding
- * noise of an FP32 sketch column). */
+/* rqrcp_factor_mixed with the sketching matrix and the sketch precision chosen by the caller.
+ * Omega: the l x m FP32 sketching matrix (device, row-major, ldo >= m), or NULL to draw it from
+ * `seed` as rqrcp_generate_omega_f32 does (ldo is then ignored; with Omega given nothing is copied
+ * from the host).  sketch: RQRCP_SKETCH_BF16 (as
+ * rqrcp_factor_mixed) or RQRCP_SKETCH_FP32, which uses the rank guard 10*sqrt(max(m,n))*2^-24
+ * (about ten times the rounding noise of an FP32 sketch column).  Errors as rqrcp_factor_mixed,
+ * with -10 ldo < m with Omega given, -11 sketch invalid, -12 jpvt NULL, -13 tau NULL. */
 int rqrcp_factor_mixed_ex(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
-                          uint64_t seed, int sketch, int32_t* jpvt, double* tau, void* work,
-                          size_t work_bytes, void* stream);
+                          uint64_t seed, const float* Omega, int64_t ldo, int sketch, int32_t* jpvt, double* tau,
+                          int64_t* rank_out, void* work, size_t work_bytes, void* stream);
 
 /*
  * Synchronises `stream`, then reads the device-side status left in `work` by the last
@@ -253,7 +271,8 @@ int rqrcp_backward_f32(int64_t m, int64_t n, int64_t k, const float* A, int64_t 
  * device's one array, which keeps the last call's contents; the status block is cleared at
  * the start of each call.  Calls on the same device that overlap on the GPU (different
  * streams or different host threads) race on the array, so serialise them.  Device-side
- * status (non-finite sketch) is not reported: a non-finite A shows as NaN/Inf in B.
+ * status (non-finite sketch) is not reported: every column of B is written, and a column of A
+ * holding NaN or Inf gives a non-finite column of B.
  */
 int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, const double* Omega, int64_t l,
                          int64_t ldo, double* B, int64_t ldb, void* stream);
@@ -268,12 +287,15 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  * 1 <= b <= b_max <= 64 (b is per matrix, e.g. from the autotuner).  `order` (device, count
  * ints) is the processing order (largest first balances best); one block per SM takes the next
  * matrix from an atomic counter and factors it alone.  All matrices share one FP32 sketching
- * matrix Omega (l_max x m_max, l_max = b_max + p, drawn from `seed` as rqrcp_generate_omega_f32);
- * matrix i uses its leading (b_i + p) x m_i block.  Per-matrix results as rqrcp_factor_mixed;
+ * matrix Omega (device, l_max x m_max row-major with ldo >= m_max, l_max = b_max + p; e.g.
+ * rqrcp_generate_omega_f32's draw, made once before the batched calls); matrix i uses its leading
+ * (b_i + p) x m_i block.  Per-matrix results as rqrcp_factor_mixed;
  * rank is -1 when the sketch of that matrix is not finite, and -2 when a tensor-core wait of
  * the block factoring it gave up after 2 s (that block then stops taking matrices; the others
- * finish the batch; matrices never taken keep rank 0).  The call is two kernels and a memset on
- * `stream` and allocates nothing (graph-capturable).  Each block holds all of its SM's tensor
+ * finish the batch; matrices never taken keep rank 0).  The call is one kernel and a memset on
+ * `stream`, copies nothing from the host and allocates nothing (graph-capturable).  Errors: -1
+ * count < 0, -2 descs NULL, -3 order NULL, -4 m_max, -5 n_max, -6 b_max, -7 p, -8 Omega NULL,
+ * -9 ldo < m_max.  Each block holds all of its SM's tensor
  * memory for the launch.  `work` needs rqrcp_batched_workspace_size(m_max, n_max, b_max, p)
  * bytes.  Limits: the block's shared memory (max(8 m_max floats, 168 KB) + n_max doubles +
  * b_max^2 doubles + ~3 KB) must fit, else RQRCP_ERR_UNSUPPORTED (m_max <= ~5600 with
@@ -281,7 +303,8 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  */
 size_t rqrcp_batched_workspace_size(int64_t m_max, int64_t n_max, int64_t b_max, int64_t p);
 int rqrcp_factor_batched(int64_t count, const void* descs, const int* order, int64_t m_max, int64_t n_max,
-                         int64_t b_max, int64_t p, uint64_t seed, void* work, size_t work_bytes, void* stream);
+                         int64_t b_max, int64_t p, const float* Omega, int64_t ldo, void* work, size_t work_bytes,
+                         void* stream);
 
 /*
  * Kernel-level timing for measurement (not part of the method).  Between
@@ -297,6 +320,24 @@ int rqrcp_factor_batched(int64_t count, const void* descs, const int* order, int
 int rqrcp_profile_begin(void);
 int rqrcp_profile_end(int nmax, int64_t* launches, double* ms, double* flops, double* bytes);
 const char* rqrcp_profile_class_name(int cls);
+
+/*
+ * Throughput probes for the roofline denominators (measurement, not part of the method).  kind:
+ *   RQRCP_PROBE_DFMA     register-resident FP64 FMA chains (8 per thread, 64 warps per SM)
+ *   RQRCP_PROBE_FFMA     the same in FP32
+ *   RQRCP_PROBE_TC_TF32  back-to-back tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, one
+ *                        CTA per SM, operands in shared memory, accumulator in tensor memory
+ *   RQRCP_PROBE_TC_BF16  the same with kind::f16 on BF16 operands (K = 16)
+ * One untimed launch, then one launch timed with CUDA events on `stream`; the call synchronises
+ * the stream.  *tflops receives the dense rate (2 flops per multiply-add) and *ms (may be NULL)
+ * the timed launch's duration.  Errors: -1 kind, -2 tflops NULL; RQRCP_ERR_TIMEOUT if a
+ * tensor-core wait gave up (2 s), RQRCP_ERR_CUDA otherwise.
+ */
+#define RQRCP_PROBE_DFMA 0
+#define RQRCP_PROBE_FFMA 1
+#define RQRCP_PROBE_TC_TF32 2
+#define RQRCP_PROBE_TC_BF16 3
+int rqrcp_peak_probe(int kind, double* tflops, double* ms, void* stream);
 
 #ifdef __cplusplus
 }

@@ -31,14 +31,15 @@ RQRCP_UPDATE_EQ5 = 5
 
 # Every symbol include/rqrcp.h declares.
 ABI_SYMBOLS = (
-    "rqrcp_error_string", "rqrcp_workspace_size", "rqrcp_generate_omega", "rqrcp_generate_omega_f32",
+    "rqrcp_error_string", "rqrcp_workspace_size", "rqrcp_generate_omega_host", "rqrcp_generate_omega",
+    "rqrcp_generate_omega_f32",
     "rqrcp_sketch", "rqrcp_factor", "rqrcp_factor_with_omega", "rqrcp_factor_mixed", "rqrcp_factor_mixed_ex",
     "rqrcp_read_status", "rqrcp_lowrank_workspace_size", "rqrcp_lowrank",
     "rqrcp_profile_begin", "rqrcp_profile_end", "rqrcp_profile_class_name",
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
     "rqrcp_backward_f32", "rqrcp_reorth_workspace_size", "rqrcp_lowrank_reorth",
     "rqrcp_batched_workspace_size", "rqrcp_factor_batched", "rqrcp_factor_ex",
-    "rqrcp_srqr_workspace_size", "rqrcp_srqr",
+    "rqrcp_srqr_workspace_size", "rqrcp_srqr", "rqrcp_peak_probe",
 )
 RQRCP_PROFILE_CLASSES = 14
 
@@ -66,21 +67,23 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         sig = {
             "rqrcp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
             "rqrcp_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i64, ctypes.c_int]),
+            "rqrcp_generate_omega_host": (ctypes.c_int, [_i64, _i64, _u64, _vp, _i64]),
             "rqrcp_generate_omega": (ctypes.c_int, [_i64, _i64, _u64, _vp, _i64, _vp]),
             "rqrcp_generate_omega_f32": (ctypes.c_int, [_i64, _i64, _u64, _vp, _i64, _vp]),
             "rqrcp_sketch": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _sz, _vp]),
-            "rqrcp_factor": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp, _sz, _vp]),
+            "rqrcp_factor": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp, _vp, _sz,
+                                            _vp]),
             "rqrcp_factor_with_omega": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _vp, _i64, _vp,
-                                                       _vp, _vp, _sz, _vp]),
+                                                       _vp, _vp, _vp, _sz, _vp]),
             "rqrcp_factor_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, ctypes.c_int,
-                                               _vp, _vp, _vp, _sz, _vp]),
+                                               _vp, _vp, _vp, _vp, _sz, _vp]),
             "rqrcp_srqr_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i64, _i64]),
             "rqrcp_srqr": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, ctypes.c_double,
                                           _i64, _u64, _i64, _vp, ctypes.POINTER(ctypes.c_double), _vp, _sz, _vp]),
-            "rqrcp_factor_mixed": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp,
+            "rqrcp_factor_mixed": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _vp, _vp, _vp,
                                                   _sz, _vp]),
-            "rqrcp_factor_mixed_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, ctypes.c_int, _vp,
-                                                     _vp, _vp, _sz, _vp]),
+            "rqrcp_factor_mixed_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64,
+                                                     ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp]),
             "rqrcp_read_status": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
             "rqrcp_lowrank_workspace_size": (_sz, [_i64, _i64, _i64]),
             "rqrcp_lowrank": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
@@ -90,13 +93,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_double)]),
             "rqrcp_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+            "rqrcp_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double), _vp]),
             "rqrcp_sketch_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp]),
             "rqrcp_lowrank_f32": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
                                                  _sz, _vp]),
             "rqrcp_backward_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
             "rqrcp_reorth_workspace_size": (_sz, [_i64, _i64, _i64]),
             "rqrcp_batched_workspace_size": (_sz, [_i64, _i64, _i64, _i64]),
-            "rqrcp_factor_batched": (ctypes.c_int, [_i64, _vp, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _sz, _vp]),
+            "rqrcp_factor_batched": (ctypes.c_int, [_i64, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _i64, _vp, _sz,
+                                                    _vp]),
             "rqrcp_lowrank_reorth": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64,
                                                     ctypes.c_double, _vp, _vp, _sz, _vp]),
             "rqrcp_backward": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64,
@@ -166,6 +172,14 @@ def rqrcp_lowrank_workspace_size(m, n, k) -> int:
     return int(load().rqrcp_lowrank_workspace_size(m, n, k))
 
 
+def rqrcp_generate_omega_host(l, m, seed):
+    """The library's host draw of Omega (l x m, row-major float64 numpy array)."""
+    import numpy as np
+    out = np.empty((l, m), dtype=np.float64)
+    _check(load().rqrcp_generate_omega_host(l, m, seed, out.ctypes.data, m), "rqrcp_generate_omega_host")
+    return out
+
+
 def rqrcp_generate_omega(l, m, seed, Omega, stream=None) -> int:
     fn = load().rqrcp_generate_omega if Omega.element_size() == 8 else load().rqrcp_generate_omega_f32
     return fn(l, m, seed, _ptr(Omega), _ld_rowmajor(Omega), _stream(stream))
@@ -186,35 +200,40 @@ def rqrcp_sketch_noalloc(A, Omega, B, stream=None) -> int:
                                        _ld(B), _stream(stream))
 
 
-def rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
+def rqrcp_factor(A, k, b, p, seed, jpvt, tau, work, stream=None, rank_out=None) -> int:
+    """rank_out: optional int64 CUDA tensor of one element that receives the rank."""
     m, n = A.shape
-    return load().rqrcp_factor(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(work),
-                               work.numel(), _stream(stream))
+    return load().rqrcp_factor(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(rank_out),
+                               _ptr(work), work.numel(), _stream(stream))
 
 
-def rqrcp_factor_with_omega(A, k, b, p, Omega, jpvt, tau, work, stream=None) -> int:
+def rqrcp_factor_with_omega(A, k, b, p, Omega, jpvt, tau, work, stream=None, rank_out=None) -> int:
     m, n = A.shape
     return load().rqrcp_factor_with_omega(m, n, _ptr(A), _ld(A), k, b, p, _ptr(Omega), _ld_rowmajor(Omega),
-                                          _ptr(jpvt), _ptr(tau), _ptr(work), work.numel(), _stream(stream))
+                                          _ptr(jpvt), _ptr(tau), _ptr(rank_out), _ptr(work), work.numel(),
+                                          _stream(stream))
 
 
-def rqrcp_factor_ex(A, k, b, p, seed, Omega, formula, jpvt, tau, work, stream=None) -> int:
+def rqrcp_factor_ex(A, k, b, p, seed, Omega, formula, jpvt, tau, work, stream=None, rank_out=None) -> int:
     m, n = A.shape
     om, ldo = (None, 0) if Omega is None else (_ptr(Omega), _ld_rowmajor(Omega))
     return load().rqrcp_factor_ex(m, n, _ptr(A), _ld(A), k, b, p, seed, om, ldo, formula, _ptr(jpvt), _ptr(tau),
-                                  _ptr(work), work.numel(), _stream(stream))
+                                  _ptr(rank_out), _ptr(work), work.numel(), _stream(stream))
 
 
-def rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream=None) -> int:
+def rqrcp_factor_mixed(A, k, b, p, seed, jpvt, tau, work, stream=None, rank_out=None) -> int:
     m, n = A.shape
-    return load().rqrcp_factor_mixed(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(work),
-                                     work.numel(), _stream(stream))
+    return load().rqrcp_factor_mixed(m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt), _ptr(tau), _ptr(rank_out),
+                                     _ptr(work), work.numel(), _stream(stream))
 
 
-def rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream=None) -> int:
+def rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream=None, Omega=None,
+                          rank_out=None) -> int:
+    """Omega: optional row-major float32 CUDA tensor ((b+p) x m) replacing the seeded sketch."""
     m, n = A.shape
-    return load().rqrcp_factor_mixed_ex(m, n, _ptr(A), _ld(A), k, b, p, seed, sketch, _ptr(jpvt), _ptr(tau),
-                                        _ptr(work), work.numel(), _stream(stream))
+    om, ldo = (None, 0) if Omega is None else (_ptr(Omega), _ld_rowmajor(Omega))
+    return load().rqrcp_factor_mixed_ex(m, n, _ptr(A), _ld(A), k, b, p, seed, om, ldo, sketch, _ptr(jpvt),
+                                        _ptr(tau), _ptr(rank_out), _ptr(work), work.numel(), _stream(stream))
 
 
 def rqrcp_read_status(work, stream=None) -> tuple[int, int]:
@@ -246,10 +265,11 @@ def rqrcp_batched_workspace_size(m_max, n_max, b_max, p) -> int:
     return int(load().rqrcp_batched_workspace_size(m_max, n_max, b_max, p))
 
 
-def rqrcp_factor_batched(count, descs, order, m_max, n_max, b_max, p, seed, work, stream=None) -> int:
-    """descs: device uint8 tensor of count x 72-byte descriptors; order: device int32 tensor."""
-    return load().rqrcp_factor_batched(count, _ptr(descs), _ptr(order), m_max, n_max, b_max, p, seed, _ptr(work),
-                                       work.numel(), _stream(stream))
+def rqrcp_factor_batched(count, descs, order, m_max, n_max, b_max, p, Omega, work, stream=None) -> int:
+    """descs: device uint8 tensor of count x 72-byte descriptors; order: device int32 tensor; Omega: row-major
+    float32 CUDA tensor of at least (b_max + p) x m_max."""
+    return load().rqrcp_factor_batched(count, _ptr(descs), _ptr(order), m_max, n_max, b_max, p, _ptr(Omega),
+                                       _ld_rowmajor(Omega), _ptr(work), work.numel(), _stream(stream))
 
 
 BATCH_DESC_BYTES = 72
@@ -298,10 +318,13 @@ class Batch:
             raise ValueError("invalid batch limits")
         self.work = workspace(need, dev)
         self.flops = float(sum(cost))
+        # the shared sketching matrix, drawn once from the seed (host draw, one copy)
+        self.omega = torch.empty((self.b_max + p, self.m_max), dtype=torch.float32, device=dev)
+        _check(rqrcp_generate_omega(self.b_max + p, self.m_max, seed, self.omega), "rqrcp_generate_omega_f32")
 
     def run(self, stream=None) -> int:
         return rqrcp_factor_batched(len(self.mats), self.descs, self.order, self.m_max, self.n_max, self.b_max,
-                                    self.p, self.seed, self.work, stream)
+                                    self.p, self.omega, self.work, stream)
 
 
 def rqrcp_backward_workspace_size(m, n, k, precision=RQRCP_PREC_FP64) -> int:
@@ -315,6 +338,17 @@ def rqrcp_backward(A, jpvt, Q1, R, dQ1, dR, dA, work, stream=None) -> int:
     fn = load().rqrcp_backward if A.element_size() == 8 else load().rqrcp_backward_f32
     return fn(m, n, k, _ptr(A), _ld(A), _ptr(jpvt), _ptr(Q1), _ld(Q1), _ptr(R), _ld(R), _ptr(dQ1), _ld(dQ1),
               _ptr(dR), _ld(dR), _ptr(dA), _ld(dA), _ptr(work), work.numel(), _stream(stream))
+
+
+RQRCP_PROBE_DFMA, RQRCP_PROBE_FFMA, RQRCP_PROBE_TC_TF32, RQRCP_PROBE_TC_BF16 = 0, 1, 2, 3
+
+
+def rqrcp_peak_probe(kind, stream=None) -> tuple[float, float]:
+    """(TFLOP/s, ms) of one timed launch of the probe `kind` (RQRCP_PROBE_*)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().rqrcp_peak_probe(int(kind), ctypes.byref(tf), ctypes.byref(ms), _stream(stream)),
+           "rqrcp_peak_probe")
+    return float(tf.value), float(ms.value)
 
 
 def rqrcp_profile_begin() -> int:
@@ -358,7 +392,7 @@ def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETC
     if work is None or work.numel() < need:
         work = workspace(need, dev)
     if mixed:
-        code = rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream)
+        code = rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream, Omega=omega)
     elif formula != RQRCP_UPDATE_EQ4:
         code = rqrcp_factor_ex(A, k, b, p, seed, omega, formula, jpvt, tau, work, stream)
     elif omega is None:
@@ -422,10 +456,11 @@ def srqr(A, l: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, g: float
 
 
 def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,
-                 overwrite: bool = False, sketch: str = "bf16") -> Factorization:
+                 overwrite: bool = False, sketch: str = "bf16", omega=None) -> Factorization:
     """Randomized QRCP of a float32 CUDA matrix (mixed form, FP64 reflectors).
 
     sketch: "bf16" (operands rounded to BF16, FP32 accumulation) or "fp32" (FP32-level sketch).
+    omega: optional row-major (b+p) x m float32 CUDA tensor replacing the seeded sketch.
     """
     import torch
     if A.dtype != torch.float32:
@@ -435,7 +470,7 @@ def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, 
     Acm = colmajor(A)
     if not overwrite:
         Acm = Acm.t().clone().t()
-    return _run_factor(Acm, k, b, p, seed, None, True, work, stream,
+    return _run_factor(Acm, k, b, p, seed, omega, True, work, stream,
                        RQRCP_SKETCH_BF16 if sketch == "bf16" else RQRCP_SKETCH_FP32)
 
 

@@ -18,7 +18,10 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librqrcp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-                     "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+                     "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+                     # host code: no fused multiply-add contraction (the host Omega draw must give
+                     # the same bits as any other IEEE-double evaluation of the same formula)
+                     "-Xcompiler", "-ffp-contract=off"]
 
 
 def _nvcc() -> str:

@@ -1289,17 +1289,16 @@ __attribute__((visibility("default"))) size_t rqrcp_batched_workspace_size(int64
 {
     if (m_max < 1 || n_max < 1 || b_max < 1 || b_max > 64 || p < 0 || b_max + p > 1024) return 0;
     const int blocks = dev_info().sms;
-    // Omega (l_max x m_max) + counter + per-block scratch
-    size_t off = ((size_t)(b_max + p) * m_max * sizeof(float) + 255) & ~(size_t)255;
-    off += 256;
+    // counter + per-block scratch
+    size_t off = 256;
     off += (size_t)blocks * batched_ws_per_block(n_max, (int)b_max, (int)p);
     return off;
 }
 
 __attribute__((visibility("default"))) int rqrcp_factor_batched(int64_t count, const void* descs, const int* order,
                                                                 int64_t m_max, int64_t n_max, int64_t b_max,
-                                                                int64_t p, uint64_t seed, void* work,
-                                                                size_t work_bytes, void* stream)
+                                                                int64_t p, const float* Omega, int64_t ldo,
+                                                                void* work, size_t work_bytes, void* stream)
 {
     if (count < 0) return -1;
     if (count > 0 && descs == nullptr) return -2;
@@ -1308,6 +1307,8 @@ __attribute__((visibility("default"))) int rqrcp_factor_batched(int64_t count, c
     if (n_max < 1) return -5;
     if (b_max < 1 || b_max > 64) return -6;
     if (p < 0 || b_max + p > 1024) return -7;
+    if (Omega == nullptr) return -8;
+    if (ldo < m_max) return -9;
     const size_t need = rqrcp_batched_workspace_size(m_max, n_max, b_max, p);
     if (work == nullptr || (reinterpret_cast<uintptr_t>(work) & 255) != 0 || work_bytes < need)
         return RQRCP_ERR_WORKSPACE;
@@ -1316,29 +1317,24 @@ __attribute__((visibility("default"))) int rqrcp_factor_batched(int64_t count, c
     if (count == 0) return RQRCP_OK;
     cudaStream_t s = (cudaStream_t)stream;
     char* w = static_cast<char*>(work);
-    float* Om = reinterpret_cast<float*>(w);
-    size_t off = ((size_t)(b_max + p) * m_max * sizeof(float) + 255) & ~(size_t)255;
-    int* counter = reinterpret_cast<int*>(w + off);
-    off += 256;
-    char* scratch = w + off;
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    int* counter = reinterpret_cast<int*>(w);
+    char* scratch = w + 256;
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (allow_max_dynamic_smem(batched_kernel) != cudaSuccess) {
             cudaGetLastError();
             return RQRCP_ERR_CUDA;
         }
-        attr_set = true;
+        attr_set.set();
     }
     const bool prof = prof_on();
     if (prof) prof_begin(K_BATCHED, s);
-    if (launch_omega<float>(b_max + p, m_max, seed, Om, m_max, s) != cudaSuccess) return RQRCP_ERR_CUDA;
     if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
         return RQRCP_ERR_CUDA;
     }
-    batched_kernel<<<dev_info().sms, BT, smem, s>>>(static_cast<const BatchDesc*>(descs), order, (int)count, Om,
-                                                     (long long)m_max, (int)p, (long long)m_max, (long long)n_max,
+    batched_kernel<<<dev_info().sms, BT, smem, s>>>(static_cast<const BatchDesc*>(descs), order, (int)count, Omega,
+                                                     (long long)ldo, (int)p, (long long)m_max, (long long)n_max,
                                                      (int)b_max, scratch, batched_ws_per_block(n_max, (int)b_max, (int)p),
                                                      counter, tensor_cores_enabled() ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return RQRCP_ERR_CUDA;

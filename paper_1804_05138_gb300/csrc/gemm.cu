@@ -202,7 +202,10 @@ template <typename T>
 __global__ void sketch_reduce_kernel(const double* __restrict__ P, int nsplit, int64_t l, int64_t n,
                                      T* __restrict__ B, int64_t ldb, Status* st)
 {
-    if (status_error(st)) return;
+    // a non-finite sketch column flagged by another block of this launch does not stop the others:
+    // every column of B is written (NaN/Inf where the input is not finite)
+    const int e0 = status_error(st);
+    if (e0 != 0 && e0 != RQRCP_ERR_NONFINITE) return;
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (j >= n) return;
@@ -439,11 +442,10 @@ cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, con
                          double* Tm, const Status* st, cudaStream_t s)
 {
     const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)bb);
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = allow_max_dynamic_smem(tform_kernel)) return e;
-        attr_set = true;
+        attr_set.set();
     }
     tform_kernel<<<bb, 128, smem, s>>>(P, nsplit, ncols, bb, tau, Tm, st);
     return cudaGetLastError();
@@ -455,18 +457,16 @@ cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t 
     if (nc <= 0) return cudaSuccess;
     const int threads = 256, nw = threads / 32;
     const size_t smem = sizeof(double) * ((size_t)bb * (bb | 1) + (size_t)nw * bb);
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = allow_max_dynamic_smem(reduce_y_kernel)) return e;
-        attr_set = true;
+        attr_set.set();
     }
     if (fp32c && bb <= 64) {
-        static bool set_c_dev[kMaxDevices] = {};
-        bool& set_c = set_c_dev[current_device()];
-        if (!set_c) {
+        static DevFlag set_c;
+        if (!set_c.done()) {
             if (cudaError_t e = allow_max_dynamic_smem(reduce_y_f32c_kernel)) return e;
-            set_c = true;
+            set_c.set();
         }
         const size_t smem_c = sizeof(float) * 4 * 64 * 65;
         reduce_y_f32c_kernel<<<(unsigned)((nc + 63) / 64), 256, smem_c, s>>>(P, nsplit, ncols, c0, bb, Tm, transT, Y,

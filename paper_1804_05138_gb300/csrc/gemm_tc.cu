@@ -404,16 +404,18 @@ size_t tc_smem_bytes(int Nb, int nst, bool bf)
 template <int NBMAX, bool BF>
 size_t tc_dyn_limit()
 {
-    static size_t lim = 0;
-    if (lim == 0) {
+    static std::atomic<size_t> lim{0};
+    size_t v = lim.load(std::memory_order_relaxed);
+    if (v == 0) {
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, (const void*)gemm_tn_tc_kernel<NBMAX, BF>) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        lim = (size_t)dev_info().max_smem_optin - fa.sharedSizeBytes;
+        v = (size_t)dev_info().max_smem_optin - fa.sharedSizeBytes;
+        lim.store(v, std::memory_order_relaxed);
     }
-    return lim;
+    return v;
 }
 
 size_t tc_dyn_limit_for(int Nb, bool bf)
@@ -540,16 +542,15 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
     a.tmem_cols = cols;
     const size_t smem = tc_smem_bytes(Nb, nst, bf);
     dim3 grid((unsigned)((N + TC_NA - 1) / TC_NA), (unsigned)((K + kchunk - 1) / kchunk));
-    auto run = [&](auto kern, bool& attr_set) -> cudaError_t {
-        if (!attr_set) {
+    auto run = [&](auto kern, DevFlag& attr_set) -> cudaError_t {
+        if (!attr_set.done()) {
             if (cudaError_t e = allow_max_dynamic_smem(kern)) return e;
-            attr_set = true;
+            attr_set.set();
         }
         kern<<<grid, TC_THREADS, smem, s>>>(mapC, mapX, a, P, const_cast<Status*>(st));
         return cudaGetLastError();
     };
-    static bool set_dev[kMaxDevices][6] = {};
-    bool(&set)[6] = set_dev[current_device()];
+    static DevFlag set[6];
     if (bf) {
         if (Nb <= 32) return run(gemm_tn_tc_kernel<32, true>, set[3]);
         if (Nb <= 64) return run(gemm_tn_tc_kernel<64, true>, set[4]);

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/rqrcp.h"
 
 namespace rq {
@@ -126,15 +128,33 @@ const DevInfo& dev_info();
 // Kernel attributes such as the dynamic shared-memory limit are set per device: the flags that
 // record "already set" are kept per device, indexed by the calling thread's current device.
 constexpr int kMaxDevices = 64;
+// The calling thread's current device, or -1 if it cannot be read or has no slot (>= kMaxDevices).
 inline int current_device()
 {
     int d = 0;
     if (cudaGetDevice(&d) != cudaSuccess) {
         cudaGetLastError();
-        d = 0;
+        return -1;
     }
-    return (d < 0 || d >= kMaxDevices) ? 0 : d;
+    return (d < 0 || d >= kMaxDevices) ? -1 : d;
 }
+
+// "Done once on this device" flag, safe when several host threads call the library.  A device
+// without a slot (current_device() < 0) gets no flag: the guarded work is redone on every call
+// there instead of borrowing another device's flag.
+struct DevFlag {
+    std::atomic<bool> f[kMaxDevices];
+    bool done() const
+    {
+        const int d = current_device();
+        return d >= 0 && f[d].load(std::memory_order_acquire);
+    }
+    void set()
+    {
+        const int d = current_device();
+        if (d >= 0) f[d].store(true, std::memory_order_release);
+    }
+};
 
 // Allow a kernel the largest dynamic shared memory the device grants next to the kernel's
 // own static shared memory.  Returns the runtime error, if any.
@@ -148,7 +168,11 @@ cudaError_t allow_max_dynamic_smem(K kernel)
     return cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
 }
 
-// Omega (l x m row-major) from Philox4x64-10 + Box-Muller.
+// Omega (l x m row-major, ldo >= m) from Philox4x64-10 + Box-Muller, drawn on the host (threads
+// over Philox blocks; the bits do not depend on the thread count).
+void host_omega(int64_t l, int64_t m, uint64_t seed, double* out, int64_t ldo);
+// The same draw copied into device memory Om (row-major, ldo) on stream s, FP64 or rounded to FP32.
+// The copy is from pageable host memory: it cannot be captured in a CUDA graph.
 template <typename T>
 cudaError_t launch_omega(int64_t l, int64_t m, uint64_t seed, T* Om, int64_t ldo, cudaStream_t s);
 

@@ -342,12 +342,11 @@ cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, dou
 {
     constexpr bool f32 = sizeof(T) == 4;
     const void* kern = f32 ? (const void*)panel_f32_kernel : (const void*)panel_kernel<double>;
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = f32 ? allow_max_dynamic_smem(panel_f32_kernel) : allow_max_dynamic_smem(panel_kernel<double>))
             return e;
-        attr_set = true;
+        attr_set.set();
     }
     const int64_t G = panel_blocks(m1, bb, (int)sizeof(T));
     const int64_t rpb = (m1 + G - 1) / G;

@@ -342,11 +342,10 @@ template <typename T>
 cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int32_t* jpvt,
                          int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s)
 {
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = allow_max_dynamic_smem(pivot_kernel<T>)) return e;
-        attr_set = true;
+        attr_set.set();
     }
     const int64_t nprime = n - i;
     // every SM takes a slice of at least 8 columns; tpc threads share a column

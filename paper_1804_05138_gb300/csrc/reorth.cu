@@ -295,14 +295,13 @@ __attribute__((visibility("default"))) int rqrcp_lowrank_reorth(int64_t m, int64
     }
     // Cholesky (cooperative), gated by the flag
     {
-        static bool attr_set_dev[kMaxDevices] = {};
-        bool& attr_set = attr_set_dev[current_device()];
-        if (!attr_set) {
+        static DevFlag attr_set;
+        if (!attr_set.done()) {
             if (allow_max_dynamic_smem(chol_kernel) != cudaSuccess) {
                 cudaGetLastError();
                 return RQRCP_ERR_CUDA;
             }
-            attr_set = true;
+            attr_set.set();
         }
         const size_t smem = sizeof(double) * (size_t)k;
         int per_sm = 0;

@@ -14,22 +14,44 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 
 namespace rq {
 
+namespace {
+void query_dev_info(int d, DevInfo& out)
+{
+    out.sms = 0;
+    out.max_smem_optin = 0;
+    cudaDeviceGetAttribute(&out.sms, cudaDevAttrMultiProcessorCount, d);
+    cudaDeviceGetAttribute(&out.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+    cudaGetLastError();
+}
+}  // namespace
+
+// Attributes of the calling thread's current device, queried once per device (under a lock, so
+// that concurrent first calls are safe); a device without a slot is queried on every call.
 const DevInfo& dev_info()
 {
-    static DevInfo cache[64];
-    static bool have[64] = {};
-    int d = 0;
-    cudaGetDevice(&d);
-    if (d < 0 || d >= 64) d = 0;
-    if (!have[d]) {
-        cudaDeviceGetAttribute(&cache[d].sms, cudaDevAttrMultiProcessorCount, d);
-        cudaDeviceGetAttribute(&cache[d].max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
-        have[d] = true;
+    static DevInfo cache[kMaxDevices];
+    static std::atomic<bool> have[kMaxDevices];
+    static std::mutex mu;
+    const int d = current_device();
+    if (d < 0) {
+        thread_local DevInfo uncached;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+        query_dev_info(dev, uncached);
+        return uncached;
+    }
+    if (!have[d].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!have[d].load(std::memory_order_relaxed)) {
+            query_dev_info(d, cache[d]);
+            have[d].store(true, std::memory_order_release);
+        }
     }
     return cache[d];
 }
@@ -157,8 +179,9 @@ int check_work(void* work, size_t work_bytes, size_t need)
 
 template <typename T>
 int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, int64_t p, uint64_t seed,
-                const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, void* work, size_t work_bytes,
-                cudaStream_t s, int sketch_bf16 = 0, int formula = RQRCP_UPDATE_EQ4, bool final_b = false)
+                const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, int64_t* rank_out, void* work,
+                size_t work_bytes, cudaStream_t s, int sketch_bf16 = 0, int formula = RQRCP_UPDATE_EQ4,
+                bool final_b = false)
 {
     const int64_t l = b + p;
     const Layout L = make_layout(m, n, b, p, sizeof(T));
@@ -291,6 +314,8 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
                       launch_bfinish<T>(B, Bc, (int)l, i + bb, nt, P, ns2, st, s));
         }
     }
+    if (rank_out != nullptr)
+        RQ_CHECK(cudaMemcpyAsync(rank_out, &st->rank, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     return RQRCP_OK;
 }
 
@@ -491,36 +516,38 @@ __attribute__((visibility("default"))) int rqrcp_sketch(int64_t m, int64_t n, co
 
 __attribute__((visibility("default"))) int rqrcp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
                                                         int64_t b, int64_t p, uint64_t seed, int32_t* jpvt,
-                                                        double* tau, void* work, size_t work_bytes, void* stream)
+                                                        double* tau, int64_t* rank_out, void* work,
+                                                        size_t work_bytes, void* stream)
 {
     if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e;
-    return factor_impl<double>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
+    return factor_impl<double>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, rank_out, work, work_bytes,
                                (cudaStream_t)stream);
 }
 
 __attribute__((visibility("default"))) int rqrcp_factor_with_omega(int64_t m, int64_t n, double* A, int64_t lda,
                                                                    int64_t k, int64_t b, int64_t p,
                                                                    const double* Omega, int64_t ldo, int32_t* jpvt,
-                                                                   double* tau, void* work, size_t work_bytes,
-                                                                   void* stream)
+                                                                   double* tau, int64_t* rank_out, void* work,
+                                                                   size_t work_bytes, void* stream)
 {
     if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 1 : e;
     if (Omega == nullptr) return -8;
     if (ldo < m) return -9;
-    return factor_impl<double>(m, n, A, lda, k, b, p, 0, Omega, ldo, jpvt, tau, work, work_bytes,
+    return factor_impl<double>(m, n, A, lda, k, b, p, 0, Omega, ldo, jpvt, tau, rank_out, work, work_bytes,
                                (cudaStream_t)stream);
 }
 
 __attribute__((visibility("default"))) int rqrcp_factor_ex(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
                                                            int64_t b, int64_t p, uint64_t seed, const double* Omega,
                                                            int64_t ldo, int formula, int32_t* jpvt, double* tau,
-                                                           void* work, size_t work_bytes, void* stream)
+                                                           int64_t* rank_out, void* work, size_t work_bytes,
+                                                           void* stream)
 {
     if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 3 : e;
     if (Omega != nullptr && ldo < m) return -10;
     if (formula != RQRCP_UPDATE_EQ4 && formula != RQRCP_UPDATE_EQ5) return -11;
-    return factor_impl<double>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, work,
-                               work_bytes, (cudaStream_t)stream, 0, formula);
+    return factor_impl<double>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, rank_out,
+                               work, work_bytes, (cudaStream_t)stream, 0, formula);
 }
 
 __attribute__((visibility("default"))) size_t rqrcp_srqr_workspace_size(int64_t m, int64_t n, int64_t l, int64_t b,
@@ -555,8 +582,8 @@ __attribute__((visibility("default"))) int rqrcp_srqr(int64_t m, int64_t n, doub
     char* w = static_cast<char*>(work);
     double* tau = reinterpret_cast<double*>(w + S.tau);
     // Alg. 3 "Compute Q, R, Pi with Algorithm 2" (to rank l; B updated after the last block too)
-    if (int e = factor_impl<double>(m, n, A, lda, l, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, w,
-                                    S.f.total, s, 0, RQRCP_UPDATE_EQ4, true))
+    if (int e = factor_impl<double>(m, n, A, lda, l, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau,
+                                    nullptr, w, S.f.total, s, 0, RQRCP_UPDATE_EQ4, true))
         return e;
     Status* st = reinterpret_cast<Status*>(w + S.f.status);
     const double* B = reinterpret_cast<const double*>(w + S.f.B);
@@ -598,23 +625,25 @@ __attribute__((visibility("default"))) int rqrcp_srqr(int64_t m, int64_t n, doub
 
 __attribute__((visibility("default"))) int rqrcp_factor_mixed(int64_t m, int64_t n, float* A, int64_t lda, int64_t k,
                                                               int64_t b, int64_t p, uint64_t seed, int32_t* jpvt,
-                                                              double* tau, void* work, size_t work_bytes,
-                                                              void* stream)
+                                                              double* tau, int64_t* rank_out, void* work,
+                                                              size_t work_bytes, void* stream)
 {
     if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e;
-    return factor_impl<float>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
+    return factor_impl<float>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, rank_out, work, work_bytes,
                               (cudaStream_t)stream, 1);
 }
 
 __attribute__((visibility("default"))) int rqrcp_factor_mixed_ex(int64_t m, int64_t n, float* A, int64_t lda,
                                                                  int64_t k, int64_t b, int64_t p, uint64_t seed,
-                                                                 int sketch, int32_t* jpvt, double* tau, void* work,
-                                                                 size_t work_bytes, void* stream)
+                                                                 const float* Omega, int64_t ldo, int sketch,
+                                                                 int32_t* jpvt, double* tau, int64_t* rank_out,
+                                                                 void* work, size_t work_bytes, void* stream)
 {
-    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 1 : e;
-    if (sketch != RQRCP_SKETCH_BF16 && sketch != RQRCP_SKETCH_FP32) return -9;
-    return factor_impl<float>(m, n, A, lda, k, b, p, seed, nullptr, 0, jpvt, tau, work, work_bytes,
-                              (cudaStream_t)stream, sketch == RQRCP_SKETCH_BF16 ? 1 : 0);
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 3 : e;
+    if (Omega != nullptr && ldo < m) return -10;
+    if (sketch != RQRCP_SKETCH_BF16 && sketch != RQRCP_SKETCH_FP32) return -11;
+    return factor_impl<float>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, rank_out,
+                              work, work_bytes, (cudaStream_t)stream, sketch == RQRCP_SKETCH_BF16 ? 1 : 0);
 }
 
 __attribute__((visibility("default"))) int rqrcp_read_status(const void* work, int64_t* rank, void* stream)

@@ -365,11 +365,10 @@ size_t srqr_solve_smem(int64_t l) { return sizeof(double) * (size_t)(l + 1); }
 cudaError_t launch_srqr_g2(const double* A, int64_t lda, int64_t l, int64_t d, uint64_t seed, double* Og, double* X,
                            double* info, const Status* st, cudaStream_t s)
 {
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = allow_max_dynamic_smem(srqr_solve_kernel)) return e;
-        attr_set = true;
+        attr_set.set();
     }
     if (cudaError_t e = launch_omega<double>(d, l + 1, seed, Og, l + 1, s)) return e;
     srqr_solve_kernel<<<(unsigned)d, kT, srqr_solve_smem(l), s>>>(A, lda, l, Og, X, st);

@@ -202,12 +202,11 @@ template <typename T>
 cudaError_t launch_bupdate(T* B, int64_t ldb, const T* A, int64_t lda, int64_t i, int bb, int64_t n,
                            double* What, const Status* st, cudaStream_t s)
 {
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = allow_max_dynamic_smem(bsolve_kernel<T>)) return e;
         if (cudaError_t e = allow_max_dynamic_smem(bapply_kernel<T>)) return e;
-        attr_set = true;
+        attr_set.set();
     }
     const size_t smem = sizeof(double) * ((size_t)bb * bb + (size_t)bb);
     bsolve_kernel<T><<<bb, 128, smem, s>>>(B, ldb, A, lda, i, bb, What, st);

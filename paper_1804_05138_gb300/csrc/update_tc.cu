@@ -327,11 +327,10 @@ cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long 
     a.maskV = maskV;
     a.ntiles = ntiles;
     a.total = ((mr + UT_BM - 1) / UT_BM) * ntiles;
-    static bool attr_set_dev[kMaxDevices] = {};
-    bool& attr_set = attr_set_dev[current_device()];
-    if (!attr_set) {
+    static DevFlag attr_set;
+    if (!attr_set.done()) {
         if (cudaError_t e = allow_max_dynamic_smem(update_tc_kernel)) return e;
-        attr_set = true;
+        attr_set.set();
     }
     long long grid = dev_info().sms;
     if (grid > a.total) grid = a.total;

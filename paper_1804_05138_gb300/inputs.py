@@ -35,8 +35,12 @@ def haar(n_rows: int, n_cols: int, seed: int) -> np.ndarray:
     return Q * d
 
 
-def spectrum_matrix(m: int, n: int, sigma: np.ndarray, seed_u: int = 1, seed_v: int = 2) -> np.ndarray:
+def spectrum_matrix(m: int, n: int, sigma: np.ndarray, seed_u: int = 1, seed_v: int = 2,
+                    rank_cap: int | None = None) -> np.ndarray:
+    """U diag(sigma) V^T with Haar U, V; ``rank_cap`` keeps only the leading triplets."""
     r = min(m, n, len(sigma))
+    if rank_cap is not None:
+        r = min(r, rank_cap)
     U = haar(m, r, seed_u)
     V = haar(n, r, seed_v)
     return np.asfortranarray((U * np.asarray(sigma[:r])) @ V.T)

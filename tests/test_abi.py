@@ -52,34 +52,42 @@ def test_workspace_size_rejects_bad_arguments(lib):
 def test_factor_argument_codes(lib):
     fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation happens first
     f = lib.rqrcp_factor
-    #            m    n    A     lda  k   b   p  seed jpvt  tau   work  bytes stream
-    assert f(0, 5, fake, 1, 1, 1, 0, 0, fake, fake, None, 0, None) == -1
-    assert f(5, 0, fake, 5, 1, 1, 0, 0, fake, fake, None, 0, None) == -2
-    assert f(5, 5, None, 5, 1, 1, 0, 0, fake, fake, None, 0, None) == -3
-    assert f(5, 5, fake, 4, 1, 1, 0, 0, fake, fake, None, 0, None) == -4
-    assert f(5, 5, fake, 5, 6, 1, 0, 0, fake, fake, None, 0, None) == -5
-    assert f(5, 5, fake, 5, 0, 1, 0, 0, fake, fake, None, 0, None) == -5
-    assert f(5, 5, fake, 5, 2, 0, 0, 0, fake, fake, None, 0, None) == -6
-    assert f(5, 5, fake, 5, 2, 1, -1, 0, fake, fake, None, 0, None) == -7
-    assert f(5, 5, fake, 5, 2, 1, 0, 0, None, fake, None, 0, None) == -9
-    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, None, None, 0, None) == -10
-    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, None, 0, None) == 4      # no workspace
+    #            m    n    A     lda  k   b   p  seed jpvt  tau  rank  work  bytes stream
+    assert f(0, 5, fake, 1, 1, 1, 0, 0, fake, fake, None, None, 0, None) == -1
+    assert f(5, 0, fake, 5, 1, 1, 0, 0, fake, fake, None, None, 0, None) == -2
+    assert f(5, 5, None, 5, 1, 1, 0, 0, fake, fake, None, None, 0, None) == -3
+    assert f(5, 5, fake, 4, 1, 1, 0, 0, fake, fake, None, None, 0, None) == -4
+    assert f(5, 5, fake, 5, 6, 1, 0, 0, fake, fake, None, None, 0, None) == -5
+    assert f(5, 5, fake, 5, 0, 1, 0, 0, fake, fake, None, None, 0, None) == -5
+    assert f(5, 5, fake, 5, 2, 0, 0, 0, fake, fake, None, None, 0, None) == -6
+    assert f(5, 5, fake, 5, 2, 1, -1, 0, fake, fake, None, None, 0, None) == -7
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, None, fake, None, None, 0, None) == -9
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, None, None, None, 0, None) == -10
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, None, None, 0, None) == 4      # no workspace
+    assert f(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, fake, None, 0, None) == 4      # rank_out given
     g = lib.rqrcp_factor_with_omega
-    assert g(5, 5, fake, 5, 2, 1, 0, None, 5, fake, fake, None, 0, None) == -8
-    assert g(5, 5, fake, 5, 2, 1, 0, fake, 4, fake, fake, None, 0, None) == -9
-    assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, None, fake, None, 0, None) == -10
-    assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, fake, None, None, 0, None) == -11
+    assert g(5, 5, fake, 5, 2, 1, 0, None, 5, fake, fake, None, None, 0, None) == -8
+    assert g(5, 5, fake, 5, 2, 1, 0, fake, 4, fake, fake, None, None, 0, None) == -9
+    assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, None, fake, None, None, 0, None) == -10
+    assert g(5, 5, fake, 5, 2, 1, 0, fake, 5, fake, None, None, None, 0, None) == -11
     h = lib.rqrcp_factor_mixed
-    assert h(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, fake, 16, None) == 4     # too small
+    assert h(5, 5, fake, 5, 2, 1, 0, 0, fake, fake, None, fake, 16, None) == 4     # too small
+    hx = lib.rqrcp_factor_mixed_ex
+    #             m  n  A    lda k  b  p  seed Omega ldo sketch jpvt tau rank work bytes stream
+    assert hx(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 0, fake, fake, None, None, 0, None) == -10
+    assert hx(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 2, fake, fake, None, None, 0, None) == -11
+    assert hx(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, None, fake, None, None, 0, None) == -12
+    assert hx(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 1, fake, None, None, None, 0, None) == -13
+    assert hx(5, 5, fake, 5, 2, 1, 0, 0, fake, 5, 1, fake, fake, None, None, 0, None) == 4  # no workspace
     x = lib.rqrcp_factor_ex
-    #            m  n  A    lda k  b  p  seed Omega ldo formula jpvt tau work bytes stream
-    assert x(5, 5, None, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, 0, None) == -3
-    assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 5, fake, fake, None, 0, None) == -10
-    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 3, fake, fake, None, 0, None) == -11
-    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, None, fake, None, 0, None) == -12
-    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, None, None, 0, None) == -13
-    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, 0, None) == 4  # no workspace
-    assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 5, 4, fake, fake, None, 0, None) == 4
+    #            m  n  A    lda k  b  p  seed Omega ldo formula jpvt tau rank work bytes stream
+    assert x(5, 5, None, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, None, 0, None) == -3
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 5, fake, fake, None, None, 0, None) == -10
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 3, fake, fake, None, None, 0, None) == -11
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, None, fake, None, None, 0, None) == -12
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, None, None, None, 0, None) == -13
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, None, 0, None) == 4  # no workspace
+    assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 5, 4, fake, fake, None, None, 0, None) == 4
     sr = lib.rqrcp_srqr
     #      m  n  A    lda l  b  p  seed Omega ldo g    d  seed_g swaps jpvt info work bytes stream
     assert sr(1, 5, fake, 5, 1, 1, 0, 0, None, 0, 5.0, 8, 0, 10, fake, None, None, 0, None) == -1
@@ -99,6 +107,15 @@ def test_other_entry_point_argument_codes(lib):
     fake = ctypes.c_void_p(0x1000)
     assert lib.rqrcp_generate_omega(0, 5, 0, fake, 5, None) == -1
     assert lib.rqrcp_generate_omega(2, 5, 0, fake, 4, None) == -5
+    assert lib.rqrcp_generate_omega_host(0, 5, 0, fake, 5) == -1
+    assert lib.rqrcp_generate_omega_host(2, 0, 0, fake, 5) == -2
+    assert lib.rqrcp_generate_omega_host(2, 5, 0, None, 5) == -4
+    assert lib.rqrcp_generate_omega_host(2, 5, 0, fake, 4) == -5
+    bt = lib.rqrcp_factor_batched
+    #        count descs order m_max n_max b_max p Omega ldo work bytes stream
+    assert bt(1, fake, fake, 8, 8, 4, 2, None, 8, None, 0, None) == -8
+    assert bt(1, fake, fake, 8, 8, 4, 2, fake, 7, None, 0, None) == -9
+    assert bt(1, fake, fake, 8, 8, 4, 2, fake, 8, None, 0, None) == 4   # no workspace
     assert lib.rqrcp_sketch(5, 5, fake, 5, fake, 3, 4, fake, 3, None, 0, None) == -7
     assert lib.rqrcp_sketch(5, 5, fake, 5, fake, 3, 5, fake, 2, None, 0, None) == -9
     assert lib.rqrcp_lowrank(5, 5, 6, fake, 5, fake, fake, fake, 5, fake, 5, None, 0, None) == -3
@@ -119,3 +136,27 @@ def test_binding_rejects_bad_python_arguments(lib):
         binding.srqr(A64.float(), 2, 2, 1)
     with pytest.raises(ValueError):
         binding.srqr(A64, 6, 2, 1)          # l must be below min(m, n): workspace size 0
+
+
+def test_host_omega_matches_oracle_bit_for_bit(lib, orc):
+    """The library's host draw of Omega (its own Philox4x64-10 + Box-Muller) equals the oracle's
+    independent implementation of the same published definition, bit for bit, at sizes that use
+    one host thread and several; the seeded factorizations use exactly this draw."""
+    import numpy as np
+    from paper_1804_05138_gb300 import binding
+    for (l, m, seed) in [(1, 1, 0), (3, 7, 5), (40, 1000, 0), (80, 32768, 0), (72, 8193, 2**63 + 11)]:
+        got = binding.rqrcp_generate_omega_host(l, m, seed)
+        want = orc.omega(l, m, seed)
+        assert got.shape == want.shape
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (l, m, seed)
+
+
+def test_host_omega_respects_leading_dimension(lib):
+    import numpy as np
+    from paper_1804_05138_gb300 import binding
+    l, m, ldo = 5, 9, 13
+    buf = np.full((l, ldo), 7.0)
+    assert lib.rqrcp_generate_omega_host(l, m, 3, buf.ctypes.data, ldo) == 0
+    dense = binding.rqrcp_generate_omega_host(l, m, 3)
+    assert np.array_equal(buf[:, :m], dense)
+    assert np.all(buf[:, m:] == 7.0)

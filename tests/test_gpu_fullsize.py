@@ -2,13 +2,14 @@
 
 Sampled outputs the oracle computes one by one (a column of A*Pi = Q R(:, j) costs O(m k)
 with the oracle's Q x), plus properties that hold at any size:
-  * 8192 x 8192 FP64 full factorization: the first block's pivots against the oracle run on
-    the same matrix and seed; sampled columns of A Pi - Q R at rounding level;
+  * 8192 x 8192 FP64 full factorization: the pivots of the first four blocks against the oracle
+    run on the same matrix and seed; sampled columns of A Pi - Q R at rounding level;
   * exactly rank-500 8192 x 8192: the guard stops at 500 and R(500:, 500:) vanishes;
   * 32768 x 16384 FP32 mixed, k = 512: sampled backward error <= 1e-6 and
-    sigma_513 <= ||R22||_2 <= 3.5 sigma_513 (power iteration on the device).  The FP64 oracle
-    itself reaches 2.93-3.14 on this spectrum (exp(-i/200), p = 16) at 4096 x 2048 and
-    8192 x 4096 over three seeds, so the 2 sigma_{k+1} target is not met by the method.
+    sigma_513 <= ||R22||_2 <= 1.2 times the plain FP64 form's ||R22||_2 on the same matrix (power
+    iteration on the device), itself <= 3.5 sigma_513.  The FP64 oracle reaches 2.93-3.14 on this
+    spectrum (exp(-i/200), p = 16) at 4096 x 2048 and 8192 x 4096 over three seeds, so the
+    2 sigma_{k+1} target is not met by the method itself.
 """
 import numpy as np
 import pytest
@@ -55,16 +56,19 @@ def test_fp64_8192_full(gpu, orc):
     assert f.rank == k
     jp = f.jpvt.cpu().numpy()
     assert sorted(jp.tolist()) == list(range(n))
-    # first block against the oracle on the same matrix and seed
-    ref = orc.rqrcp_seeded(A0h, b, b, p, seed=0)
+    # the first four blocks against the oracle on the same matrix and seed (the seeded sketch is
+    # the oracle's draw bit for bit): the whole pivot sequence up to the first near-tie
+    kb = 4 * b
+    ref = orc.rqrcp_seeded(A0h, kb, b, p, seed=0)
     sep = ref.gaps >= 1e-10
-    upto = b if sep.all() else int(np.argmin(sep))
-    assert upto >= 8
+    upto = kb if sep.all() else int(np.argmin(sep))
+    assert upto >= b
     assert np.array_equal(jp[:upto], ref.jpvt[:upto])
     # sampled columns of A Pi - Q R
     Af = f.A.cpu().numpy()
     tau = f.tau.cpu().numpy()
-    cols = [0, 1, 63, 64, 1000, 4095, 4096, 7000, 8190, 8191]
+    cols = sorted(set([0, 1, 63, 64, 127, 128, 255, 256, 1000, 2047, 2048, 4095, 4096, 5555, 7000, 8127, 8128,
+                       8190, 8191] + list(np.random.default_rng(3).integers(0, n, 13))))
     res = _sampled_residuals(orc, [A0h[:, jp[j]] for j in cols], Af, [_r_column(Af[:, j], j, k) for j in cols],
                              tau, k)
     assert res.max() <= 1e-13, res
@@ -98,15 +102,24 @@ def test_mixed_32768x16384_k512(gpu, orc):
     Rc = [_r_column(f.A[:, j].double().cpu().numpy(), j, k) for j in cols]
     res = _sampled_residuals(orc, A0h_cols, Vh, Rc, tau, k)
     assert res.max() <= 1e-6, res
-    # ||R22||_2 by power iteration on the device
-    R22 = f.A[k:, k:]
+    # ||R22||_2 by power iteration on the device, beside the plain FP64 form's on the same matrix
+    # (the FP64 form is the oracle's computation to rounding: same pivots up to near-ties)
+    ratio = _r22_norm(f.A[k:, k:]) / sig[k]
+    A64 = A0.double()
+    del f
+    f64 = gpu.factor(A64, k, b, p, seed=0, overwrite=True)
+    ratio64 = _r22_norm(f64.A[k:, k:]) / sig[k]
+    assert 1.0 - 1e-3 <= ratio64 <= 3.5, ratio64
+    assert 1.0 - 1e-3 <= ratio <= 1.2 * ratio64, (ratio, ratio64)
+
+
+def _r22_norm(R22, iters=60):
+    import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
-    x = torch.randn(n - k, device="cuda", generator=g)
-    for _ in range(60):
+    x = torch.randn(R22.shape[1], device="cuda", generator=g, dtype=R22.dtype)
+    for _ in range(iters):
         y = R22 @ x
         x = R22.t() @ y
         x = x / torch.linalg.norm(x)
-    nrm22 = torch.linalg.norm(R22 @ x).item()
-    ratio = nrm22 / sig[k]
-    assert 1.0 - 1e-3 <= ratio <= 3.5, ratio
+    return torch.linalg.norm(R22 @ x).item()

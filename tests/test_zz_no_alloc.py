@@ -59,3 +59,31 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(gpu):
     # n * l * 8 bytes for one split must fit the 8 MiB array (minus its 256-byte status block)
     assert lib.rqrcp_sketch_noalloc(10, 16384, fake, 10, fake, 64, 10, fake, 64, None) == gpu.RQRCP_ERR_UNSUPPORTED
     assert lib.rqrcp_sketch_noalloc(0, 5, fake, 1, fake, 2, 1, fake, 2, None) == -1
+
+
+def test_noalloc_with_a_non_finite_entry_writes_every_column(gpu):
+    """An Inf in one column of A makes that column of B non-finite; every other column is still
+    written and equals the workspace sketch (status is not reported by this entry point)."""
+    import torch
+    m, n, l = 600, 500, 24
+    A0 = inputs.gaussian(m, n, seed=3)
+    A0[17, 123] = np.inf
+    Om = inputs.gaussian_sketch(l, m, seed=4)
+    A = gpu.colmajor(torch.from_numpy(A0).cuda())
+    Omg = torch.from_numpy(Om).cuda()
+    B_ref = torch.empty((n, l), dtype=torch.float64, device="cuda").t()
+    work = gpu.workspace(gpu.rqrcp_workspace_size(m, n, 1, l, 0), "cuda")
+    assert gpu.rqrcp_sketch(A, Omg, B_ref, work) == 0
+    code, _ = gpu.rqrcp_read_status(work)
+    assert code == gpu.RQRCP_ERR_NONFINITE
+    B_na = torch.full((n, l), 12345.0, dtype=torch.float64, device="cuda").t()
+    assert gpu.rqrcp_sketch_noalloc(A, Omg, B_na) == 0
+    torch.cuda.synchronize()
+    got, ref = B_na.cpu().numpy(), B_ref.cpu().numpy()
+    assert not np.isfinite(got[:, 123]).any()
+    keep = np.ones(n, dtype=bool)
+    keep[123] = False
+    assert np.all(np.isfinite(got[:, keep]))
+    # the two entry points may split the sum over m differently: each is within m*u*(|Omega||A|)
+    bound = 2.0 * m * U * (np.abs(Om) @ np.abs(np.where(np.isfinite(A0), A0, 0.0)))
+    assert np.all(np.abs(got[:, keep] - ref[:, keep]) <= bound[:, keep])
