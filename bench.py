@@ -824,11 +824,13 @@ def run_batched(args, w, rank, world, local_rank):
     all_shapes = inputs.batched_shapes(args.count, seed=0)
     table = autotune.load_or_tune(all_shapes, p=p)
     all_bs = [autotune.choose(table, m, n, k) for (m, n, k) in all_shapes]
+    all_tiles = [autotune.choose_tiles(table, m, n, k) for (m, n, k) in all_shapes]
     # N ranks: each factors its LPT share of the one batch (independent matrices, no exchange)
     costs = [binding.batch_cost(m, n, k, b, p) for (m, n, k), b in zip(all_shapes, all_bs)]
     mine = sorted(partition.lpt_partition(costs, world)[rank]) if world > 1 else list(range(len(all_shapes)))
     shapes = [all_shapes[i] for i in mine]
     bs = [all_bs[i] for i in mine]
+    tiles = [all_tiles[i] for i in mine]
     # the matrices are column-major views (ld = m) into one device pool, so the end-to-end run
     # moves the batch with one copy each way and the restore between steps is one copy
     pool = torch.empty(sum(m * n for m, n, _ in shapes), dtype=torch.float32, device=dev)
@@ -842,7 +844,7 @@ def run_batched(args, w, rank, world, local_rank):
         mats.append(view)
         off += m * n
     pristine_pool = pool.clone()
-    batch = binding.Batch(mats, [k for _, _, k in shapes], bs, p=p, seed=0)
+    batch = binding.Batch(mats, [k for _, _, k in shapes], bs, p=p, seed=0, tiles=tiles)
     F = batch.flops
     stream = torch.cuda.Stream(device=dev)
 
@@ -917,6 +919,9 @@ def run_batched(args, w, rank, world, local_rank):
                    w["desc"].replace("512 FP32 matrices", f"the first {args.count} of the 512 FP32 matrices"),
                    "count": len(all_shapes), "p": p, "b_histogram":
                    {str(b): int(c) for b, c in zip(*np.unique(bs, return_counts=True))},
+                   "tiles_histogram": {str(t): int(c) for t, c in zip(*np.unique(tiles, return_counts=True))},
+                   "autotune_table": {key: {"b": v["b"], "tiles": v["tiles"]} if isinstance(v, dict) else v
+                                      for key, v in sorted(table.items())},
                    "counted_gflop_per_step": round(F / 1e9, 3), "bytes_per_step": nbytes,
                    "l2": "inputs larger than L2: 2.6 GB of matrices restored before every step",
                    "parallelism": f"batch partitioned over {world} ranks (LPT on counted flops)" if world > 1

@@ -282,7 +282,12 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  * launch (the paper factors one matrix at a time; batching is the GPU form of running Alg. 2 on
  * many small problems).  `descs` is a device array of `count` descriptors, 72 bytes each, with
  * this layout (8-byte aligned, in order): float* A, int32_t* jpvt (n), double* tau (k),
- * int64_t* rank (1), int64_t m, int64_t n, int64_t k, int64_t lda, int32_t b, int32_t pad.
+ * int64_t* rank (1), int64_t m, int64_t n, int64_t k, int64_t lda, int32_t b, int32_t tiles.
+ * `tiles` picks the tile shapes of the matrix's contractions (0: the library's default rules; an OR
+ * of RQRCP_TILES_*, e.g. from the autotuner): the trailing update C -= V Y on 64 x 128 FP32 SIMT
+ * tiles (UPDATE_SIMT) or 128 x 64 tcgen05 tiles (UPDATE_TC; default: tcgen05 for b > 16), the
+ * sketch on SIMT tiles instead of tcgen05 (SKETCH_SIMT), the Gram V^T [V C] on 64 x 128 tiles
+ * instead of the smallest of 16 x 512 / 32 x 256 / 64 x 128 that holds b rows (GRAM_RT64).
  * Every matrix needs 1 <= k <= min(m,n) <= max(m_max, n_max), m <= m_max, n <= n_max,
  * 1 <= b <= b_max <= 64 (b is per matrix, e.g. from the autotuner).  `order` (device, count
  * ints) is the processing order (largest first balances best); one block per SM takes the next
@@ -301,6 +306,10 @@ int rqrcp_sketch_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, con
  * b_max^2 doubles + ~3 KB) must fit, else RQRCP_ERR_UNSUPPORTED (m_max <= ~5600 with
  * n_max = 2048, b_max = 64).
  */
+#define RQRCP_TILES_UPDATE_SIMT 1
+#define RQRCP_TILES_UPDATE_TC 2
+#define RQRCP_TILES_SKETCH_SIMT 4
+#define RQRCP_TILES_GRAM_RT64 8
 size_t rqrcp_batched_workspace_size(int64_t m_max, int64_t n_max, int64_t b_max, int64_t p);
 int rqrcp_factor_batched(int64_t count, const void* descs, const int* order, int64_t m_max, int64_t n_max,
                          int64_t b_max, int64_t p, const float* Omega, int64_t ldo, void* work, size_t work_bytes,

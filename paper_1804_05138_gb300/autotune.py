@@ -1,9 +1,14 @@
-"""Autotuner for the batched factorization: block size b per shape bucket.
+"""Autotuner for the batched factorization: block size b and contraction tile shapes per shape bucket.
 
-Shapes are grouped into coarse buckets of (m, n, k).  For each bucket, up to a few
-representative matrices are factored with every candidate b (b <= k) through the batched
-entry point itself, timed with CUDA events (best of `reps`), and the fastest b is kept.
-Tables are cached per GPU name and oversampling in paper_1804_05138_gb300/_build/.
+Shapes are grouped into coarse buckets of (m, n, k).  For each bucket, up to a few representative
+matrices are factored through the batched entry point itself, timed with CUDA events (best of
+`reps`):
+  1. every candidate b (b <= k) with the default tile rules;
+  2. with the fastest b, every tile variant (RQRCP_TILES_*): the trailing update on 64 x 128 SIMT
+     tiles or on 128 x 64 tcgen05 tiles, the sketch on SIMT tiles, the Gram V^T [V C] on 64 x 128
+     tiles; a variant replaces the default only if it is faster by more than `margin`.
+Tables map a bucket to {"b": b, "tiles": t}; they are cached per GPU name, precision (the batched
+form is FP32) and oversampling p in paper_1804_05138_gb300/_build/.
 """
 from __future__ import annotations
 
@@ -13,7 +18,10 @@ import os
 from . import binding
 
 CANDIDATES = (16, 32, 64)
+TILE_VARIANTS = (binding.RQRCP_TILES_UPDATE_SIMT, binding.RQRCP_TILES_UPDATE_TC, binding.RQRCP_TILES_SKETCH_SIMT,
+                 binding.RQRCP_TILES_GRAM_RT64)
 _HERE = os.path.dirname(os.path.abspath(__file__))
+TABLE_VERSION = 2
 
 
 def bucket(m: int, n: int, k: int) -> str:
@@ -24,14 +32,29 @@ def default_b(m: int, n: int, k: int) -> int:
     return max(1, min(64, k))
 
 
+def _entry(table: dict, m: int, n: int, k: int) -> dict:
+    e = table.get(bucket(m, n, k))
+    if e is None:
+        return {"b": default_b(m, n, k), "tiles": 0}
+    if isinstance(e, dict):
+        return {"b": int(e.get("b", default_b(m, n, k))), "tiles": int(e.get("tiles", 0))}
+    return {"b": int(e), "tiles": 0}
+
+
 def choose(table: dict, m: int, n: int, k: int) -> int:
-    return max(1, min(int(table.get(bucket(m, n, k), default_b(m, n, k))), k, 64))
+    """Block size b for an m x n matrix with target rank k."""
+    return max(1, min(_entry(table, m, n, k)["b"], k, 64))
 
 
-def _time_batch(mats, ks, bs, p, reps):
+def choose_tiles(table: dict, m: int, n: int, k: int) -> int:
+    """Tile-shape choice (an OR of RQRCP_TILES_*) for an m x n matrix with target rank k."""
+    return _entry(table, m, n, k)["tiles"]
+
+
+def _time_batch(mats, ks, bs, p, reps, tiles=None):
     import torch
     orig = [A.clone() for A in mats]
-    batch = binding.Batch(mats, ks, bs, p=p)
+    batch = binding.Batch(mats, ks, bs, p=p, tiles=tiles)
     best = float("inf")
     for _ in range(reps + 1):
         for A, O in zip(batch.mats, orig):
@@ -47,8 +70,10 @@ def _time_batch(mats, ks, bs, p, reps):
     return best
 
 
-def tune(shapes, p: int = 8, candidates=CANDIDATES, reps: int = 2, per_bucket: int = 3, seed: int = 0):
-    """Return {bucket: b} for the given (m, n, k) shapes, measured on the current GPU."""
+def tune(shapes, p: int = 8, candidates=CANDIDATES, reps: int = 2, per_bucket: int = 3, seed: int = 0,
+         variants=TILE_VARIANTS, margin: float = 0.02):
+    """Return {bucket: {"b": b, "tiles": t, "ms": {...}}} for the given (m, n, k) shapes, measured on the
+    current GPU."""
     import numpy as np
     import torch
     groups = {}
@@ -63,14 +88,23 @@ def tune(shapes, p: int = 8, candidates=CANDIDATES, reps: int = 2, per_bucket: i
         mats = [torch.randn((n, m), device="cuda").t() for (m, n, _) in pick]
         ks = [k for _, _, k in pick]
         timings = {b: _time_batch(mats, ks, [b] * len(ks), p, reps) for b in cands}
-        table[key] = int(min(timings, key=timings.get))
+        b_best = int(min(timings, key=timings.get))
+        t_best, ms_best = 0, timings[b_best]
+        tile_ms = {"0": round(ms_best, 4)}
+        for t in variants:
+            ms = _time_batch(mats, ks, [b_best] * len(ks), p, reps, tiles=[t] * len(ks))
+            tile_ms[str(t)] = round(ms, 4)
+            if ms < ms_best * (1.0 - margin):
+                t_best, ms_best = t, ms
+        table[key] = {"b": b_best, "tiles": t_best, "ms_b": {str(b): round(v, 4) for b, v in timings.items()},
+                      "ms_tiles": tile_ms}
     return table
 
 
 def cache_path(p: int) -> str:
     import torch
     name = torch.cuda.get_device_name().replace(" ", "_")
-    return os.path.join(_HERE, "_build", f"autotune_batched_{name}_p{p}.json")
+    return os.path.join(_HERE, "_build", f"autotune_batched_v{TABLE_VERSION}_{name}_fp32_p{p}.json")
 
 
 def load_or_tune(shapes, p: int = 8) -> dict:

@@ -275,15 +275,19 @@ def rqrcp_factor_batched(count, descs, order, m_max, n_max, b_max, p, Omega, wor
 BATCH_DESC_BYTES = 72
 
 
-def batch_descriptors(mats, jpvts, taus, ranks, ks, bs):
+RQRCP_TILES_UPDATE_SIMT, RQRCP_TILES_UPDATE_TC, RQRCP_TILES_SKETCH_SIMT, RQRCP_TILES_GRAM_RT64 = 1, 2, 4, 8
+
+
+def batch_descriptors(mats, jpvts, taus, ranks, ks, bs, tiles=None):
     """Pack the 72-byte descriptors (layout of include/rqrcp.h) into a host uint8 array."""
     import numpy as np
     dt = np.dtype([("A", "<u8"), ("jpvt", "<u8"), ("tau", "<u8"), ("rank", "<u8"), ("m", "<i8"), ("n", "<i8"),
-                   ("k", "<i8"), ("lda", "<i8"), ("b", "<i4"), ("pad", "<i4")])
+                   ("k", "<i8"), ("lda", "<i8"), ("b", "<i4"), ("tiles", "<i4")])
     assert dt.itemsize == BATCH_DESC_BYTES
+    tiles = [0] * len(mats) if tiles is None else list(tiles)
     rec = np.zeros(len(mats), dtype=dt)
-    for i, (A, jp, tu, rk, k, b) in enumerate(zip(mats, jpvts, taus, ranks, ks, bs)):
-        rec[i] = (A.data_ptr(), jp.data_ptr(), tu.data_ptr(), rk.data_ptr(), A.shape[0], A.shape[1], k, _ld(A), b, 0)
+    for i, (A, jp, tu, rk, k, b, t) in enumerate(zip(mats, jpvts, taus, ranks, ks, bs, tiles)):
+        rec[i] = (A.data_ptr(), jp.data_ptr(), tu.data_ptr(), rk.data_ptr(), A.shape[0], A.shape[1], k, _ld(A), b, t)
     return rec.view(np.uint8)
 
 
@@ -296,17 +300,18 @@ def batch_cost(m, n, k, b, p):
 class Batch:
     """Prepared batched call: descriptors, order and workspace on the device; `run()` enqueues it."""
 
-    def __init__(self, mats, ks, bs, p=8, seed=0):
+    def __init__(self, mats, ks, bs, p=8, seed=0, tiles=None):
         import numpy as np
         import torch
         self.mats = [colmajor(A) for A in mats]
         dev = self.mats[0].device
         self.ks, self.bs, self.p, self.seed = list(ks), list(bs), p, seed
+        self.tiles = [0] * len(self.mats) if tiles is None else [int(t) for t in tiles]
         self.jpvts = [torch.empty(A.shape[1], dtype=torch.int32, device=dev) for A in self.mats]
         self.taus = [torch.empty(k, dtype=torch.float64, device=dev) for k in self.ks]
         self.ranks = torch.zeros(len(self.mats), dtype=torch.int64, device=dev)
         rank_views = [self.ranks[i:i + 1] for i in range(len(self.mats))]
-        host = batch_descriptors(self.mats, self.jpvts, self.taus, rank_views, self.ks, self.bs)
+        host = batch_descriptors(self.mats, self.jpvts, self.taus, rank_views, self.ks, self.bs, self.tiles)
         self.descs = torch.from_numpy(host.copy()).to(dev)
         cost = [batch_cost(A.shape[0], A.shape[1], k, b, p) for A, k, b in zip(self.mats, self.ks, self.bs)]
         self.order = torch.from_numpy(np.argsort(-np.asarray(cost), kind="stable").astype(np.int32)).to(dev)

@@ -27,7 +27,7 @@ struct BatchDesc {
     double* tau;
     long long* rank;  // pivots before the rank guard fired; -1 when the sketch is not finite
     long long m, n, k, lda;
-    int b, pad;
+    int b, tiles;  // tiles: RQRCP_TILES_* choices of the contractions' tile shapes (0 = default rules)
 };
 
 namespace {
@@ -449,7 +449,7 @@ __device__ bool blk_gemm_tn_tc(const float* X, long long ldx, int maskX, const f
 // keeps more bytes in flight per block than the tensor-core stages (raw, hi and lo parts) allow.
 __device__ bool blk_gemm_tn(const float* X, long long ldx, int maskX, const float* C, long long ldc, long long maskC,
                             long long M, long long N, long long K, float* Out, long long ldo, int out_rowmajor,
-                            const Smem& sm, int tensor)
+                            const Smem& sm, int tensor, int rt_min = 0)
 {
     if (M <= 0 || N <= 0) return true;
     if (tensor && M <= kTcNbMax) {
@@ -462,8 +462,10 @@ __device__ bool blk_gemm_tn(const float* X, long long ldx, int maskX, const floa
         default: return blk_gemm_tn_tc<24>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
         }
     }
-    if (M <= 16) blk_gemm_tn_rt<16>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
-    else if (M <= 32) blk_gemm_tn_rt<32>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+    // the smallest RT >= M (and >= rt_min): RT x (8192 / RT) output tiles
+    const long long Mr = M > rt_min ? M : rt_min;
+    if (Mr <= 16) blk_gemm_tn_rt<16>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
+    else if (Mr <= 32) blk_gemm_tn_rt<32>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
     else blk_gemm_tn_rt<64>(X, ldx, maskX, C, ldc, maskC, M, N, K, Out, ldo, out_rowmajor, sm);
     return true;
 }
@@ -1034,7 +1036,8 @@ __device__ bool factor_one(const BatchDesc& d, const float* Om, long long ldo, i
     float* A = d.A;
     for (long long c = tid; c < n; c += BT) d.jpvt[c] = (int32_t)c;
     // sketch B = Omega(0:l, 0:m) A, row-major l x n
-    if (!blk_gemm_tn(Om, ldo, 0, A, lda, 0, l, n, m, Bw, n, 1, sm, sm.tc)) {
+    const int tiles = d.tiles;
+    if (!blk_gemm_tn(Om, ldo, 0, A, lda, 0, l, n, m, Bw, n, 1, sm, (tiles & RQRCP_TILES_SKETCH_SIMT) ? 0 : sm.tc)) {
         if (tid == 0) *d.rank = -2;
         __syncthreads();
         return false;
@@ -1093,7 +1096,8 @@ __device__ bool factor_one(const BatchDesc& d, const float* Om, long long ldo, i
         const long long nt = n - i - bb;
         if (nt <= 0) continue;
         // W = V^T [V C] (bb x (n-i), column-major ld bb), T, Y = T^T W(:, bb:), C -= V Y
-        if (!blk_gemm_tn(Vp, lda, 1, Vp, lda, bb, bb, n - i, m1, Ww, bb, 0, sm, 0)) {
+        if (!blk_gemm_tn(Vp, lda, 1, Vp, lda, bb, bb, n - i, m1, Ww, bb, 0, sm, 0,
+                         (tiles & RQRCP_TILES_GRAM_RT64) ? 64 : 0)) {
             if (tid == 0) *d.rank = -2;
             __syncthreads();
             return false;
@@ -1132,9 +1136,12 @@ __device__ bool factor_one(const BatchDesc& d, const float* Om, long long ldo, i
             }
             __syncthreads();
         }
-        // tensor cores for bb > 16 (measured 9 % faster at bb = 32); at bb = 16 the SIMT form, whose
-        // shared-memory ring keeps more of C in flight, measured 13 % faster
-        if (sm.tc && bb > 16) {
+        // default: tensor cores for bb > 16 (measured 9 % faster at bb = 32); at bb = 16 the SIMT
+        // form, whose shared-memory ring keeps more of C in flight, measured 13 % faster; the
+        // descriptor's tile choice overrides the rule either way
+        const bool update_tc = sm.tc && ((tiles & RQRCP_TILES_UPDATE_TC) ? true
+                                         : (tiles & RQRCP_TILES_UPDATE_SIMT) ? false : bb > 16);
+        if (update_tc) {
             const bool u_ok = bb <= 32 ? blk_gemm_update_tc<1>(Vp + (long long)bb * lda, lda, Vp, lda, 1, Yw, bb, m1, nt, bb, sm)
                                        : blk_gemm_update_tc<2>(Vp + (long long)bb * lda, lda, Vp, lda, 1, Yw, bb, m1, nt, bb, sm);
             if (!u_ok) {

@@ -31,34 +31,39 @@ __device__ __forceinline__ T vmask(T stored, int64_t q, int64_t r)
     return q > r ? stored : (q == r ? T(1) : T(0));
 }
 
-template <typename T>
+// RA register rows per thread: the block's tile is TMX = 16 RA rows of the result by TN columns
+// (RA = 4 for the compact-WY Gram with bb <= 64; 3, 5 or 6 so that a sketch of l = b + p rows fits
+// one tile without computing rows beyond l).
+template <typename T, int RA>
 __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, int64_t ldx,
                                                      const T* __restrict__ C, int64_t ldc, int64_t M,
                                                      int64_t N, int64_t K, int64_t kchunk,
                                                      double* __restrict__ P, int maskX, int64_t maskC,
                                                      int bf16, const Status* st)
 {
+    constexpr int TMX = 16 * RA;
+    static_assert((TK * TMX) % NT == 0, "the X slice must split evenly over the block");
     if (status_error(st)) return;
-    __shared__ T Xs[TK][TM + 1];
+    __shared__ T Xs[TK][TMX + 1];
     __shared__ T Cs[TK][TN + 1];
     const int tid = threadIdx.x;
     const int tm = tid & 15, tn = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.x * TM;
+    const int64_t m0 = (int64_t)blockIdx.x * TMX;
     const int64_t n0 = (int64_t)blockIdx.y * TN;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
     const int64_t kend = min(K, kbeg + kchunk);
 
     // Two-level accumulation: a 64-deep inner sum in T, folded into an outer T sum.
-    T acc[4][4], outer[4][4];
+    T acc[RA][4], outer[RA][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = outer[a][b] = T(0);
 
     int inner = 0;
     for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
 #pragma unroll
-        for (int it = 0; it < (TK * TM) / NT; ++it) {
+        for (int it = 0; it < (TK * TMX) / NT; ++it) {
             const int e = tid + it * NT;
             const int kk = e & (TK - 1);
             const int mm = e / TK;
@@ -90,13 +95,13 @@ __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, in
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < TK; ++kk) {
-            T xa[4], cb[4];
+            T xa[RA], cb[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][tm + 16 * a];
+            for (int a = 0; a < RA; ++a) xa[a] = Xs[kk][tm + 16 * a];
 #pragma unroll
             for (int b = 0; b < 4; ++b) cb[b] = Cs[kk][tn + 16 * b];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < RA; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], cb[b], acc[a][b]);
         }
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, in
         if (++inner == 4) {
             inner = 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < RA; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     outer[a][b] += acc[a][b];
@@ -118,12 +123,16 @@ __global__ void __launch_bounds__(NT) gemm_tn_kernel(const T* __restrict__ X, in
         const int64_t c = n0 + tn + 16 * b;
         if (c >= N) continue;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < RA; ++a) {
             const int64_t r = m0 + tm + 16 * a;
             if (r < M) Pz[c * M + r] = (double)outer[a][b] + (double)acc[a][b];
         }
     }
 }
+
+// Register rows per thread of the SIMT contraction for an M-row result: one tile of 48, 64, 80 or
+// 96 rows when M fits, else 64-row tiles.
+inline int gemm_tn_ra(int64_t M) { return M <= 48 ? 3 : M <= 64 ? 4 : M <= 80 ? 5 : M <= 96 ? 6 : 4; }
 
 template <typename T>
 __global__ void __launch_bounds__(NT) gemm_update_kernel(T* __restrict__ C, int64_t ldc,
@@ -387,23 +396,41 @@ __global__ void __launch_bounds__(256) reduce_y_f32c_kernel(const double* __rest
 
 }  // namespace
 
-int gemm_tn_blocks_per_sm(int elem_bytes)
+template <typename T, int RA>
+int occupancy_of_gemm_tn()
 {
-    static int occ[2] = {0, 0};
-    const int idx = elem_bytes == 8 ? 0 : 1;
-    if (occ[idx] == 0) {
-        int v = 0;
-        const cudaError_t e = elem_bytes == 8
-                                  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_tn_kernel<double>, NT, 0)
-                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_tn_kernel<float>, NT, 0);
-        if (e != cudaSuccess || v < 1) {
+    static std::atomic<int> occ{0};
+    int v = occ.load(std::memory_order_relaxed);
+    if (v == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_tn_kernel<T, RA>, NT, 0) != cudaSuccess || v < 1) {
             cudaGetLastError();
             v = 1;
         }
-        occ[idx] = v;
+        occ.store(v, std::memory_order_relaxed);
     }
-    return occ[idx];
+    return v;
 }
+
+int gemm_tn_blocks_per_sm(int elem_bytes, int64_t M)
+{
+    const int ra = gemm_tn_ra(M);
+    if (elem_bytes == 8) {
+        switch (ra) {
+        case 3: return occupancy_of_gemm_tn<double, 3>();
+        case 5: return occupancy_of_gemm_tn<double, 5>();
+        case 6: return occupancy_of_gemm_tn<double, 6>();
+        default: return occupancy_of_gemm_tn<double, 4>();
+        }
+    }
+    switch (ra) {
+    case 3: return occupancy_of_gemm_tn<float, 3>();
+    case 5: return occupancy_of_gemm_tn<float, 5>();
+    case 6: return occupancy_of_gemm_tn<float, 6>();
+    default: return occupancy_of_gemm_tn<float, 4>();
+    }
+}
+
+int gemm_tn_tile_rows(int64_t M) { return 16 * gemm_tn_ra(M); }
 
 template <typename T>
 cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int64_t M, int64_t N,
@@ -411,8 +438,15 @@ cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int
                            const Status* st, cudaStream_t s, int bf16)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((N + TN - 1) / TN), (unsigned)((K + kchunk - 1) / kchunk));
-    gemm_tn_kernel<T><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, bf16, st);
+    const int ra = gemm_tn_ra(M);
+    const int64_t tmx = 16 * ra;
+    dim3 grid((unsigned)((M + tmx - 1) / tmx), (unsigned)((N + TN - 1) / TN), (unsigned)((K + kchunk - 1) / kchunk));
+    switch (ra) {
+    case 3: gemm_tn_kernel<T, 3><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, bf16, st); break;
+    case 5: gemm_tn_kernel<T, 5><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, bf16, st); break;
+    case 6: gemm_tn_kernel<T, 6><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, bf16, st); break;
+    default: gemm_tn_kernel<T, 4><<<grid, NT, 0, s>>>(X, ldx, C, ldc, M, N, K, kchunk, P, maskX, maskC, bf16, st);
+    }
     return cudaGetLastError();
 }
 

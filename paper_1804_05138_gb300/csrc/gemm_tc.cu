@@ -368,6 +368,275 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
+// 3xTF32 contraction for M <= 64 (the Gram [V^T V | V^T C] of the compact-WY update), with
+// 64-row chunks, three products and separate split and drain warps:
+//   * a chunk is two 32-row boxes of C (128 columns) and two 32-row boxes of [X_hi; X_lo];
+//   * per chunk the MMA warp issues eight A_hi x [X_hi; X_lo] MMAs (N = 2 Nb) and then eight
+//     A_lo x X_hi MMAs (N = Nb) into the chunk's accumulator: hi hi' lands alone in columns
+//     0..Nb-1 (eight accumulation steps per chunk), hi lo' + lo hi' in Nb..2Nb-1 (the lo lo'
+//     product, below 2^-22 of the product, is dropped);
+//   * warps 2..9 (two per tensor-memory lane quarter, 32 rows of the chunk each) split the landed
+//     C tile into TF32 hi/lo parts and store them to the chunk's A buffer in tensor memory;
+//   * warps 10..17 (two per lane quarter, Nb/2 output columns each) drain the accumulator of the
+//     previous chunk into FP32 registers while the next chunk is split and multiplied; every
+//     TC_FOLD3 chunks a compensated fold (TwoSum) into a second register set.
+// Tensor memory: D0, D1 (2 Nb columns each), then A0, A1 (128 columns each: 64 hi, 64 lo).
+constexpr int TC3_KC = 64;
+constexpr int TC3_MAXST = 6;
+constexpr int TC3_FOLD = 8;  // 64-row chunks summed in FP32 registers between compensated folds
+
+template <int NBMAX>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tn_tc3_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapX, TcArgs a,
+                       double* __restrict__ P, Status* st)
+{
+    constexpr int KC = TC3_KC;
+    constexpr int CQ = NBMAX / 2;  // output columns per drain thread (upper bound)
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = status_error(st);
+    __syncthreads();
+    if (s_skip) return;  // block-uniform: warp 1's tensor-memory allocation is warp-collective
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const int Nb = a.Nb;
+    const int boxC = TC_NA * 32 * 4;           // one 32-row box of C: 16 KB
+    const int boxX = 2 * Nb * 128;             // one 32-row box of [X_hi; X_lo]
+    const int tileC = 2 * boxC, tileX = 2 * boxX;
+    const int dcols = 2 * Nb;
+    const int stage_bytes = tileC + tileX;
+    const int nst = a.nst;
+    __shared__ __align__(8) uint64_t full[TC3_MAXST], empty[TC3_MAXST], aready[2], accfull[2], accempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&aready[b], 8);
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], 8);
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t tA = tmem + (uint32_t)(2 * dcols);
+    const long long n0 = (long long)blockIdx.x * TC_NA;
+    const long long kbeg = (long long)blockIdx.y * a.kchunk;
+    const long long kend = min(a.K, kbeg + a.kchunk);
+    const int nchunks = (int)((kend - kbeg + KC - 1) / KC);
+    auto stage_ptr = [&](int s) { return base + (size_t)s * stage_bytes; };
+    auto fail = [&]() {
+        s_fail = 1;
+        set_error(st, RQRCP_ERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kc = 0; kc < nchunks; ++kc) {
+                const int s = kc % nst;
+                if (kc >= nst && !mbar_wait(&empty[s], (unsigned)((kc - nst) / nst) & 1u, &s_fail)) {
+                    fail();
+                    break;
+                }
+                unsigned char* sp = stage_ptr(s);
+                const int k0 = (int)(kbeg + (long long)kc * KC);
+                mbar_expect_tx(&full[s], tileC + tileX);
+                tma_load_2d(sp, &mapC, k0, (int)n0, &full[s]);
+                tma_load_2d(sp + boxC, &mapC, k0 + 32, (int)n0, &full[s]);
+                tma_load_2d(sp + tileC, &mapX, k0, 0, &full[s]);
+                tma_load_2d(sp + tileC + boxX, &mapX, k0 + 32, 0, &full[s]);
+                issued = kc + 1;
+            }
+            // the copies still in flight land before the block leaves (bounded)
+            for (int kc = (issued > nst ? issued - nst : 0); kc < issued; ++kc)
+                mbar_wait(&full[kc % nst], (unsigned)(kc / nst) & 1u, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id_full = idesc_tf32(TC_NA, 2 * Nb), id_half = idesc_tf32(TC_NA, Nb);
+            int issued = 0;
+            for (int kc = 0; kc < nchunks; ++kc) {
+                const int s = kc % nst, b = kc & 1;
+                if (!mbar_wait(&aready[b], (unsigned)(kc >> 1) & 1u, &s_fail) ||
+                    (kc >= 2 && !mbar_wait(&accempty[b], (unsigned)((kc - 2) >> 1) & 1u, &s_fail))) {
+                    fail();
+                    break;
+                }
+                fence_after();
+                const unsigned char* xt = stage_ptr(s) + tileC;
+                const uint32_t td = tmem + (uint32_t)(b * dcols);
+                const uint32_t ta = tA + (uint32_t)(b * 2 * KC);
+                const uint64_t dx0 = umma_desc(xt), dx1 = umma_desc(xt + boxX);
+                // k-step j starts 32 bytes further into the 128-byte swizzle rows of its box: the
+                // descriptor's address field (bytes >> 4) advances by 2 without carry
+#pragma unroll
+                for (int j = 0; j < KC / 8; ++j)
+                    mma_tf32_ts(td, ta + 8 * j, (j < 4 ? dx0 : dx1) + 2 * (j & 3), id_full, j > 0 ? 1 : 0);
+                // the small lo hi' products join hi lo' in columns Nb..2Nb-1, so that the accumulator
+                // of the large hi hi' terms takes only the chunk's eight steps
+#pragma unroll
+                for (int j = 0; j < KC / 8; ++j)
+                    mma_tf32_ts(td + (uint32_t)Nb, ta + KC + 8 * j, (j < 4 ? dx0 : dx1) + 2 * (j & 3), id_half, 1);
+                mma_commit(&empty[s]);
+                mma_commit(&accfull[b]);
+                issued = kc + 1;
+            }
+            // every MMA chain completes before tensor memory is freed (bounded)
+            if (issued > 0) mbar_wait(&empty[(issued - 1) % nst], (unsigned)((issued - 1) / nst) & 1u, nullptr);
+        }
+    } else if (warp < 10) {
+        // split warps: lane quarter q, rows 32 h2 .. 32 h2 + 31 of each chunk (box h2)
+        const int q = warp & 3, h2 = (warp - 2) >> 2;
+        const int row = 32 * q + lane;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const long long c = n0 + row;
+        for (int kc = 0; kc < nchunks; ++kc) {
+            const int s = kc % nst, b = kc & 1;
+            // the landed stage, and A[b] free again: the MMAs of chunk kc - 2 have completed
+            bool ok = mbar_wait(&full[s], (unsigned)(kc / nst) & 1u, &s_fail);
+            if (ok && kc >= 2) ok = mbar_wait(&accfull[b], (unsigned)((kc - 2) >> 1) & 1u, &s_fail);
+            if (!__all_sync(0xffffffffu, ok)) {
+                fail();
+                break;
+            }
+            fence_after();
+            const unsigned char* box = stage_ptr(s) + h2 * boxC + row * 128;
+            const int k0 = (int)(kbeg + (long long)kc * KC) + 32 * h2;
+            const uint32_t ta = tA + lane_base + (uint32_t)(b * 2 * KC + 32 * h2);
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float v[16];
+#pragma unroll
+                for (int pc = 0; pc < 4; ++pc) {
+                    const int piece = (4 * half + pc) ^ (row & 7);
+                    const float4 f = *reinterpret_cast<const float4*>(box + piece * 16);
+                    v[4 * pc] = f.x;
+                    v[4 * pc + 1] = f.y;
+                    v[4 * pc + 2] = f.z;
+                    v[4 * pc + 3] = f.w;
+                }
+                if (c < a.maskC && k0 < a.maskC) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const long long qq = (long long)k0 + 16 * half + u;
+                        if (qq < c) v[u] = 0.f;
+                        else if (qq == c) v[u] = 1.f;
+                    }
+                }
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const float hv = tf32_rn(v[u]);
+                    hi[u] = __float_as_uint(hv);
+                    lo[u] = __float_as_uint(tf32_rn(v[u] - hv));
+                }
+                const uint32_t th = ta + (uint32_t)(16 * half), tl = th + (uint32_t)KC;
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16};" ::"r"(th),
+                    "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]),
+                    "r"(hi[8]), "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]),
+                    "r"(hi[15])
+                    : "memory");
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16};" ::"r"(tl),
+                    "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+                    "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]),
+                    "r"(lo[15])
+                    : "memory");
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aready[b]);
+        }
+    } else {
+        // drain warps: lane quarter q, output columns cb .. cb + qc - 1
+        const int q = warp & 3, hd = (warp - 10) >> 2;
+        const int qc = Nb >> 1;
+        const int cb = hd * qc;
+        const int row = 32 * q + lane;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const long long c = n0 + row;
+        float acc[CQ], sum[CQ];
+#pragma unroll
+        for (int j = 0; j < CQ; ++j) acc[j] = sum[j] = 0.f;
+        auto fold = [&]() {
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) {
+                const float t = sum[j] + acc[j];
+                const float bp = t - sum[j];
+                const float e = (sum[j] - (t - bp)) + (acc[j] - bp);
+                sum[j] = t;
+                acc[j] = e;
+            }
+        };
+        bool ok = true;
+        for (int kc = 0; kc < nchunks; ++kc) {
+            const int b = kc & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&accfull[b], (unsigned)(kc >> 1) & 1u, &s_fail))) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t tb = tmem + lane_base + (uint32_t)(b * dcols + cb);
+            // groups of 8 columns: the X_hi product at tb + j, the X_lo product at tb + Nb + j
+#pragma unroll
+            for (int g0 = 0; g0 < CQ; g0 += 8) {
+                if (g0 < qc) {
+                    uint32_t rh[8], rl[8];
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(rh[0]), "=r"(rh[1]), "=r"(rh[2]), "=r"(rh[3]), "=r"(rh[4]), "=r"(rh[5]),
+                                   "=r"(rh[6]), "=r"(rh[7])
+                                 : "r"(tb + (uint32_t)g0));
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(rl[0]), "=r"(rl[1]), "=r"(rl[2]), "=r"(rl[3]), "=r"(rl[4]), "=r"(rl[5]),
+                                   "=r"(rl[6]), "=r"(rl[7])
+                                 : "r"(tb + (uint32_t)(Nb + g0)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc[g0 + u] += __uint_as_float(rl[u]) + __uint_as_float(rh[u]);
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[b]);
+            if ((kc + 1) % TC3_FOLD == 0) fold();
+        }
+        if (!ok) {
+            fail();
+        } else if (nchunks > 0) {
+            fold();
+            double* Pz = P + (long long)blockIdx.y * a.N * a.M;
+            if (c < a.N) {
+#pragma unroll
+                for (int j = 0; j < CQ; ++j)
+                    if (j < qc && cb + j < a.M) Pz[c * a.M + cb + j] = (double)sum[j] + (double)acc[j];
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
 }  // namespace
 
 namespace {
@@ -424,6 +693,34 @@ size_t tc_dyn_limit_for(int Nb, bool bf)
     return Nb <= 32 ? tc_dyn_limit<32, false>() : Nb <= 64 ? tc_dyn_limit<64, false>() : tc_dyn_limit<96, false>();
 }
 
+// The 3xTF32 contraction for M <= 64 (gemm_tn_tc3_kernel): stage = two C boxes + two X boxes.
+size_t tc3_smem_bytes(int Nb, int nst) { return 1024 + (size_t)nst * ((size_t)TC_NA * TC3_KC * 4 + 4 * (size_t)Nb * 128); }
+
+template <int NBMAX>
+size_t tc3_dyn_limit()
+{
+    static std::atomic<size_t> lim{0};
+    size_t v = lim.load(std::memory_order_relaxed);
+    if (v == 0) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, (const void*)gemm_tn_tc3_kernel<NBMAX>) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        v = (size_t)dev_info().max_smem_optin - fa.sharedSizeBytes;
+        lim.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+int tc3_stages(int Nb)
+{
+    const size_t lim = Nb <= 16 ? tc3_dyn_limit<16>() : Nb <= 32 ? tc3_dyn_limit<32>() : tc3_dyn_limit<64>();
+    for (int nst = TC3_MAXST; nst >= 2; --nst)
+        if (tc3_smem_bytes(Nb, nst) <= lim) return nst;
+    return 0;
+}
+
 // Pipeline depth: TC_MAXST stages where they fit, else fewer (0: not even 2 fit).
 int tc_stages(int Nb, bool bf)
 {
@@ -463,7 +760,9 @@ bool tc_gemm_supported(long long M, long long ldc, const void* C, int bf16)
 {
     if (!(M >= 1 && M <= 96 && (ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tensor_map_encoder() != nullptr))
         return false;
-    return tc_stages((int)(((M + 15) / 16) * 16), bf16 != 0) >= 2;
+    const int Nb = (int)(((M + 15) / 16) * 16);
+    if (!bf16 && Nb <= 64) return tc3_stages(Nb) >= 2;
+    return tc_stages(Nb, bf16 != 0) >= 2;
 }
 
 size_t tc_xsplit_bytes(long long M, long long K)
@@ -473,10 +772,10 @@ size_t tc_xsplit_bytes(long long M, long long K)
 
 // Split-K chunk for the tensor-core kernel (one resident block per SM): the split count S <= 16
 // minimising waves x (rows per split + a pipeline fill of about three chunks), splits of at
-// least 256 rows; a multiple of the chunk height (32, or 64 for the BF16 form).
-long long tc_kchunk(long long N, long long K, int& nsplit, int bf16)
+// least 256 rows; a multiple of the chunk height (64 for the BF16 form and for M <= 64, else 32).
+long long tc_kchunk(long long N, long long K, int& nsplit, int bf16, long long M)
 {
-    const long long KC = bf16 ? 64 : TC_KC;
+    const long long KC = (bf16 || M <= 64) ? 64 : TC_KC;
     const long long ntiles = (N + TC_NA - 1) / TC_NA;
     const long long sms = dev_info().sms;
     long long smax = (K + 255) / 256;
@@ -528,6 +827,34 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
         }
     }
     if (!encode_map(&mapC, C, K, N, ldc, TC_NA)) return cudaErrorInvalidValue;
+    if (!bf && Nb <= 64) {
+        // 3xTF32, 64-row chunks, three products (gemm_tn_tc3_kernel)
+        const int nst3 = tc3_stages(Nb);
+        if (nst3 < 2 || kchunk % TC3_KC != 0) return cudaErrorInvalidValue;
+        TcArgs a3;
+        a3.M = (int)M;
+        a3.Nb = Nb;
+        a3.N = N;
+        a3.K = K;
+        a3.kchunk = kchunk;
+        a3.maskC = maskC;
+        a3.nst = nst3;
+        a3.tmem_cols = 512;  // D0, D1 (2 Nb each), A0, A1 (128 each)
+        const size_t smem3 = tc3_smem_bytes(Nb, nst3);
+        dim3 grid3((unsigned)((N + TC_NA - 1) / TC_NA), (unsigned)((K + kchunk - 1) / kchunk));
+        auto run3 = [&](auto kern, DevFlag& attr_set) -> cudaError_t {
+            if (!attr_set.done()) {
+                if (cudaError_t e = allow_max_dynamic_smem(kern)) return e;
+                attr_set.set();
+            }
+            kern<<<grid3, TC_THREADS, smem3, s>>>(mapC, mapX, a3, P, const_cast<Status*>(st));
+            return cudaGetLastError();
+        };
+        static DevFlag set3[3];
+        if (Nb <= 16) return run3(gemm_tn_tc3_kernel<16>, set3[0]);
+        if (Nb <= 32) return run3(gemm_tn_tc3_kernel<32>, set3[1]);
+        return run3(gemm_tn_tc3_kernel<64>, set3[2]);
+    }
     TcArgs a;
     a.M = (int)M;
     a.Nb = Nb;

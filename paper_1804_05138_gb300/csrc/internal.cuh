@@ -187,19 +187,21 @@ cudaError_t launch_gemm_tn(const T* X, int64_t ldx, const T* C, int64_t ldc, int
                            const Status* st, cudaStream_t s, int bf16 = 0);
 
 // Blocks of the SIMT split-K contraction (launch_gemm_tn) resident per SM for FP64 (8) or FP32 (4)
-// elements.
-int gemm_tn_blocks_per_sm(int elem_bytes);
+// elements and an M-row result, and the rows of one of its tiles (48, 64, 80 or 96: a result of up
+// to 96 rows is one tile, larger ones are 64-row tiles).
+int gemm_tn_blocks_per_sm(int elem_bytes, int64_t M);
+int gemm_tn_tile_rows(int64_t M);
 
 // Tensor-core (tcgen05 kind::tf32, 3xTF32) split-K contraction with the output of
 // launch_gemm_tn<float>: X(q, r) = X[r * ldx + q] (q < K, r < M; unit-lower reflector structure
 // for r < maskX), C(q, c) = C[c * ldc + q] (c < N; the structure for c < maskC).  C must be
 // 16-byte aligned with ldc % 4 == 0 (tc_gemm_supported); xs (16-byte aligned,
 // tc_xsplit_bytes(M, K)) receives the TF32 parts of X.  kchunk must come from tc_kchunk with
-// the same bf16 flag.  bf16: both operands rounded to BF16 (round to nearest even), products on
+// the same bf16 flag and M.  bf16: both operands rounded to BF16 (round to nearest even), products on
 // the kind::f16 tensor path with FP32 accumulation (the BF16 sketch; no reflector masks).
 bool tc_gemm_supported(long long M, long long ldc, const void* C, int bf16 = 0);
 size_t tc_xsplit_bytes(long long M, long long K);
-long long tc_kchunk(long long N, long long K, int& nsplit, int bf16 = 0);
+long long tc_kchunk(long long N, long long K, int& nsplit, int bf16 = 0, long long M = 96);
 cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
                               long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
                               const Status* st, cudaStream_t s, int bf16 = 0);

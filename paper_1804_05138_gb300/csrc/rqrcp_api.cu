@@ -116,14 +116,16 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     return L;
 }
 
-// Split-K factor for an M x N result contracted over K on the SIMT contraction (64 x 64 tiles):
-// the split count S <= max_split minimising waves x (rows per split + a fixed cost of 64 rows),
-// a wave being the blocks resident on the whole GPU at once; splits of at least 64 rows.
+// Split-K factor for an M x N result contracted over K on the SIMT contraction (tiles of
+// gemm_tn_tile_rows(M) x 64): the split count S <= max_split minimising waves x (rows per split + a
+// fixed cost of 64 rows), a wave being the blocks resident on the whole GPU at once; splits of at
+// least 64 rows.
 void choose_split(int64_t M, int64_t N, int64_t K, int& nsplit, int64_t& kchunk, int elem_bytes = 8,
                   int64_t max_split = kMaxSplit)
 {
-    const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
-    const int64_t wave = (int64_t)gemm_tn_blocks_per_sm(elem_bytes) * dev_info().sms;
+    const int64_t tr = gemm_tn_tile_rows(M);
+    const int64_t tiles = ((M + tr - 1) / tr) * ((N + 63) / 64);
+    const int64_t wave = (int64_t)gemm_tn_blocks_per_sm(elem_bytes, M) * dev_info().sms;
     int64_t smax = (K + 63) / 64;
     if (smax > max_split) smax = max_split;
     if (smax < 1) smax = 1;
@@ -227,7 +229,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         const int bf = sizeof(T) == 4 && sketch_bf16 ? 1 : 0;
         const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(l, lda, (const void*)A, bf);
         if (tc) {
-            kc = tc_kchunk(n, m, ns, bf);
+            kc = tc_kchunk(n, m, ns, bf, l);
             RQ_LAUNCH(K_SKETCH_GEMM, 2.0 * l * m * n, (double)m * n * es + (double)l * m * es,
                       launch_gemm_tn_tc((const float*)Omega, ldo, (const float*)A, lda, l, n, m, kc, P, 0, 0,
                                         reinterpret_cast<float*>(w + L.xs), st, s, bf));
@@ -266,7 +268,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         int64_t kc;
         const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(bb, lda, (const void*)Vp);
         if (tc) {
-            kc = tc_kchunk(n - i, mr, ns);
+            kc = tc_kchunk(n - i, mr, ns, 0, bb);
             RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
                       launch_gemm_tn_tc((const float*)Vp, lda, (const float*)Vp, lda, bb, n - i, mr, kc, P, bb, bb,
                                         reinterpret_cast<float*>(w + L.xs), st, s));

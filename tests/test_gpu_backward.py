@@ -7,7 +7,7 @@
   directions (pivots unchanged) to 1e-6.
 * FP32 at 4096 x 4096, k = 256, sigma_i = 1/(1+i)^2: the same gradient against the FP64
   oracle adjoint computed with the GPU's permutation and against the library's FP64 backward
-  kernels fed the same permutation; the FP32 error is bounded by 4 kappa(R11) 2^-24 normwise,
+  kernels fed the same permutation; the FP32 error is bounded by kappa(R11) 2^-24 / 4 normwise,
   kappa(R11) measured in the test.
 """
 import numpy as np
@@ -108,7 +108,8 @@ def test_backward_fp32_4096_k256_vs_oracle(ag, orc):
     gradient with the GPU's permutation, from the oracle (closed form + adjoint) and from the
     library's FP64 backward kernels.  The bar follows the error of the FP32 computation: the
     adjoint applies R11^{-T}, so FP32 rounding of the factors (about 2^-24 relative) grows by
-    kappa(R11), measured here from the FP64 R11; the bar is 4 kappa(R11) 2^-24."""
+    kappa(R11), measured here from the FP64 R11.  The bar is kappa(R11) 2^-24 / 4 (the normwise
+    worst case overstates the error: measured 8.7e-5 against kappa(R11) 2^-24 = 2.6e-3 here)."""
     import torch
     m = n = 4096
     k, b, p = 256, 64, 8
@@ -127,7 +128,7 @@ def test_backward_fp32_4096_k256_vs_oracle(ag, orc):
     want = _oracle_grad(orc, A32, jp, k, G1d, G2d)
     Q1o, R11o, R12o = orc.truncated_qr_forward(A32[:, jp], k)
     kappa = float(np.linalg.cond(R11o))
-    bar = 4.0 * kappa * 2.0 ** -24
+    bar = 0.25 * kappa * 2.0 ** -24
     rel = np.linalg.norm(got - want) / np.linalg.norm(want)
     g64 = _gpu64_grad(A32, jp, Q1o, np.concatenate([R11o, R12o], axis=1), G1d, G2d)
     assert np.linalg.norm(g64 - want) <= 1e-10 * np.linalg.norm(want)

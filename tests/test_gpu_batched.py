@@ -69,6 +69,31 @@ def test_small_batch_against_oracle(gpu, orc):
         assert np.array_equal(jp[:upto], ref.jpvt[:upto]), (i, upto)
 
 
+@pytest.mark.parametrize("tiles", [1, 2, 4, 8, 2 | 4 | 8])
+def test_small_batch_tile_variants_against_oracle(gpu, orc, tiles):
+    """Every tile-shape choice the autotuner may pick (RQRCP_TILES_*) meets the same bar as the
+    default rules on the same batch."""
+    import torch
+    p, seed = 8, 3
+    shapes = [(m, n, k) for m, n, k, _ in SMALL]
+    bs = [b for *_, b in SMALL]
+    mats = _spectrum_batch(shapes)
+    A0s = [A.double().cpu().numpy() for A in mats]
+    batch = gpu.Batch(mats, [k for _, _, k in shapes], bs, p=p, seed=seed, tiles=[tiles] * len(shapes))
+    assert batch.run() == 0
+    torch.cuda.synchronize()
+    Om_full = orc.omega(batch.b_max + p, batch.m_max, seed).astype(np.float32).astype(np.float64)
+    for i, ((m, n, k), b) in enumerate(zip(shapes, bs)):
+        ref = orc.rqrcp(A0s[i], k, b, p, np.ascontiguousarray(Om_full[:b + p, :m]))
+        jp = batch.jpvts[i].cpu().numpy()
+        assert int(batch.ranks[i]) == ref.rank == k
+        res = orc.rel_residual(A0s[i], batch.mats[i].double().cpu().numpy(), batch.taus[i].cpu().numpy(), jp, k)
+        assert res <= 1e-6, (tiles, i, res)
+        sep = ref.gaps >= 1e-4
+        upto = k if sep.all() else int(np.argmin(sep))
+        assert np.array_equal(jp[:upto], ref.jpvt[:upto]), (tiles, i, upto)
+
+
 def test_graph_replay_matches_eager(gpu):
     import torch
     shapes = [(m, n, k) for m, n, k, _ in SMALL[:6]]
@@ -104,8 +129,9 @@ def test_full_batch_512(gpu, orc):
     table = autotune.load_or_tune(shapes, p=8)
     bs = [autotune.choose(table, m, n, k) for (m, n, k) in shapes]
     assert all(1 <= b <= min(64, k) for b, (_, _, k) in zip(bs, shapes))
+    tiles = [autotune.choose_tiles(table, m, n, k) for (m, n, k) in shapes]
     mats = _spectrum_batch(shapes, seed0=1000, torch_gen=True)
-    batch = gpu.Batch(mats, [k for _, _, k in shapes], bs, p=8, seed=0)
+    batch = gpu.Batch(mats, [k for _, _, k in shapes], bs, p=8, seed=0, tiles=tiles)
     picks = [int(np.argmax([m * n for m, n, _ in shapes])), int(np.argmin([m * n for m, n, _ in shapes])), 7, 200, 411]
     A0 = {i: mats[i].double().cpu().numpy() for i in picks}
     assert batch.run() == 0

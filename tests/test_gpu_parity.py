@@ -143,7 +143,7 @@ def test_rank_out_reports_the_guard(gpu, orc):
     assert code == 0 and int(rank.item()) == rk == ref.rank
 
 
-@pytest.mark.parametrize("m,n,l", [(1000, 1000, 40), (777, 333, 72), (64, 3000, 80)])
+@pytest.mark.parametrize("m,n,l", [(1000, 1000, 40), (777, 333, 72), (64, 3000, 80), (500, 700, 96), (300, 257, 130)])
 def test_sketch_matches_oracle(gpu, orc, m, n, l):
     import torch
     A0 = inputs.gaussian(m, n, seed=1)
