@@ -254,10 +254,22 @@ cudaError_t launch_swaps(T* A, int64_t lda, int64_t m, int bb, const long long* 
 // Status block reset (rank = k) and jpvt = 0..n-1.
 cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s);
 
-// Cooperative Householder panel QR of A(i:m, i:i+bb) (FP64 reflector generation).
+// Cooperative Householder panel QR of A(i:m, i:i+bb) (FP64 reflector generation).  skip (FP32 form
+// only, device int, may be null): the kernel returns at once when *skip == 0 (the CholeskyQR2 panel
+// factored the panel).
 template <typename T>
 cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, double* part, Status* st,
-                         cudaStream_t s);
+                         cudaStream_t s, const int* skip = nullptr);
+
+// CholeskyQR2 panel with Householder reconstruction for the FP32 form (cholqr.cu): writes the panel's
+// R, reflector tails and tau in the layout of launch_panel<float>, or leaves the panel untouched and
+// sets *flag_out = 1 when the panel is too ill-conditioned (launch_panel with skip = that flag then
+// factors it).  ws: cholqr_ws_bytes(m1) bytes, 256-byte aligned.
+bool cholqr_supported(int bb);
+bool cholqr_enabled();
+size_t cholqr_ws_bytes(int64_t m_max);
+cudaError_t launch_cholqr_panel(float* A, int64_t lda, int64_t m1, int bb, double* tau, void* ws, int** flag_out,
+                                const Status* st, cudaStream_t s);
 size_t panel_part_bytes(int bb);
 bool panel_fits(int64_t m1, int bb, int elem_bytes);
 bool pivot_fits(int64_t ncols, int l, int elem_bytes);

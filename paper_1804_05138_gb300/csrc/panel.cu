@@ -192,9 +192,12 @@ __device__ __forceinline__ void dot2_acc(float x, float y, float& s, float& c)
 
 __global__ void __launch_bounds__(kPanelThreads) panel_f32_kernel(float* __restrict__ A, int64_t lda, int64_t m1, int bb,
                                                         int64_t rpb, double* __restrict__ tau,
-                                                        double* __restrict__ part, Status* st)
+                                                        double* __restrict__ part, Status* st,
+                                                        const int* __restrict__ skip)
 {
     if (status_error(st)) return;
+    // the CholeskyQR2 panel (cholqr.cu) already factored this panel unless it set its fallback flag
+    if (skip != nullptr && *(volatile const int*)skip == 0) return;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, NTH = blockDim.x;
     extern __shared__ __align__(16) double smd[];
     const int bbp = pow2_at_least(bb);
@@ -338,7 +341,7 @@ bool panel_fits(int64_t m1, int bb, int elem_bytes)
 
 template <typename T>
 cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, double* part, Status* st,
-                         cudaStream_t s)
+                         cudaStream_t s, const int* skip)
 {
     constexpr bool f32 = sizeof(T) == 4;
     const void* kern = f32 ? (const void*)panel_f32_kernel : (const void*)panel_kernel<double>;
@@ -358,11 +361,15 @@ cudaError_t launch_panel(T* A, int64_t lda, int64_t m1, int bb, double* tau, dou
     if ((int64_t)per_sm * dev_info().sms < G) return cudaErrorCooperativeLaunchTooLarge;
     int64_t ldav = lda, m1v = m1, rpbv = rpb;
     int bbv = bb;
-    void* args[] = {&A, &ldav, &m1v, &bbv, &rpbv, &tau, &part, &st};
-    return cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(threads), args, smem, s);
+    const int* skipv = skip;
+    void* args_f64[] = {&A, &ldav, &m1v, &bbv, &rpbv, &tau, &part, &st};
+    void* args_f32[] = {&A, &ldav, &m1v, &bbv, &rpbv, &tau, &part, &st, &skipv};
+    return cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(threads), f32 ? args_f32 : args_f64, smem, s);
 }
 
-template cudaError_t launch_panel<double>(double*, int64_t, int64_t, int, double*, double*, Status*, cudaStream_t);
-template cudaError_t launch_panel<float>(float*, int64_t, int64_t, int, double*, double*, Status*, cudaStream_t);
+template cudaError_t launch_panel<double>(double*, int64_t, int64_t, int, double*, double*, Status*, cudaStream_t,
+                                          const int*);
+template cudaError_t launch_panel<float>(float*, int64_t, int64_t, int, double*, double*, Status*, cudaStream_t,
+                                         const int*);
 
 }  // namespace rq

@@ -69,6 +69,17 @@ bool tensor_cores_enabled()
     }
     return v == 1;
 }
+// RQRCP_PANEL=householder in the environment keeps the FP32 form on the cooperative Householder
+// panel (one grid-wide step per column) instead of the CholeskyQR2 panel, for A/B timing.
+bool cholqr_enabled()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("RQRCP_PANEL");
+        v = (e != nullptr && (e[0] == 'h' || e[0] == 'H')) ? 0 : 1;
+    }
+    return v == 1;
+}
 template <typename T>
 cudaError_t launch_eye(T* Q, int64_t ldq, int64_t m, int64_t k, cudaStream_t s);
 
@@ -80,7 +91,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, total;
+    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
@@ -112,6 +123,8 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
         const size_t xs = tc_xsplit_bytes(l > b ? l : b, m), ys = tc_update_ws_bytes(n);
         L.xs = take(esz == sizeof(float) ? (xs > ys ? xs : ys) : 0);
     }
+    // FP32 form: the CholeskyQR2 panel's partial Grams, factors and Q1 (m x 64)
+    L.cqr = take(esz == sizeof(float) ? cholqr_ws_bytes(m) : 0);
     L.total = off;
     return L;
 }
@@ -260,8 +273,20 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
             RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * l * es, launch_swaps<T>(Bc, l, l, bb, swapmap, tmp, st, s));
         T* Vp = A + i * lda + i;
         const int64_t mr = m - i;
-        RQ_LAUNCH(K_PANEL, 2.0 * mr * bb * bb - 2.0 * bb * bb * bb / 3.0, 2.0 * mr * bb * es,
-                  launch_panel<T>(Vp, lda, mr, bb, tau + i, part, st, s));
+        if (sizeof(T) == 4 && cholqr_enabled() && cholqr_supported(bb)) {
+            // CholeskyQR2 + Householder reconstruction; the cooperative Householder panel after it
+            // returns at once unless the panel was too ill-conditioned for CholeskyQR2
+            int* cqr_flag = nullptr;
+            const bool prof_ = prof_on();
+            if (prof_) prof_begin(K_PANEL, s);
+            RQ_CHECK(launch_cholqr_panel(reinterpret_cast<float*>(Vp), lda, mr, bb, tau + i, w + L.cqr, &cqr_flag, st,
+                                         s));
+            RQ_CHECK(launch_panel<T>(Vp, lda, mr, bb, tau + i, part, st, s, cqr_flag));
+            if (prof_) prof_end(K_PANEL, 2.0 * mr * bb * bb - 2.0 * bb * bb * bb / 3.0, 2.0 * mr * bb * es, s);
+        } else {
+            RQ_LAUNCH(K_PANEL, 2.0 * mr * bb * bb - 2.0 * bb * bb * bb / 3.0, 2.0 * mr * bb * es,
+                      launch_panel<T>(Vp, lda, mr, bb, tau + i, part, st, s));
+        }
         const int64_t nt = n - i - bb;
         if (nt <= 0) continue;
         int ns;
