@@ -431,8 +431,8 @@ def gpu_launch_count(prof, mixed):
     """Kernels the library launched in the profiled region: classes x kernels per launch of each."""
     per = {"swap": 2, "bupdate": 2, "omega": 0}
     if mixed:  # tensor-core contractions: an operand-splitting kernel, then the contraction; the
-        # CholeskyQR2 panel: two Gram, reduce and Cholesky passes, the rebuild, the row pass and
-        # the (normally idle) Householder fallback
+        # CholeskyQR2 panel: two Gram, reduce and Cholesky passes, the row solve between them, the
+        # rebuild, the row solve below it and the (normally idle) Householder fallback
         per.update({"sketch_gemm": 2, "wy_gemm_tn": 2, "wy_update": 2, "panel": 9})
     return sum(v["launches"] * per.get(kname, 1) for kname, v in prof.items())
 

@@ -2,348 +2,535 @@
 // form by CholeskyQR2 with Householder reconstruction, instead of one grid-wide step per column.
 //
 // For the (m1 x bb) FP32 panel P (bb <= 64):
-//   pass 1  G1 = P^T P (Dot2 sums of exact FP32 products per block, FP64 across blocks in a fixed
-//           order), G1 = R1^T R1 (FP64 Cholesky);
-//   pass 2  Q1 = P R1^{-1} row by row (forward substitution with R1 as float pairs and Dot2 sums,
-//           rounded to FP32), G2 = Q1^T Q1, G2 = R2^T R2; R = R2 R1 and P = (Q1 R2^{-1}) R;
+//   pass 1  G1 = P^T P (FP32 sums folded into float pairs every 32 rows, FP64 across blocks in a
+//           fixed order), G1 = R1^T R1 (Cholesky in float-pair arithmetic, about 44 significant bits,
+//           on G1 scaled by a power of two);
+//   pass 2  Q1 = P R1^{-1} row by row (forward substitution in FP32 with R1 rounded to FP32: the
+//           substitution is backward stable), G2 = Q1^T Q1, G2 = R2^T R2; R = R2 R1 and
+//           P = (Q1 R2^{-1}) R;
 //   rebuild with Q2 = Q1 R2^{-1} (orthonormal to FP32 level), the LU factorization without pivoting
 //           Q2 - S = [L1; L2] U, S = diag(s_j) with s_j = -sign of the j-th pivot, gives the
 //           Householder vectors V = [L1; L2] (unit lower), tau_j = -s_j U(j,j) and R_house = S R:
 //           the representation xGEQRF computes (xLARFG sign convention), up to rounding (Ballard
 //           et al., "Reconstructing Householder vectors from tall-skinny QR", 2014).  The top bb rows
-//           of Q2 are formed and factored in FP64 in one block; the rows below are V2 = Q1 (U R2)^{-1},
-//           again row by row with float-pair coefficients.
-// CholeskyQR2 needs kappa(P) well below u^{-1/2} of the Gram's arithmetic; a pivot of G1 below
-// 2^-36 of its diagonal entry (kappa(P) beyond about 2.6e5), or a pivot of G2 below 1/2, sets a
-// flag on the device: the panel is then left untouched and the cooperative Householder panel
-// kernel launched after this one factors it instead (it reads the flag and returns at once when
-// the CholeskyQR2 result was written).  No host synchronisation.
+//           of Q2 are formed and factored in one block; the rows below are V2 = Q1 (U R2)^{-1}, one
+//           row per thread.
+// The small factorizations run in float pairs (Dekker products by FMA, Knuth sums) because one SM
+// issues FP64 at a small fraction of its FP32 rate; their steps deal the trailing entries out evenly
+// over the block's threads from a table and take one barrier each.  CholeskyQR2 needs kappa(P) well
+// below the inverse square root of the Gram's precision: a pivot of G1 below 2^-20 of its diagonal
+// entry (kappa(P) beyond about 1e3; G1 is summed in FP32), or a pivot of G2 below 1/2, sets a flag;
+// the panel is then left untouched and the cooperative Householder panel kernel launched after this
+// one factors it instead (it reads the flag and returns at once when the CholeskyQR2 result was
+// written).  No host synchronisation.
 #include "internal.cuh"
 
 namespace rq {
 namespace {
 
 constexpr int kCqrMaxB = 64;
+constexpr int kLd = kCqrMaxB + 1;                      // odd stride: a column of a row-major tile hits distinct banks
+constexpr int kLx = kCqrMaxB + 4;                      // Gram tiles: 16-byte aligned rows for 128-bit loads
 constexpr int kCqrNE = kCqrMaxB * (kCqrMaxB + 1) / 2;  // packed upper-triangle entries
-constexpr int kCqrRows = 256;                          // panel rows per block of the row passes
-constexpr int kCqrThreads = 256;
-constexpr int kCqrSmallThreads = 512;
+constexpr int kCqrRows = 128;                          // panel rows per Gram block
+constexpr int kGramTiles = 16 * 17 / 2;                // 4 x 4 micro-tiles on and above the diagonal
+constexpr int kGramThreads = 160;
+constexpr int kSolveThreads = 128;                     // one panel row per thread
+constexpr int kSmallThreads = 512;
+constexpr int kRedWarps = 8;
+// pass-1 pivot test: the Gram G1 is summed in FP32 (folded into pairs), so CholeskyQR2 is kept only
+// while kappa(P) stays below about 2^10
+constexpr float kCqrPass1Thr = 9.5367431640625e-07f;  // 2^-20
 
-// entry e of the packed upper triangle (row-major): (i, j), i <= j
-__device__ __forceinline__ void tri_ij(int e, int bb, int& i, int& j)
+// ---------------------------------------------------------------------------------- float pairs
+struct df {
+    float h, l;
+};
+__device__ __forceinline__ df df_two_sum(float a, float b)
 {
-    int r = 0, start = 0;
-    while (start + (bb - r) <= e) {
-        start += bb - r;
-        ++r;
-    }
-    i = r;
-    j = r + (e - start);
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
+    const float s = a + b;
     const float z = s - a;
-    e = (a - (s - z)) + (b - z);
+    return {s, (a - (s - z)) + (b - z)};
 }
-
-// (sh, sl) += x * y with the product's rounding error (FMA) and the sum's (TwoSum) carried in sl.
-__device__ __forceinline__ void dot2_add(float& sh, float& sl, float x, float y)
+__device__ __forceinline__ df df_quick(float a, float b)  // |a| >= |b|
 {
-    const float p = x * y;
-    const float pe = fmaf(x, y, -p);
-    float t, e;
-    two_sum(sh, p, t, e);
-    sh = t;
-    sl += e + pe;
+    const float s = a + b;
+    return {s, b - (s - a)};
 }
-
-// Row solve q R = p for one row (R upper bb x bb as float pairs Rh/Rl, row-major [q * ld + c]) with
-// Dot2 sums; rinv[c] = 1 / R(c, c) in FP32.  q may alias p.
-__device__ __forceinline__ void row_solve(float* q, const float* p, int bb, const float* Rh, const float* Rl, int ld,
-                                          const float* rinv)
+__device__ __forceinline__ df df_add(df a, df b)
 {
-    for (int c = 0; c < bb; ++c) {
-        float sh = p[c], sl = 0.f;
-        for (int k = 0; k < c; ++k) {
-            const float qk = q[k];
-            dot2_add(sh, sl, -qk, Rh[k * ld + c]);
-            sl = fmaf(-qk, Rl[k * ld + c], sl);
-        }
-        q[c] = (sh + sl) * rinv[c];
+    const df s = df_two_sum(a.h, b.h);
+    return df_quick(s.h, s.l + a.l + b.l);
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p);
+    return df_quick(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+// c - a b
+__device__ __forceinline__ df df_fms(df c, df a, df b) { return df_add(c, df_neg(df_mul(a, b))); }
+// 1 / a: FP32 reciprocal refined by one Newton step in pairs
+__device__ __forceinline__ df df_rcp(df a)
+{
+    const float r = 1.0f / a.h;
+    const df e = df_add({1.0f, 0.0f}, df_neg(df_mul(a, {r, 0.0f})));  // 1 - a r
+    return df_add({r, 0.0f}, df_mul({r, 0.0f}, e));
+}
+// a^{-1/2}: FP32 reciprocal square root refined by one Newton step in pairs
+__device__ __forceinline__ df df_rsqrt(df a)
+{
+    const float y = rsqrtf(a.h);
+    const float p = y * y;
+    const df yy = {p, fmaf(y, y, -p)};
+    const df e = df_add({1.0f, 0.0f}, df_neg(df_mul(a, yy)));  // 1 - a y^2
+    return df_add({y, 0.0f}, df_mul({0.5f * y, 0.0f}, e));
+}
+__device__ __forceinline__ df df_of(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_dbl(df a) { return (double)a.h + (double)a.l; }
+
+// --------------------------------------------------------------------------- index tables
+// packed upper-triangle index of (i, j), i <= j, row-major
+__device__ __forceinline__ int tri_index(int i, int j, int bb) { return i * bb - i * (i - 1) / 2 + (j - i); }
+// first entry of shell m = min(r, c) when a bb x bb square is listed shell by shell
+__device__ __forceinline__ int sq_start(int m, int bb) { return 2 * bb * m - m * m; }
+__device__ __forceinline__ int tab_r(uint16_t t) { return t & 0xff; }
+__device__ __forceinline__ int tab_c(uint16_t t) { return t >> 8; }
+
+// tab[tri_index(i, j, bb)] = (i, j): the entries of rows > j form the suffix from tri_index(j+1, j+1).
+__device__ void build_tri_table(uint16_t* tab, int bb)
+{
+    const int i = threadIdx.x;
+    if (i < bb) {
+        const int base = tri_index(i, i, bb);
+        for (int j = i; j < bb; ++j) tab[base + j - i] = (uint16_t)(i | (j << 8));
+    }
+}
+// The bb x bb square shell by shell: shell m lists (m, m), (m, m+1 .. bb-1), (m+1 .. bb-1, m); the
+// entries with min(r, c) > j form the suffix from sq_start(j + 1).
+__device__ void build_sq_table(uint16_t* tab, int bb)
+{
+    const int m = threadIdx.x;
+    if (m < bb) {
+        int e = sq_start(m, bb);
+        tab[e++] = (uint16_t)(m | (m << 8));
+        for (int c = m + 1; c < bb; ++c) tab[e++] = (uint16_t)(m | (c << 8));
+        for (int r = m + 1; r < bb; ++r) tab[e++] = (uint16_t)(r | (m << 8));
     }
 }
 
-// Pass 1 (Rh == nullptr): Gram partials of the panel rows of this block.  Pass 2: first Q1 = P R1^{-1}
-// for the block's rows (stored to Q1, ld m1), then the Gram partials of Q1.  part[g * NE + e] (FP64).
-__global__ void __launch_bounds__(kCqrThreads) cqr_gram_kernel(const float* __restrict__ P, int64_t ldp, int64_t m1,
-                                                               int bb, const float* __restrict__ R1h,
-                                                               const float* __restrict__ R1l,
-                                                               const float* __restrict__ r1inv, float* __restrict__ Q1,
-                                                               double* __restrict__ part, const int* flag,
-                                                               const Status* st)
+// ------------------------------------------------------------------------------- row solves
+// x := x R^{-1} for one row held in registers (x(c) = 0 for c >= bb): R upper triangular in FP32,
+// row-major with ld kCqrMaxB, 16-byte aligned, zero outside its bb x bb upper triangle; (rh, rl) the
+// float pairs of 1 / R(c, c), (1, 0) for c >= bb.  Column-oriented substitution: q(c) = x(c) / R(c, c),
+// then x(j) -= q(c) R(c, j) for j > c, in FP32 with FMA.  Every thread of a warp reads the same R
+// entries (broadcast loads).
+__device__ __forceinline__ void row_solve_regs(float (&x)[kCqrMaxB], const float* __restrict__ R, const float* rh,
+                                               const float* rl)
+{
+#pragma unroll
+    for (int c = 0; c < kCqrMaxB; ++c) {
+        const float q = fmaf(x[c], rl[c], x[c] * rh[c]);
+        x[c] = q;
+        const float4* Rc = reinterpret_cast<const float4*>(R + c * kCqrMaxB);
+#pragma unroll
+        for (int t = (c + 1) >> 2; t < kCqrMaxB / 4; ++t) {
+            const float4 v = Rc[t];
+            if (4 * t + 0 > c) x[4 * t + 0] = fmaf(-q, v.x, x[4 * t + 0]);
+            if (4 * t + 1 > c) x[4 * t + 1] = fmaf(-q, v.y, x[4 * t + 1]);
+            if (4 * t + 2 > c) x[4 * t + 2] = fmaf(-q, v.z, x[4 * t + 2]);
+            if (4 * t + 3 > c) x[4 * t + 3] = fmaf(-q, v.w, x[4 * t + 3]);
+        }
+    }
+}
+
+// Y(r, 0:bb) = X(r, 0:bb) R^{-1} for the rows r = row0 .. row0 + nrows - 1 of the column-major X (ld ldx)
+// and Y (ld ldy), one row per thread (coalesced column loads and stores): R is the bb x bb upper
+// triangle of Rg (FP32, row-major, ld kCqrMaxB) and (rhg, rlg) the pairs of its diagonal's
+// reciprocals.  Returns at once when the flag is set.
+__global__ void __launch_bounds__(kSolveThreads) cqr_solve_kernel(const float* __restrict__ X, int64_t ldx,
+                                                                  float* __restrict__ Y, int64_t ldy, int64_t row0,
+                                                                  int64_t nrows, int bb, const float* __restrict__ Rg,
+                                                                  const float* __restrict__ rhg,
+                                                                  const float* __restrict__ rlg, const int* flag,
+                                                                  const Status* st)
 {
     if (status_error(st)) return;
-    if (R1h != nullptr && *(volatile const int*)flag) return;  // pass 1 already chose the fallback
-    extern __shared__ float cqr_sm[];
-    float(*X)[kCqrMaxB + 1] = reinterpret_cast<float(*)[kCqrMaxB + 1]>(cqr_sm);  // kCqrRows rows
-    float* sRh = cqr_sm + kCqrRows * (kCqrMaxB + 1);
-    float* sRl = sRh + kCqrMaxB * kCqrMaxB;
-    float* sri = sRl + kCqrMaxB * kCqrMaxB;
+    if (*(volatile const int*)flag) return;
+    __shared__ __align__(16) float sR[kCqrMaxB * kCqrMaxB];
+    __shared__ float srh[kCqrMaxB], srl[kCqrMaxB];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kCqrMaxB * kCqrMaxB; e += kSolveThreads) {
+        const int i = e >> 6, j = e & (kCqrMaxB - 1);
+        sR[e] = (i <= j && j < bb) ? Rg[e] : 0.f;
+    }
+    if (tid < kCqrMaxB) {
+        srh[tid] = tid < bb ? rhg[tid] : 1.f;
+        srl[tid] = tid < bb ? rlg[tid] : 0.f;
+    }
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kSolveThreads + tid;
+    if (r >= nrows) return;
+    const float* xr = X + row0 + r;
+    float x[kCqrMaxB];
+#pragma unroll
+    for (int c = 0; c < kCqrMaxB; ++c) x[c] = c < bb ? xr[(int64_t)c * ldx] : 0.f;
+    row_solve_regs(x, sR, srh, srl);
+    float* yr = Y + row0 + r;
+#pragma unroll
+    for (int c = 0; c < kCqrMaxB; ++c)
+        if (c < bb) yr[(int64_t)c * ldy] = x[c];
+}
+
+// ------------------------------------------------------------------------------------ Gram
+// Gram partials of the kCqrRows-row block g of X (m1 x bb, column-major, ld ldx): part[g * NE + e]
+// (FP64) for the packed upper triangle.  Thread t < 136 owns the 4 x 4 micro-tile (I, J), I <= J, of
+// the 64 x 64 Gram (two 128-bit shared loads and 16 FMA per row), FP32 sums folded into float pairs
+// every 32 rows.  In pass 2 the kernel returns at once when the flag is set.
+__global__ void __launch_bounds__(kGramThreads) cqr_gram_kernel(const float* __restrict__ X, int64_t ldx, int64_t m1,
+                                                                int bb, double* __restrict__ part, const int* flag,
+                                                                int pass, const Status* st)
+{
+    if (status_error(st)) return;
+    if (pass == 2 && *(volatile const int*)flag) return;
+    __shared__ __align__(16) float T[kCqrRows][kLx];
     const int tid = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * kCqrRows;
     const int nr = (int)min((int64_t)kCqrRows, m1 - r0);
-    for (int e = tid; e < nr * bb; e += kCqrThreads) {
-        const int r = e % nr, c = e / nr;
-        X[r][c] = P[(int64_t)c * ldp + r0 + r];
-    }
-    if (R1h != nullptr) {
-        for (int e = tid; e < bb * bb; e += kCqrThreads) {
-            const int o = (e / bb) * kCqrMaxB + e % bb;
-            sRh[o] = R1h[o];
-            sRl[o] = R1l[o];
-        }
-        for (int e = tid; e < bb; e += kCqrThreads) sri[e] = r1inv[e];
+    for (int e = tid; e < kCqrRows * kCqrMaxB; e += kGramThreads) {
+        const int r = e & (kCqrRows - 1), c = e >> 7;
+        T[r][c] = (r < nr && c < bb) ? X[(int64_t)c * ldx + r0 + r] : 0.f;
     }
     __syncthreads();
-    if (R1h != nullptr) {
-        // this thread's row, solved in place in the shared tile (stride kCqrMaxB + 1: no bank conflicts)
-        if (tid < nr) row_solve(X[tid], X[tid], bb, sRh, sRl, kCqrMaxB, sri);
-        __syncthreads();
-        for (int e = tid; e < nr * bb; e += kCqrThreads) {
-            const int r = e % nr, c = e / nr;
-            Q1[(int64_t)c * m1 + r0 + r] = X[r][c];
+    if (tid >= kGramTiles) return;
+    int I = 0, rem = tid;
+    while (rem >= 16 - I) {
+        rem -= 16 - I;
+        ++I;
+    }
+    const int J = I + rem;
+    if (4 * J >= bb) return;  // the tile holds no entry (i, j), i <= j < bb
+    float a[16], sh[16], sl[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) a[t] = sh[t] = sl[t] = 0.f;
+    for (int rb = 0; rb < nr; rb += 32) {
+        const int re = min(nr, rb + 32);
+#pragma unroll 4
+        for (int r = rb; r < re; ++r) {
+            const float4 x = *reinterpret_cast<const float4*>(&T[r][4 * I]);
+            const float4 y = *reinterpret_cast<const float4*>(&T[r][4 * J]);
+            const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) a[4 * u + v] = fmaf(xv[u], yv[v], a[4 * u + v]);
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const df s = df_two_sum(sh[t], a[t]);
+            sh[t] = s.h;
+            sl[t] += s.l;
+            a[t] = 0.f;
         }
     }
-    const int ne = bb * (bb + 1) / 2;
-    for (int e = tid; e < ne; e += kCqrThreads) {
-        int i, j;
-        tri_ij(e, bb, i, j);
-        float sh = 0.f, sl = 0.f;
-        for (int r = 0; r < nr; ++r) dot2_add(sh, sl, X[r][i], X[r][j]);
-        part[(size_t)blockIdx.x * kCqrNE + e] = (double)sh + (double)sl;
-    }
+    double* out = part + (size_t)blockIdx.x * kCqrNE;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = 4 * I + u, j = 4 * J + v;
+            if (i <= j && j < bb) out[tri_index(i, j, bb)] = (double)sh[4 * u + v] + (double)sl[4 * u + v];
+        }
 }
 
-// G[e] = sum over blocks g (in order) of part[g * NE + e].
-__global__ void cqr_reduce_kernel(const double* __restrict__ part, int nblk, int ne, double* __restrict__ G,
-                                  const int* flag, int pass, const Status* st)
+// G[e] = sum over blocks g of part[g * NE + e]: 32 entries per block (coalesced rows of part), warp w
+// sums the blocks g = w (mod 8) in order, then the eight sums are added in warp order.
+__global__ void __launch_bounds__(32 * kRedWarps) cqr_reduce_kernel(const double* __restrict__ part, int nblk,
+                                                                    int ne, double* __restrict__ G, const int* flag,
+                                                                    int pass, const Status* st)
 {
     if (status_error(st)) return;
     if (pass == 2 && *(volatile const int*)flag) return;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    double s0 = 0.0, s1 = 0.0;
-    int g = 0;
-    for (; g + 1 < nblk; g += 2) {
-        s0 += part[(size_t)g * kCqrNE + e];
-        s1 += part[(size_t)(g + 1) * kCqrNE + e];
+    __shared__ double red[kRedWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (e < ne)
+        for (int g = w; g < nblk; g += kRedWarps) s += part[(size_t)g * kCqrNE + e];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < ne) {
+        double t = red[0][lane];
+        for (int k = 1; k < kRedWarps; ++k) t += red[k][lane];
+        G[e] = t;
     }
-    if (g < nblk) s0 += part[(size_t)g * kCqrNE + e];
-    G[e] = s0 + s1;
 }
 
-// One block: Cholesky G = R^T R in FP64 (right-looking, reciprocal square roots), the fallback test,
-// R as float pairs (row-major, ld kCqrMaxB) with FP32 reciprocals of its diagonal, and for pass 2 the
-// product R = R2 R1 (FP64) into Rprod.
-__global__ void __launch_bounds__(kCqrSmallThreads) cqr_chol_kernel(const double* __restrict__ Gpk, int bb, int pass,
-                                                                    double* __restrict__ R, float* __restrict__ Rh,
-                                                                    float* __restrict__ Rl, float* __restrict__ rinv,
-                                                                    const double* __restrict__ R1,
-                                                                    double* __restrict__ Rprod, int* flag,
-                                                                    const Status* st)
+// ------------------------------------------------------------------------- small factorizations
+// Right-looking Cholesky G = R^T R of the bb x bb float-pair matrix (H, L) (upper triangle, stride
+// kLd), in place, by all the block's threads.  Step j subtracts A(j, r) A(j, c) / A(j, j) from every
+// (r, c) with j < r <= c, the entries dealt out evenly over the threads through the table tab
+// (build_tri_table), and ends with one barrier; row j stays unscaled until the end, when
+// R(j, c) = A(j, c) / sqrt(A(j, j)).  Returns false (uniformly in the block) if a pivot is not above
+// thr times its original diagonal entry d0.  The caller has synchronised the block after filling
+// (H, L), tab and d0; rs: 2 kCqrMaxB floats of scratch.
+__device__ bool df_cholesky(float (*H)[kLd], float (*L)[kLd], int bb, const uint16_t* tab, const float* d0, float thr,
+                            float* rs)
 {
-    if (status_error(st)) return;
-    if (pass == 2 && *(volatile const int*)flag) return;
-    __shared__ double S[kCqrMaxB][kCqrMaxB + 1];
-    __shared__ double d0[kCqrMaxB];
-    __shared__ int s_fail;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < bb * bb; e += kCqrSmallThreads) S[e / bb][e % bb] = 0.0;
-    if (tid == 0) s_fail = 0;
-    __syncthreads();
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int ne = bb * (bb + 1) / 2;
-    for (int e = tid; e < ne; e += kCqrSmallThreads) {
-        int i, j;
-        tri_ij(e, bb, i, j);
-        S[i][j] = Gpk[e];
-    }
-    __syncthreads();
-    for (int j = tid; j < bb; j += kCqrSmallThreads) d0[j] = S[j][j];
-    __syncthreads();
-    const double thr = pass == 1 ? 1.4551915228366852e-11 /* 2^-36 */ : 0.5;
     for (int j = 0; j < bb; ++j) {
-        const double djj = S[j][j];
-        const bool ok = djj > thr * d0[j] && djj > 0.0;
-        const double rs = ok ? rsqrt(djj) : 0.0;
-        __syncthreads();
-        if (!ok) {
-            if (tid == 0) s_fail = 1;
-            break;
-        }
-        // row j of R: S(j, j:) * rs; trailing update S(r, c) -= R(j, r) R(j, c), j < r <= c
-        for (int c = j + tid; c < bb; c += kCqrSmallThreads) S[j][c] = c == j ? djj * rs : S[j][c] * rs;
-        __syncthreads();
-        const int w = bb - j - 1;
-        for (int e = tid; e < w * w; e += kCqrSmallThreads) {
-            const int r = j + 1 + e / w, c = j + 1 + e % w;
-            if (r <= c) S[r][c] -= S[j][r] * S[j][c];
+        const df d = {H[j][j], L[j][j]};
+        // the pivot test in FP32 (every thread reads the same values: uniform)
+        if (!(d.h > thr * d0[j])) return false;
+        const df rd = df_rcp(d);
+        for (int e = tri_index(j + 1, j + 1, bb) + tid; e < ne; e += nt) {
+            const uint16_t t = tab[e];
+            const int r = tab_r(t), c = tab_c(t);
+            const df a = df_mul({H[j][r], L[j][r]}, rd);
+            const df v = df_fms({H[r][c], L[r][c]}, a, {H[j][c], L[j][c]});
+            H[r][c] = v.h;
+            L[r][c] = v.l;
         }
         __syncthreads();
     }
+    if (tid < bb) {
+        const df y = df_rsqrt({H[tid][tid], L[tid][tid]});
+        rs[tid] = y.h;
+        rs[kCqrMaxB + tid] = y.l;
+    }
     __syncthreads();
-    if (s_fail) {
+    for (int e = tid; e < ne; e += nt) {
+        const uint16_t t = tab[e];
+        const int i = tab_r(t), c = tab_c(t);
+        const df v = df_mul({H[i][c], L[i][c]}, {rs[i], rs[kCqrMaxB + i]});
+        H[i][c] = v.h;
+        L[i][c] = v.l;
+    }
+    __syncthreads();
+    return true;
+}
+
+// Pass-1 factor: the Cholesky factor R1 of G1 (scaled by a power of two for the pair arithmetic and
+// scaled back), as float pairs Rh/Rl (row-major, ld kCqrMaxB, the bb x bb upper triangle) with the
+// pairs of 1 / R1(j, j).  flag = 0 on success, 1 when the panel goes to the Householder fallback.
+__global__ void __launch_bounds__(kSmallThreads) cqr_small1_kernel(const double* __restrict__ Gpk, int bb,
+                                                                   float* __restrict__ Rh, float* __restrict__ Rl,
+                                                                   float* __restrict__ rh, float* __restrict__ rl,
+                                                                   int* flag, const Status* st)
+{
+    if (status_error(st)) return;
+    __shared__ float H[kCqrMaxB][kLd], L[kCqrMaxB][kLd];
+    __shared__ float d0[kCqrMaxB], rs[2 * kCqrMaxB];
+    __shared__ uint16_t tab[kCqrNE];
+    __shared__ double wmax[2];
+    const int tid = threadIdx.x, ne = bb * (bb + 1) / 2;
+    build_tri_table(tab, bb);
+    if (tid < 64) {
+        double m = tid < bb ? Gpk[tri_index(tid, tid, bb)] : 0.0;
+        if (!(m <= 1.7976931348623157e308)) m = 0.0;  // a non-finite Gram: its pivots fail below
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    }
+    __syncthreads();
+    const double mx = fmax(wmax[0], wmax[1]);
+    // 2^-2e with 2^e near sqrt(mx): the scaled diagonal is within [1/4, 4]
+    const int ex = mx > 0.0 ? ilogb(mx) / 2 : 0;
+    const double sc = ldexp(1.0, -2 * ex);
+    for (int e = tid; e < ne; e += kSmallThreads) {
+        const uint16_t t = tab[e];
+        const int i = tab_r(t), c = tab_c(t);
+        const df v = df_of(Gpk[e] * sc);
+        H[i][c] = v.h;
+        L[i][c] = v.l;
+        if (i == c) d0[i] = v.h;
+    }
+    __syncthreads();
+    if (!df_cholesky(H, L, bb, tab, d0, kCqrPass1Thr, rs)) {
         if (tid == 0) *flag = 1;
         return;
     }
-    for (int e = tid; e < bb * bb; e += kCqrSmallThreads) {
-        const int i = e / bb, j = e % bb;
-        const double v = i <= j ? S[i][j] : 0.0;
-        R[i * kCqrMaxB + j] = v;
-        const float h = (float)v;
-        Rh[i * kCqrMaxB + j] = h;
-        Rl[i * kCqrMaxB + j] = (float)(v - (double)h);
+    // R1 = R1_scaled 2^ex
+    const float un = ldexpf(1.0f, ex);
+    for (int e = tid; e < ne; e += kSmallThreads) {
+        const uint16_t t = tab[e];
+        const int i = tab_r(t), c = tab_c(t);
+        Rh[i * kCqrMaxB + c] = H[i][c] * un;
+        Rl[i * kCqrMaxB + c] = L[i][c] * un;
     }
-    for (int j = tid; j < bb; j += kCqrSmallThreads) rinv[j] = (float)(1.0 / S[j][j]);
-    if (pass == 1 && tid == 0) *flag = 0;
-    if (pass == 2) {
-        // Rprod = R2 R1 (both upper): (i, j) = sum_{i <= q <= j} R2(i, q) R1(q, j)
-        __syncthreads();
-        for (int e = tid; e < bb * bb; e += kCqrSmallThreads) {
-            const int i = e / bb, j = e % bb;
-            double s = 0.0;
-            for (int q = i; q <= j; ++q) s += S[i][q] * R1[q * kCqrMaxB + j];
-            Rprod[i * kCqrMaxB + j] = i <= j ? s : 0.0;
-        }
+    if (tid < bb) {
+        const df r = df_rcp({H[tid][tid] * un, L[tid][tid] * un});
+        rh[tid] = r.h;
+        rl[tid] = r.l;
     }
+    if (tid == 0) *flag = 0;
 }
 
-// One block: Q2top = Q1(0:bb, :) R2^{-1} (row solves), its LU without pivoting with the signs
-// s_j = -sign(pivot), tau_j = -s_j U(j, j), W = U R2 as float pairs for the rows below, and the
-// panel's top bb rows: R_house = S (R2 R1) on and above the diagonal, L1 below it.
-__global__ void __launch_bounds__(kCqrSmallThreads) cqr_lu_kernel(
-    const float* __restrict__ Q1, int64_t m1, int bb, const float* __restrict__ R2h, const float* __restrict__ R2l,
-    const float* __restrict__ r2inv, const double* __restrict__ R2, const double* __restrict__ Rprod,
-    float* __restrict__ A, int64_t lda, double* __restrict__ tau, float* __restrict__ Wh, float* __restrict__ Wl,
-    float* __restrict__ winv, const int* flag, const Status* st)
+// Pass-2 factor and the reconstruction, in one block: R2 from G2 (fallback if a pivot is below 1/2),
+// R = R2 R1, Q2top = Q1(0:bb, :) R2^{-1}, its LU without pivoting with s_j = -sign(pivot),
+// tau_j = -s_j U(j, j), W = U R2 in FP32 (with the pairs of 1 / W(j, j)) for the rows below, and the
+// panel's top bb rows: R_house = S R on and above the diagonal, L1 below it.
+struct Small2Smem {
+    float H[kCqrMaxB][kLd], L[kCqrMaxB][kLd];    // G2, then R2 (upper triangle)
+    float UH[kCqrMaxB][kLd], UL[kCqrMaxB][kLd];  // Q2top, then its LU
+    float E[kCqrMaxB][kLd];                      // R2 - I in FP32
+    float R1[kCqrMaxB][kLd];                     // R1 in FP32
+    __align__(16) float R2f[kCqrMaxB * kCqrMaxB];  // R2 in FP32 for the row solve (ld kCqrMaxB)
+    float r2h[kCqrMaxB], r2l[kCqrMaxB];
+    float pvh[kCqrMaxB], pvl[kCqrMaxB], rph[kCqrMaxB], rpl[kCqrMaxB], sgn[kCqrMaxB];
+    float d0[kCqrMaxB], rs[2 * kCqrMaxB];
+    uint16_t tri[kCqrNE];
+    uint16_t sq[kCqrMaxB * kCqrMaxB];
+};
+
+__global__ void __launch_bounds__(kSmallThreads) cqr_small2_kernel(
+    const double* __restrict__ Gpk, int bb, const float* __restrict__ R1h, const float* __restrict__ R1l,
+    const float* __restrict__ Q1, int64_t m1, float* __restrict__ A, int64_t lda, double* __restrict__ tau,
+    float* __restrict__ Wg, float* __restrict__ wh, float* __restrict__ wl, int* flag, const Status* st)
 {
     if (status_error(st)) return;
     if (*(volatile const int*)flag) return;
-    extern __shared__ double cqr_lu_sm[];
-    double(*U)[kCqrMaxB + 1] = reinterpret_cast<double(*)[kCqrMaxB + 1]>(cqr_lu_sm);
-    double* sgn = cqr_lu_sm + kCqrMaxB * (kCqrMaxB + 1);
-    float* sRh = reinterpret_cast<float*>(sgn + kCqrMaxB);
-    float* sRl = sRh + kCqrMaxB * kCqrMaxB;
-    float* sri = sRl + kCqrMaxB * kCqrMaxB;
-    float(*Xq)[kCqrMaxB + 1] = reinterpret_cast<float(*)[kCqrMaxB + 1]>(sri + kCqrMaxB);
-    const int tid = threadIdx.x;
-    for (int e = tid; e < bb * bb; e += kCqrSmallThreads) {
-        sRh[(e / bb) * kCqrMaxB + e % bb] = R2h[(e / bb) * kCqrMaxB + e % bb];
-        sRl[(e / bb) * kCqrMaxB + e % bb] = R2l[(e / bb) * kCqrMaxB + e % bb];
-        Xq[e % bb][e / bb] = Q1[(int64_t)(e / bb) * m1 + e % bb];
+    extern __shared__ __align__(16) unsigned char cqr_s2_raw[];
+    Small2Smem& S = *reinterpret_cast<Small2Smem*>(cqr_s2_raw);
+    const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+    const int ne = bb * (bb + 1) / 2, nsq = bb * bb;
+    build_tri_table(S.tri, bb);
+    build_sq_table(S.sq, bb);
+    __syncthreads();
+    for (int e = tid; e < ne; e += kSmallThreads) {
+        const uint16_t t = S.tri[e];
+        const int i = tab_r(t), c = tab_c(t);
+        const df v = df_of(Gpk[e]);
+        S.H[i][c] = v.h;
+        S.L[i][c] = v.l;
+        if (i == c) S.d0[i] = v.h;
     }
-    for (int e = tid; e < bb; e += kCqrSmallThreads) sri[e] = r2inv[e];
     __syncthreads();
-    // Q2 rows = Q1 rows R2^{-1} (row solves; the FP32 result is what the rows below see too)
-    if (tid < bb) row_solve(Xq[tid], Xq[tid], bb, sRh, sRl, kCqrMaxB, sri);
+    if (!df_cholesky(S.H, S.L, bb, S.tri, S.d0, 0.5f, S.rs)) {
+        if (tid == 0) *flag = 1;
+        return;
+    }
+    // R2 in FP32 (padded) for the row solve, E = R2 - I, R1 in FP32; the reciprocal pairs of R2's diagonal
+    for (int e = tid; e < kCqrMaxB * kCqrMaxB; e += kSmallThreads) {
+        const int i = e >> 6, j = e & (kCqrMaxB - 1);
+        const bool in = i <= j && j < bb;
+        S.R2f[e] = in ? S.H[i][j] : 0.f;
+        S.E[i][j] = in ? (S.H[i][j] - (i == j ? 1.f : 0.f)) + S.L[i][j] : 0.f;
+        S.R1[i][j] = in ? R1h[i * kCqrMaxB + j] : 0.f;
+    }
+    if (tid < kCqrMaxB) {
+        const df r = tid < bb ? df_rcp({S.H[tid][tid], S.L[tid][tid]}) : df{1.f, 0.f};
+        S.r2h[tid] = r.h;
+        S.r2l[tid] = r.l;
+    }
     __syncthreads();
-    for (int e = tid; e < bb * bb; e += kCqrSmallThreads) U[e / bb][e % bb] = (double)Xq[e / bb][e % bb];
+    // Q2top rows = Q1top rows R2^{-1}, one row per thread
+    if (tid < bb) {
+        float x[kCqrMaxB];
+#pragma unroll
+        for (int c = 0; c < kCqrMaxB; ++c) x[c] = c < bb ? Q1[(int64_t)c * m1 + tid] : 0.f;
+        row_solve_regs(x, S.R2f, S.r2h, S.r2l);
+#pragma unroll
+        for (int c = 0; c < kCqrMaxB; ++c) {
+            S.UH[tid][c] = x[c];
+            S.UL[tid][c] = 0.f;
+        }
+    }
     __syncthreads();
-    // LU of Q2top - S, right-looking, FP64; the sign is chosen at each pivot
+    // LU of Q2top - S in pairs, right-looking: step j subtracts U(r, j) U(j, c) / piv_j from every
+    // (r, c) with r, c > j (dealt out evenly through the shell table), one barrier per step; the
+    // pivots and the scaling of column j into L(:, j) are applied after the last step
     for (int j = 0; j < bb; ++j) {
+        const df a = {S.UH[j][j], S.UL[j][j]};
+        const float s = a.h >= 0.f ? -1.f : 1.f;
+        const df piv = df_add(a, {-s, 0.f});
+        const df rp = df_rcp(piv);
         if (tid == 0) {
-            const double s = U[j][j] >= 0.0 ? -1.0 : 1.0;
-            sgn[j] = s;
-            U[j][j] -= s;
+            S.pvh[j] = piv.h;
+            S.pvl[j] = piv.l;
+            S.rph[j] = rp.h;
+            S.rpl[j] = rp.l;
+            S.sgn[j] = s;
+        }
+        for (int e = sq_start(j + 1, bb) + tid; e < nsq; e += kSmallThreads) {
+            const uint16_t t = S.sq[e];
+            const int r = tab_r(t), c = tab_c(t);
+            const df l = df_mul({S.UH[r][j], S.UL[r][j]}, rp);
+            const df v = df_fms({S.UH[r][c], S.UL[r][c]}, l, {S.UH[j][c], S.UL[j][c]});
+            S.UH[r][c] = v.h;
+            S.UL[r][c] = v.l;
         }
         __syncthreads();
-        const double piv = U[j][j];
-        const double rp = 1.0 / piv;
-        for (int r = j + 1 + tid; r < bb; r += kCqrSmallThreads) U[r][j] *= rp;
-        __syncthreads();
-        const int w = bb - j - 1;
-        for (int e = tid; e < w * w; e += kCqrSmallThreads) {
-            const int r = j + 1 + e / w, c = j + 1 + e % w;
-            U[r][c] -= U[r][j] * U[j][c];
+    }
+    if (tx < bb)
+        for (int r = ty; r < bb; r += kSmallThreads / 64) {
+            if (r == tx) {
+                S.UH[r][tx] = S.pvh[tx];
+                S.UL[r][tx] = S.pvl[tx];
+            } else if (r > tx) {
+                const df v = df_mul({S.UH[r][tx], S.UL[r][tx]}, {S.rph[tx], S.rpl[tx]});
+                S.UH[r][tx] = v.h;
+                S.UL[r][tx] = v.l;
+            }
         }
-        __syncthreads();
-    }
-    // tau, the panel's top rows, and W = U R2 (upper x upper) as float pairs
-    for (int j = tid; j < bb; j += kCqrSmallThreads) tau[j] = -sgn[j] * U[j][j];
-    for (int e = tid; e < bb * bb; e += kCqrSmallThreads) {
-        const int i = e / bb, j = e % bb;
-        const float v = i <= j ? (float)(sgn[i] * Rprod[i * kCqrMaxB + j]) : (float)U[i][j];
-        A[(int64_t)j * lda + i] = v;
-        double w = 0.0;
-        for (int q = i; q <= j; ++q) w += U[i][q] * R2[q * kCqrMaxB + j];
-        w = i <= j ? w : 0.0;
-        const float h = (float)w;
-        Wh[i * kCqrMaxB + j] = h;
-        Wl[i * kCqrMaxB + j] = (float)(w - (double)h);
-        if (i == j) winv[i] = (float)(1.0 / w);
-    }
+    __syncthreads();
+    // tau, the panel's top rows (R_house = S R2 R1 above, L1 below the diagonal) and W = U R2.
+    // R2 = I + E with E at the level of Q1's departure from orthogonality (FP32 rounding), so
+    // R2 R1 = R1 + E R1 and U R2 = U + U E: the leading terms stay float pairs and the small
+    // corrections are plain FP32 sums.
+    if (tid < bb) tau[tid] = -(double)S.sgn[tid] * df_dbl({S.pvh[tid], S.pvl[tid]});
+    if (tx < bb)
+        for (int i = ty; i < bb; i += kSmallThreads / 64) {
+            const int j = tx;
+            float out;
+            if (i <= j) {
+                float cr = 0.f, cw = 0.f;
+                for (int q = i; q <= j; ++q) {
+                    cr = fmaf(S.E[i][q], S.R1[q][j], cr);
+                    cw = fmaf(S.UH[i][q], S.E[q][j], cw);
+                }
+                const df r = df_add({R1h[i * kCqrMaxB + j], R1l[i * kCqrMaxB + j]}, {cr, 0.f});
+                const df w = df_add({S.UH[i][j], S.UL[i][j]}, {cw, 0.f});
+                out = S.sgn[i] * (r.h + r.l);
+                Wg[i * kCqrMaxB + j] = w.h + w.l;
+                if (i == j) {
+                    const df wr = df_rcp(w);
+                    wh[i] = wr.h;
+                    wl[i] = wr.l;
+                }
+            } else {
+                out = S.UH[i][j] + S.UL[i][j];
+            }
+            A[(int64_t)j * lda + i] = out;
+        }
 }
 
-// Rows r >= bb of the panel: V(r, :) = Q1(r, :) (U R2)^{-1}, one row per thread.
-__global__ void __launch_bounds__(kCqrThreads) cqr_vform_kernel(const float* __restrict__ Q1, int64_t m1, int bb,
-                                                                const float* __restrict__ Wh,
-                                                                const float* __restrict__ Wl,
-                                                                const float* __restrict__ winv, float* __restrict__ A,
-                                                                int64_t lda, const int* flag, const Status* st)
-{
-    if (status_error(st)) return;
-    if (*(volatile const int*)flag) return;
-    extern __shared__ float cqr_v_sm[];
-    float(*X)[kCqrMaxB + 1] = reinterpret_cast<float(*)[kCqrMaxB + 1]>(cqr_v_sm);  // kCqrThreads rows
-    float* sWh = cqr_v_sm + kCqrThreads * (kCqrMaxB + 1);
-    float* sWl = sWh + kCqrMaxB * kCqrMaxB;
-    float* swi = sWl + kCqrMaxB * kCqrMaxB;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < bb * bb; e += kCqrThreads) {
-        sWh[(e / bb) * kCqrMaxB + e % bb] = Wh[(e / bb) * kCqrMaxB + e % bb];
-        sWl[(e / bb) * kCqrMaxB + e % bb] = Wl[(e / bb) * kCqrMaxB + e % bb];
-    }
-    for (int e = tid; e < bb; e += kCqrThreads) swi[e] = winv[e];
-    const int64_t rb0 = bb + (int64_t)blockIdx.x * kCqrThreads;
-    const int nr = (int)min((int64_t)kCqrThreads, m1 - rb0);
-    for (int e = tid; e < nr * bb; e += kCqrThreads) {
-        const int r = e % nr, c = e / nr;
-        X[r][c] = Q1[(int64_t)c * m1 + rb0 + r];
-    }
-    __syncthreads();
-    if (tid < nr) row_solve(X[tid], X[tid], bb, sWh, sWl, kCqrMaxB, swi);
-    __syncthreads();
-    for (int e = tid; e < nr * bb; e += kCqrThreads) {
-        const int r = e % nr, c = e / nr;
-        A[(int64_t)c * lda + rb0 + r] = X[r][c];
-    }
-}
-
-constexpr size_t kGramSmem = sizeof(float) * ((size_t)kCqrRows * (kCqrMaxB + 1) + 2 * kCqrMaxB * kCqrMaxB + kCqrMaxB);
-constexpr size_t kVformSmem = sizeof(float) * ((size_t)kCqrThreads * (kCqrMaxB + 1) + 2 * kCqrMaxB * kCqrMaxB + kCqrMaxB);
-constexpr size_t kLuSmem = sizeof(double) * ((size_t)kCqrMaxB * (kCqrMaxB + 1) + kCqrMaxB) +
-                           sizeof(float) * (2 * kCqrMaxB * kCqrMaxB + kCqrMaxB + (size_t)kCqrMaxB * (kCqrMaxB + 1));
-
-}  // namespace
+constexpr size_t kSmall2Smem = sizeof(Small2Smem);
 
 // Regions of the CholeskyQR2 workspace for an m1-row panel, each 256-byte aligned, in this order:
-// partial Grams, reduced Gram, R1, R2, R2 R1 (FP64), R1, R2, U R2 as float pairs, three reciprocal
-// vectors, Q1 (m1 x 64 FP32), the fallback flag.
+// partial Grams, reduced Gram, R1 as float pairs, W = U R2 in FP32, the reciprocal pairs of their
+// diagonals, Q1 (m1 x 64 FP32), the fallback flag.
+constexpr int kCqrRegions = 9;
 size_t cholqr_region_bytes(int i, int64_t m1)
 {
     const int64_t nblk = (m1 + kCqrRows - 1) / kCqrRows;
     switch (i) {
     case 0: return sizeof(double) * (size_t)nblk * kCqrNE;
     case 1: return sizeof(double) * kCqrNE;
-    case 2: case 3: case 4: return sizeof(double) * kCqrMaxB * kCqrMaxB;
-    case 5: case 6: case 7: case 8: case 9: case 10: return sizeof(float) * kCqrMaxB * kCqrMaxB;
-    case 11: case 12: case 13: return sizeof(float) * kCqrMaxB;
-    case 14: return sizeof(float) * (size_t)m1 * kCqrMaxB;
+    case 2: case 3: case 4: return sizeof(float) * kCqrMaxB * kCqrMaxB;
+    case 5: case 6: return 2 * sizeof(float) * kCqrMaxB;
+    case 7: return sizeof(float) * (size_t)m1 * kCqrMaxB;
     default: return 256;
     }
 }
-constexpr int kCqrRegions = 16;
+
+}  // namespace
 
 size_t cholqr_ws_bytes(int64_t m_max)
 {
@@ -366,51 +553,41 @@ cudaError_t launch_cholqr_panel(float* A, int64_t lda, int64_t m1, int bb, doubl
     }
     double* part = reinterpret_cast<double*>(reg[0]);
     double* G = reinterpret_cast<double*>(reg[1]);
-    double* R1 = reinterpret_cast<double*>(reg[2]);
-    double* R2 = reinterpret_cast<double*>(reg[3]);
-    double* Rp = reinterpret_cast<double*>(reg[4]);
-    float* R1h = reinterpret_cast<float*>(reg[5]);
-    float* R1l = reinterpret_cast<float*>(reg[6]);
-    float* R2h = reinterpret_cast<float*>(reg[7]);
-    float* R2l = reinterpret_cast<float*>(reg[8]);
-    float* Wh = reinterpret_cast<float*>(reg[9]);
-    float* Wl = reinterpret_cast<float*>(reg[10]);
-    float* r1i = reinterpret_cast<float*>(reg[11]);
-    float* r2i = reinterpret_cast<float*>(reg[12]);
-    float* wi = reinterpret_cast<float*>(reg[13]);
-    float* Q1 = reinterpret_cast<float*>(reg[14]);
-    int* flag = reinterpret_cast<int*>(reg[15]);
+    float* R1h = reinterpret_cast<float*>(reg[2]);
+    float* R1l = reinterpret_cast<float*>(reg[3]);
+    float* W = reinterpret_cast<float*>(reg[4]);
+    float* r1h = reinterpret_cast<float*>(reg[5]);
+    float* r1l = r1h + kCqrMaxB;
+    float* wrh = reinterpret_cast<float*>(reg[6]);
+    float* wrl = wrh + kCqrMaxB;
+    float* Q1 = reinterpret_cast<float*>(reg[7]);
+    int* flag = reinterpret_cast<int*>(reg[8]);
     *flag_out = flag;
     const int ne = bb * (bb + 1) / 2;
-    const unsigned rb = (unsigned)((ne + 127) / 128);
+    const unsigned rb = (unsigned)((ne + 31) / 32);
+    const unsigned sb = (unsigned)((m1 + kSolveThreads - 1) / kSolveThreads);
     static DevFlag attr_set;
     if (!attr_set.done()) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)cqr_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kGramSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void*)cqr_vform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kVformSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void*)cqr_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLuSmem);
+        const cudaError_t e = cudaFuncSetAttribute((const void*)cqr_small2_kernel,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall2Smem);
         if (e != cudaSuccess) return e;
         attr_set.set();
     }
     // pass 1
-    cqr_gram_kernel<<<nblk, kCqrThreads, kGramSmem, s>>>(A, lda, m1, bb, nullptr, nullptr, nullptr, nullptr, part, flag,
-                                                        st);
-    cqr_reduce_kernel<<<rb, 128, 0, s>>>(part, nblk, ne, G, flag, 1, st);
-    cqr_chol_kernel<<<1, kCqrSmallThreads, 0, s>>>(G, bb, 1, R1, R1h, R1l, r1i, nullptr, nullptr, flag, st);
-    // pass 2 (Q1 = P R1^{-1} fused with its Gram)
-    cqr_gram_kernel<<<nblk, kCqrThreads, kGramSmem, s>>>(A, lda, m1, bb, R1h, R1l, r1i, Q1, part, flag, st);
-    cqr_reduce_kernel<<<rb, 128, 0, s>>>(part, nblk, ne, G, flag, 2, st);
-    cqr_chol_kernel<<<1, kCqrSmallThreads, 0, s>>>(G, bb, 2, R2, R2h, R2l, r2i, R1, Rp, flag, st);
-    // Householder reconstruction
-    cqr_lu_kernel<<<1, kCqrSmallThreads, kLuSmem, s>>>(Q1, m1, bb, R2h, R2l, r2i, R2, Rp, A, lda, tau, Wh, Wl, wi,
-                                                        flag, st);
+    cqr_gram_kernel<<<nblk, kGramThreads, 0, s>>>(A, lda, m1, bb, part, flag, 1, st);
+    cqr_reduce_kernel<<<rb, 32 * kRedWarps, 0, s>>>(part, nblk, ne, G, flag, 1, st);
+    cqr_small1_kernel<<<1, kSmallThreads, 0, s>>>(G, bb, R1h, R1l, r1h, r1l, flag, st);
+    // pass 2: Q1 = P R1^{-1}, its Gram
+    cqr_solve_kernel<<<sb, kSolveThreads, 0, s>>>(A, lda, Q1, m1, 0, m1, bb, R1h, r1h, r1l, flag, st);
+    cqr_gram_kernel<<<nblk, kGramThreads, 0, s>>>(Q1, m1, m1, bb, part, flag, 2, st);
+    cqr_reduce_kernel<<<rb, 32 * kRedWarps, 0, s>>>(part, nblk, ne, G, flag, 2, st);
+    // R2, R = R2 R1, the reconstruction and the panel's top rows
+    cqr_small2_kernel<<<1, kSmallThreads, kSmall2Smem, s>>>(G, bb, R1h, R1l, Q1, m1, A, lda, tau, W, wrh, wrl, flag,
+                                                           st);
+    // the rows below: V2 = Q1 W^{-1}
     if (m1 > bb)
-        cqr_vform_kernel<<<(unsigned)((m1 - bb + kCqrThreads - 1) / kCqrThreads), kCqrThreads, kVformSmem, s>>>(
-            Q1, m1, bb, Wh, Wl, wi, A, lda, flag, st);
+        cqr_solve_kernel<<<(unsigned)((m1 - bb + kSolveThreads - 1) / kSolveThreads), kSolveThreads, 0, s>>>(
+            Q1, m1, A, lda, bb, m1 - bb, bb, W, wrh, wrl, flag, st);
     return cudaGetLastError();
 }
 
