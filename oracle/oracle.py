@@ -75,6 +75,11 @@ def _load():
         lib.orc_rqrcp2.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _i64, _dp, ctypes.c_int, ctypes.c_int,
                                    _i32p, _dp, _i64p, _dp, _dp]
         lib.orc_rqrcp2.restype = ctypes.c_int
+        lib.orc_rqrcp3.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _i64, _dp, ctypes.c_int, ctypes.c_int,
+                                   _i64p, _i64, _i32p, _dp, _i64p, _dp, _dp]
+        lib.orc_rqrcp3.restype = ctypes.c_int
+        lib.orc_tournament.argtypes = [_dp, _i64, _i64, _i64, _i64, _i64, _i64, _i64p, _dp]
+        lib.orc_tournament.restype = ctypes.c_int64
         lib.orc_round_bf16.argtypes = [_i64, _dp, _dp]
         lib.orc_round_bf16.restype = None
         lib.orc_form_q.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
@@ -138,13 +143,32 @@ class RQRCPResult:
         self.A, self.jpvt, self.tau, self.rank, self.gaps, self.B = A, jpvt, tau, rank, gaps, B
 
 
+def tournament(X: np.ndarray, bb: int, gs: int, fanin: int = 4, pos0: int = 0):
+    """QR with tournament pivoting on the l x nc matrix X (column s has position pos0 + s):
+    leaves of gs consecutive columns, fan-in `fanin`, every choice Alg. 1 with ties to the
+    smallest position.  Returns (the min(bb, nc) chosen positions in order, the smallest
+    relative gap of all choices)."""
+    lib = _load()
+    Xf = _fortran64(X)
+    l, nc = Xf.shape
+    sel = np.zeros(max(bb, 1), dtype=np.int64)
+    gap = np.zeros(1, dtype=np.float64)
+    ns = lib.orc_tournament(_ptr(Xf, ctypes.c_double), l, nc, pos0, bb, gs, fanin, _ptr(sel, ctypes.c_int64),
+                            _ptr(gap, ctypes.c_double))
+    if ns < 0:
+        raise ValueError("orc_tournament: invalid arguments")
+    return sel[:ns], float(gap[0])
+
+
 def rqrcp(A: np.ndarray, k: int, b: int, p: int, Omega: np.ndarray, formula: int = 4,
-          sketch_bf16: bool = False) -> RQRCPResult:
+          sketch_bf16: bool = False, tgs=None, fanin: int = 4) -> RQRCPResult:
     """Alg. 2 (RQRCP) with the sketch Omega given explicitly (l x m, l = b + p).
 
     formula=4 updates B with Eq. (4) (Duersch-Gu), formula=5 with Eq. (5) (Martinsson et al.).
     sketch_bf16: the mixed form's BF16 sketch (Omega and A rounded to FP32 then BF16 for the
     initial B = Omega A only; exact products and FP64 sums).
+    tgs: None for the partial QRCP of Alg. 2; else QR with tournament pivoting on B, tgs[q] the
+    leaf group size of block q (an int gives every block the same size) with fan-in `fanin`.
     """
     lib = _load()
     Af = _fortran64(A)
@@ -158,18 +182,28 @@ def rqrcp(A: np.ndarray, k: int, b: int, p: int, Omega: np.ndarray, formula: int
     rank = np.zeros(1, dtype=np.int64)
     gaps = np.zeros(max(k, 1), dtype=np.float64)
     B = np.zeros((l, n), dtype=np.float64, order="F")
-    rc = lib.orc_rqrcp2(m, n, _ptr(Af, ctypes.c_double), max(m, 1), k, b, p, _ptr(Om, ctypes.c_double),
-                        formula, 1 if sketch_bf16 else 0, _ptr(jpvt, ctypes.c_int32), _ptr(tau, ctypes.c_double),
-                        _ptr(rank, ctypes.c_int64), _ptr(gaps, ctypes.c_double), _ptr(B, ctypes.c_double))
+    nblk = (k + b - 1) // b
+    if tgs is None:
+        tg = None
+        tgp = ctypes.POINTER(ctypes.c_int64)()
+    else:
+        tg = np.array([tgs] * nblk if np.isscalar(tgs) else list(tgs), dtype=np.int64)
+        if tg.shape != (nblk,):
+            raise ValueError(f"tgs needs {nblk} group sizes")
+        tgp = _ptr(tg, ctypes.c_int64)
+    rc = lib.orc_rqrcp3(m, n, _ptr(Af, ctypes.c_double), max(m, 1), k, b, p, _ptr(Om, ctypes.c_double),
+                        formula, 1 if sketch_bf16 else 0, tgp, fanin, _ptr(jpvt, ctypes.c_int32),
+                        _ptr(tau, ctypes.c_double), _ptr(rank, ctypes.c_int64), _ptr(gaps, ctypes.c_double),
+                        _ptr(B, ctypes.c_double))
     if rc != 0:
         raise ValueError(f"orc_rqrcp: error {rc}")
     return RQRCPResult(Af, jpvt, tau[:k], int(rank[0]), gaps[:k], B)
 
 
 def rqrcp_seeded(A: np.ndarray, k: int, b: int, p: int, seed: int, formula: int = 4,
-                 sketch_bf16: bool = False) -> RQRCPResult:
+                 sketch_bf16: bool = False, tgs=None, fanin: int = 4) -> RQRCPResult:
     """Alg. 2 with Omega drawn from the seed by the oracle's own Philox generator."""
-    return rqrcp(A, k, b, p, omega(b + p, A.shape[0], seed), formula, sketch_bf16)
+    return rqrcp(A, k, b, p, omega(b + p, A.shape[0], seed), formula, sketch_bf16, tgs, fanin)
 
 
 # --------------------------------------------------------------------------- Alg. 3

@@ -45,6 +45,14 @@
  *    the column now at position l, whose entries below row l are zero.  The swap loop is
  *    capped at max_swaps (the paper only states that it ends), and skipped when the RQRCP
  *    stage's rank guard fired before l pivots (R_hat is then singular to working precision).
+ *  - QR with tournament pivoting on B (the paper's future work, Sec. VI; orc_tournament and
+ *    orc_rqrcp3 with group sizes): the leaves are consecutive groups of gs columns of B(:, i:n)
+ *    in their positions at the start of the block; a node concatenates the choices of fanin
+ *    consecutive groups in group order, each group's choices in the order they were taken, and
+ *    reads them from B as it was at the start of the block; every choice is Alg. 1 on rows
+ *    0..l-1 of its candidates with ties to the smallest position.  The block's pivots are the
+ *    root's choices in their order; the rank guard tests the norm^2 of the chosen column's
+ *    trailing rows at its step (against the same bound as the greedy search).
  */
 #include <math.h>
 #include <stdint.h>
@@ -199,6 +207,102 @@ ORC_EXPORT int orc_qrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
 }
 
 /* ------------------------------------------------------------------------- */
+/* One selection of QR with tournament pivoting (Demmel, Grigori, Gu, Xiang,    */
+/* "Communication avoiding rank revealing QR factorization with column          */
+/* pivoting", SIAM J. Matrix Anal. Appl. 36 (2015)): Alg. 1 for `steps` steps   */
+/* on the nc candidate columns X(:, cand[s] - pos0) (l rows, ld l), copied to   */
+/* W first; the squared norms of rows t..l-1 are recomputed at every step and   */
+/* the largest wins, ties to the smallest position cand[s].  out[t] = the       */
+/* position chosen at step t; *mingap is lowered to (nu_max - nu_second) /      */
+/* nu_max of every step (1.0 with a single candidate, 0.0 if nu_max is 0).      */
+/* ------------------------------------------------------------------------- */
+static void tour_select(const double* X, int64_t l, int64_t pos0, const int64_t* cand, int64_t nc,
+                        int64_t steps, int64_t* out, double* mingap, double* W, char* act)
+{
+    for (int64_t s = 0; s < nc; ++s) {
+        memcpy(&AT(W, l, 0, s), &AT(X, l, 0, cand[s] - pos0), sizeof(double) * (size_t)l);
+        act[s] = 1;
+    }
+    for (int64_t t = 0; t < steps; ++t) {
+        int64_t best = -1;
+        double v1 = -1.0, v2 = -1.0;
+        for (int64_t s = 0; s < nc; ++s) {
+            if (!act[s]) continue;
+            double nu = 0.0;
+            for (int64_t r = t; r < l; ++r) nu += AT(W, l, r, s) * AT(W, l, r, s);
+            if (best < 0 || nu > v1 || (nu == v1 && cand[s] < cand[best])) {
+                if (best >= 0) v2 = v1;
+                v1 = nu;
+                best = s;
+            } else if (nu > v2) {
+                v2 = nu;
+            }
+        }
+        const double gap = v2 < 0.0 ? 1.0 : (v1 > 0.0 ? (v1 - v2) / v1 : 0.0);
+        if (gap < *mingap) *mingap = gap;
+        out[t] = cand[best];
+        act[best] = 0;
+        double* x = &AT(W, l, t, best);
+        const double tb = house_gen(l - t, x);
+        for (int64_t s = 0; s < nc; ++s)
+            if (act[s]) house_apply(l - t, x, tb, &AT(W, l, t, s));
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* QR with tournament pivoting, the choice of bb of the nc columns of X (l x nc, */
+/* ld l; column s has position pos0 + s): leaves are the consecutive groups of   */
+/* gs columns, each choosing min(bb, its size) columns by tour_select; while     */
+/* more than one group is left, each run of fanin consecutive groups becomes one */
+/* group that chooses min(bb, candidates) of its children's choices              */
+/* (concatenated in child order), read from X.  sel[0..min(bb, nc)) receives     */
+/* the last group's choices in their order; returns that count, or -1.          */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT int64_t orc_tournament(const double* X, int64_t l, int64_t nc, int64_t pos0, int64_t bb, int64_t gs,
+                                  int64_t fanin, int64_t* sel, double* mingap)
+{
+    if (l < 1 || nc < 1 || bb < 1 || gs < 1 || fanin < 2) return -1;
+    int64_t P = (nc + gs - 1) / gs;
+    int64_t* ch = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P * bb));   /* choices per group */
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)P);
+    int64_t* nch = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P * bb));
+    int64_t* ncnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)P);
+    int64_t* cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)(fanin * bb > gs ? fanin * bb : gs));
+    const int64_t wcols = fanin * bb > gs ? fanin * bb : gs;
+    double* W = (double*)malloc(sizeof(double) * (size_t)(l * wcols));
+    char* act = (char*)malloc((size_t)wcols);
+    if (!ch || !cnt || !nch || !ncnt || !cand || !W || !act) {
+        free(ch); free(cnt); free(nch); free(ncnt); free(cand); free(W); free(act);
+        return -1;
+    }
+    double gap = 1.0;
+    for (int64_t g = 0; g < P; ++g) {   /* leaves */
+        const int64_t c0 = g * gs, c1 = (g + 1) * gs < nc ? (g + 1) * gs : nc;
+        for (int64_t s = c0; s < c1; ++s) cand[s - c0] = pos0 + s;
+        cnt[g] = bb < c1 - c0 ? bb : c1 - c0;
+        tour_select(X, l, pos0, cand, c1 - c0, cnt[g], &ch[g * bb], &gap, W, act);
+    }
+    while (P > 1) {                     /* one level of the reduction tree */
+        const int64_t P2 = (P + fanin - 1) / fanin;
+        for (int64_t q = 0; q < P2; ++q) {
+            int64_t nc2 = 0;
+            for (int64_t g = q * fanin; g < (q + 1) * fanin && g < P; ++g)
+                for (int64_t t = 0; t < cnt[g]; ++t) cand[nc2++] = ch[g * bb + t];
+            ncnt[q] = bb < nc2 ? bb : nc2;
+            tour_select(X, l, pos0, cand, nc2, ncnt[q], &nch[q * bb], &gap, W, act);
+        }
+        memcpy(ch, nch, sizeof(int64_t) * (size_t)(P2 * bb));
+        memcpy(cnt, ncnt, sizeof(int64_t) * (size_t)P2);
+        P = P2;
+    }
+    const int64_t ns = cnt[0];
+    memcpy(sel, ch, sizeof(int64_t) * (size_t)ns);
+    if (mingap) *mingap = gap;
+    free(ch); free(cnt); free(nch); free(ncnt); free(cand); free(W); free(act);
+    return ns;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Alg. 2: randomized QRCP.                                                    */
 /*   formula == 4 : B updated by Eq. (4) (Duersch-Gu), in place, after the      */
 /*                  partial QRCP on B has transformed it.                       */
@@ -217,6 +321,10 @@ ORC_EXPORT int orc_qrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k,
 ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
                           int64_t p, const double* Omega, int formula, int sketch_bf16, int32_t* jpvt,
                           double* tau, int64_t* rank_out, double* gaps, double* Bout);
+ORC_EXPORT int orc_rqrcp3(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
+                          int64_t p, const double* Omega, int formula, int sketch_bf16, const int64_t* tgs,
+                          int64_t fanin, int32_t* jpvt, double* tau, int64_t* rank_out, double* gaps,
+                          double* Bout);
 
 ORC_EXPORT int orc_rqrcp(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
                          int64_t p, const double* Omega, int formula, int32_t* jpvt, double* tau,
@@ -230,12 +338,26 @@ ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t 
                           int64_t p, const double* Omega, int formula, int sketch_bf16, int32_t* jpvt,
                           double* tau, int64_t* rank_out, double* gaps, double* Bout)
 {
+    return orc_rqrcp3(m, n, A, lda, k, b, p, Omega, formula, sketch_bf16, NULL, 0, jpvt, tau, rank_out, gaps,
+                      Bout);
+}
+
+/* orc_rqrcp2 with the pivot rule: tgs == NULL the partial QRCP of Alg. 2 (Alg. 1 on B); else QR  */
+/* with tournament pivoting on B (formula 4 only), tgs[q] the leaf group size of block q (the     */
+/* block starting at column q*b) and fanin the tree's fan-in.  gaps[c] of a tournament block is   */
+/* the smallest gap of all the choices the block's tournament made.                               */
+ORC_EXPORT int orc_rqrcp3(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b,
+                          int64_t p, const double* Omega, int formula, int sketch_bf16, const int64_t* tgs,
+                          int64_t fanin, int32_t* jpvt, double* tau, int64_t* rank_out, double* gaps,
+                          double* Bout)
+{
     if (m < 1 || n < 1) return -1;
     if (lda < m) return -4;
     if (k < 1 || k > (m < n ? m : n)) return -5;
     if (b < 1) return -6;
     if (p < 0) return -7;
     if (formula != 4 && formula != 5) return -9;
+    if (tgs && (formula != 4 || fanin < 2)) return -11;
     const int64_t l = b + p;
     double* B = (double*)malloc(sizeof(double) * (size_t)(l * n));
     double* Bq = (double*)malloc(sizeof(double) * (size_t)(l * n));   /* QRCP copy (formula 5) */
@@ -293,18 +415,46 @@ ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t 
         if (pivoting) {
             double* Q = B;
             if (formula == 5) { memcpy(Bq, B, sizeof(double) * (size_t)(l * n)); Q = Bq; }
+            /* tournament: the block's pivots chosen up front from B(:, i:n) as it is now; who[]
+               and where[] follow the transpositions (position -> original position and back) */
+            int64_t* tsel = NULL;
+            int64_t* who = NULL;
+            int64_t* where = NULL;
+            double tgap = 1.0;
+            if (tgs) {
+                tsel = (int64_t*)malloc(sizeof(int64_t) * (size_t)bb);
+                who = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+                where = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+                if (!tsel || !who || !where ||
+                    orc_tournament(&AT(Q, l, 0, i), l, n - i, i, bb, tgs[i / b], fanin, tsel, &tgap) != bb) {
+                    free(tsel); free(who); free(where); free(B); free(Bq); free(Wh); free(Ob);
+                    return 1;
+                }
+                for (int64_t j = 0; j < n; ++j) who[j] = where[j] = j;
+            }
             for (int64_t t = 0; t < bb; ++t) {
                 const int64_t c = i + t;
                 int64_t best = c;
                 double v1 = -1.0, v2 = -1.0;
-                for (int64_t s = c; s < n; ++s) {
-                    double nu = 0.0;
-                    for (int64_t r = t; r < l; ++r) nu += AT(Q, l, r, s) * AT(Q, l, r, s);
-                    if (nu > v1) { v2 = v1; v1 = nu; best = s; }
-                    else if (nu > v2) v2 = nu;
+                if (tgs) {
+                    best = where[tsel[t]];
+                    v1 = 0.0;
+                    for (int64_t r = t; r < l; ++r) v1 += AT(Q, l, r, best) * AT(Q, l, r, best);
+                } else {
+                    for (int64_t s = c; s < n; ++s) {
+                        double nu = 0.0;
+                        for (int64_t r = t; r < l; ++r) nu += AT(Q, l, r, s) * AT(Q, l, r, s);
+                        if (nu > v1) { v2 = v1; v1 = nu; best = s; }
+                        else if (nu > v2) v2 = nu;
+                    }
                 }
                 if (v1 <= guard) { pivoting = 0; rank = c; break; }
-                if (gaps) gaps[c] = (v2 < 0.0) ? 1.0 : (v1 - v2) / v1;
+                if (gaps) gaps[c] = tgs ? tgap : ((v2 < 0.0) ? 1.0 : (v1 - v2) / v1);
+                if (tgs) {   /* the transposition c <-> best in the position maps */
+                    const int64_t oc = who[c], ob = who[best];
+                    who[c] = ob; who[best] = oc;
+                    where[ob] = c; where[oc] = best;
+                }
                 /* Alg. 2 "Swap ... columns in A, Pi" (and in B). */
                 swap_cols(A, lda, m, c, best);
                 swap_cols(B, l, l, c, best);
@@ -317,6 +467,7 @@ ORC_EXPORT int orc_rqrcp2(int64_t m, int64_t n, double* A, int64_t lda, int64_t 
                 for (int64_t s = c + 1; s < n; ++s) house_apply(l - t, x, tb, &AT(Q, l, t, s));
                 for (int64_t r = t + 1; r < l; ++r) x[r - t] = 0.0; /* R_hat is upper */
             }
+            free(tsel); free(who); free(where);
         }
 
         /* --- Alg. 2 "unpivoted QR on A(i:m, i:i+b-1)" --- */
