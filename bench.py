@@ -441,10 +441,10 @@ class Form:
     """One form of the factorization (plain FP64 or mixed) on one matrix, with its device
     buffers and the sketching matrix Omega on the device (the seeded draw, made once)."""
 
-    def __init__(self, prec, A0, w, dev):
+    def __init__(self, prec, A0, w, dev, pivot="greedy"):
         import torch
         from paper_1804_05138_gb300 import binding
-        self.prec, self.w, self.dev = prec, w, dev
+        self.prec, self.w, self.dev, self.pivot = prec, w, dev, pivot
         m, n, k, b, p = w["m"], w["n"], w["k"], w["b"], w["p"]
         self.mixed = prec == "mixed"
         self.A0 = A0
@@ -462,6 +462,14 @@ class Form:
         the host draw of Omega; else Omega already on the device)."""
         from paper_1804_05138_gb300 import binding
         k, b, p = self.w["k"], self.w["b"], self.w["p"]
+        if self.pivot == "tournament":  # QR with tournament pivoting on B, automatic leaf groups
+            om = None if seeded else self.omega
+            if self.mixed:
+                return binding.rqrcp_factor_mixed_tournament(self.A, k, b, p, 0, binding.RQRCP_SKETCH_BF16, 0,
+                                                             self.jpvt, self.tau, self.work, stream, Omega=om,
+                                                             rank_out=self.rank)
+            return binding.rqrcp_factor_tournament(self.A, k, b, p, 0, om, 0, self.jpvt, self.tau, self.work, stream,
+                                                   rank_out=self.rank)
         if self.mixed:
             om = None if seeded else self.omega
             return binding.rqrcp_factor_mixed_ex(self.A, k, b, p, 0, binding.RQRCP_SKETCH_BF16, self.jpvt, self.tau,
@@ -599,6 +607,8 @@ def run_ours(args, w, rank, world, local_rank):
                                                hbm_src, fp64_peak, fp64_src)
     if not diff:
         extra["accuracy"] = acc
+    if mixed and not diff and not args.no_tournament:
+        extra["tournament"] = run_tournament_extra(args, w, A0, dev, stream, ms_per_step, acc, hbm_peak, fp64_peak)
     if args.srqr and not mixed and not diff:
         extra["srqr"] = run_srqr_extra(args, w, A0, dev, stream)
 
@@ -751,6 +761,31 @@ def run_other_form(args, w, Agen, other, dev, stream, value_ms, value_acc, hbm_p
            "kernels": kernels, "gpu_launches": gpu_launch_count(prof, other == "mixed") + steps}
     if other == "mixed":
         out["lowrank_reorth"] = reorth_extra(form, w, dev, stream)
+    del form
+    if other == "mixed" and not args.no_tournament:
+        out["tournament"] = run_tournament_extra(args, w, A0, dev, stream, oms, acc, hbm_peak, fp64_peak)
+    return out
+
+
+def run_tournament_extra(args, w, A0, dev, stream, greedy_ms, greedy_acc, hbm_peak, fp64_peak):
+    """The same form with QR with tournament pivoting on B in place of Alg. 2's partial QRCP:
+    time, the pivot search's time per pivot against the greedy search's, accuracy."""
+    k, b = w["k"], w["b"]
+    mixed = A0.element_size() == 4
+    form = Form("mixed" if mixed else "fp64", A0, w, dev, pivot="tournament")
+    steps = max(3, args.steps) if mixed else 3
+    ms, prof = form.timed(stream, steps, 2)
+    tms = sum(ms) / len(ms)
+    kernels = kernel_rooflines(prof, "mixed" if mixed else "fp64", hbm_peak, fp64_peak,
+                               steps_per_launch=k / ((k + b - 1) // b))
+    acc = form.accuracy(A0)
+    out = {"pivot": "tournament (leaf groups max(2b, (n-i)/SMs), fan-in 4)", "ms_per_step": round(tms, 3),
+           "steps": steps, "value": round(counted_flops(w["m"], w["n"], k, b + w["p"]) / (tms * 1e-3) / 1e9, 3),
+           "unit": "GFLOP/s", "greedy_ms": round(greedy_ms, 3), "speedup_over_greedy": round(greedy_ms / tms, 4),
+           "pivot_us_per_step": kernels.get("pivot", {}).get("us_per_step"), "accuracy": acc,
+           "r22_ratio_vs_greedy": (round(acc["r22_over_sigma_k1"] / greedy_acc["r22_over_sigma_k1"], 4)
+                                   if "r22_over_sigma_k1" in acc and "r22_over_sigma_k1" in greedy_acc else None),
+           "kernel_time_share": {kname: v["share"] for kname, v in kernels.items()}}
     del form
     return out
 
@@ -1001,6 +1036,8 @@ def main():
                     help="plain FP64 workloads: also time SRQR (Alg. 3) to rank L on the same matrix")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other form (mixed / plain FP64) on the same matrix")
+    ap.add_argument("--no-tournament", action="store_true",
+                    help="skip the mixed form with QR with tournament pivoting on the sketch (extra.tournament)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -195,6 +195,42 @@ int rqrcp_factor_mixed_ex(int64_t m, int64_t n, float* A, int64_t lda, int64_t k
                           int64_t* rank_out, void* work, size_t work_bytes, void* stream);
 
 /*
+ * QR with tournament pivoting on the sketch in place of Alg. 2's partial QRCP on B (the paper's
+ * future work, Sec. VI: "QR with tournament pivoting in place of partial QRCP"; Demmel, Grigori,
+ * Gu and Xiang, SIAM J. Matrix Anal. Appl. 36 (2015)).  For each block of bb = min(b, k - i)
+ * pivots the n - i trailing sketch columns are split into leaf groups of G consecutive columns;
+ * each leaf chooses min(bb, its size) columns by bb greedy steps of Alg. 1 (squared norms of the
+ * trailing rows recomputed at every step, the largest first, ties to the smallest position); each
+ * node of a tree with fan-in F chooses min(bb, candidates) of its children's choices the same way,
+ * reading the children's columns as they were at the start of the block, concatenated in child
+ * order; the root's choices, in their order, are the block's pivots.  The rank guard tests each
+ * chosen column's trailing squared norm at its step against the bound of the corresponding
+ * greedy entry point.  Everything else (panel, compact-WY update, Eq. (4)) is as in rqrcp_factor
+ * (FP64) or rqrcp_factor_mixed_ex (FP32); the workspace is the same.  group_cols: 0 for
+ * G = max(2b, ceil((n - i) / SMs)), lowered to the largest group one SM holds; > 0 for G =
+ * group_cols (at least b).  F = 4, or 2 when four blocks of candidates do not fit one SM.
+ * Errors: as rqrcp_factor_ex with -11 group_cols < 0 (FP64 form); as rqrcp_factor_mixed_ex with
+ * -12 group_cols < 0 and -13 jpvt, -14 tau (FP32 form); RQRCP_ERR_UNSUPPORTED when b + p > 256
+ * or a group does not fit one SM's shared memory.
+ */
+int rqrcp_factor_tournament(int64_t m, int64_t n, double* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                            uint64_t seed, const double* Omega, int64_t ldo, int64_t group_cols, int32_t* jpvt,
+                            double* tau, int64_t* rank_out, void* work, size_t work_bytes, void* stream);
+int rqrcp_factor_mixed_tournament(int64_t m, int64_t n, float* A, int64_t lda, int64_t k, int64_t b, int64_t p,
+                                  uint64_t seed, const float* Omega, int64_t ldo, int sketch, int64_t group_cols,
+                                  int32_t* jpvt, double* tau, int64_t* rank_out, void* work, size_t work_bytes,
+                                  void* stream);
+
+/* The leaf group size G and the fan-in F that the tournament entry points use for a block of bb
+ * pivots (block size b, oversampling p) over ncols trailing columns of elem_bytes-byte elements
+ * (8: FP64 form, 4: FP32 form), with the caller's group_cols (0: automatic).  Host only; reads the
+ * current device's SM count and shared-memory size.  Errors: -1 ncols < 1, -2 bb not in
+ * [1, ncols], -3 b not in [bb, 128], -4 p < 0, -5 elem_bytes, -6 group_cols < 0, -7/-8 NULL
+ * outputs; RQRCP_ERR_UNSUPPORTED as above. */
+int rqrcp_tournament_config(int64_t ncols, int64_t bb, int64_t b, int64_t p, int elem_bytes, int64_t group_cols,
+                            int64_t* group_out, int64_t* fanin_out);
+
+/*
  * Synchronises `stream`, then reads the device-side status left in `work` by the last
  * factorization: returns RQRCP_OK, RQRCP_ERR_NONFINITE or RQRCP_ERR_TIMEOUT (or
  * RQRCP_ERR_CUDA if the synchronisation itself fails) and stores the rank (number of

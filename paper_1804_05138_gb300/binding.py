@@ -39,7 +39,8 @@ ABI_SYMBOLS = (
     "rqrcp_sketch_noalloc", "rqrcp_lowrank_f32", "rqrcp_backward_workspace_size", "rqrcp_backward",
     "rqrcp_backward_f32", "rqrcp_reorth_workspace_size", "rqrcp_lowrank_reorth",
     "rqrcp_batched_workspace_size", "rqrcp_factor_batched", "rqrcp_factor_ex",
-    "rqrcp_srqr_workspace_size", "rqrcp_srqr", "rqrcp_peak_probe",
+    "rqrcp_srqr_workspace_size", "rqrcp_srqr", "rqrcp_peak_probe", "rqrcp_factor_tournament",
+    "rqrcp_factor_mixed_tournament", "rqrcp_tournament_config",
 )
 RQRCP_PROFILE_CLASSES = 14
 
@@ -84,6 +85,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                   _sz, _vp]),
             "rqrcp_factor_mixed_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64,
                                                      ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "rqrcp_factor_tournament": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64,
+                                                       _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "rqrcp_factor_mixed_tournament": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _i64, _u64, _vp,
+                                                             _i64, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "rqrcp_tournament_config": (ctypes.c_int, [_i64, _i64, _i64, _i64, ctypes.c_int, _i64,
+                                                       ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "rqrcp_read_status": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
             "rqrcp_lowrank_workspace_size": (_sz, [_i64, _i64, _i64]),
             "rqrcp_lowrank": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp,
@@ -236,6 +243,31 @@ def rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream=None
                                         _ptr(tau), _ptr(rank_out), _ptr(work), work.numel(), _stream(stream))
 
 
+def rqrcp_factor_tournament(A, k, b, p, seed, Omega, group_cols, jpvt, tau, work, stream=None,
+                            rank_out=None) -> int:
+    m, n = A.shape
+    om, ldo = (None, 0) if Omega is None else (_ptr(Omega), _ld_rowmajor(Omega))
+    return load().rqrcp_factor_tournament(m, n, _ptr(A), _ld(A), k, b, p, seed, om, ldo, group_cols, _ptr(jpvt),
+                                          _ptr(tau), _ptr(rank_out), _ptr(work), work.numel(), _stream(stream))
+
+
+def rqrcp_factor_mixed_tournament(A, k, b, p, seed, sketch, group_cols, jpvt, tau, work, stream=None, Omega=None,
+                                  rank_out=None) -> int:
+    m, n = A.shape
+    om, ldo = (None, 0) if Omega is None else (_ptr(Omega), _ld_rowmajor(Omega))
+    return load().rqrcp_factor_mixed_tournament(m, n, _ptr(A), _ld(A), k, b, p, seed, om, ldo, sketch, group_cols,
+                                                _ptr(jpvt), _ptr(tau), _ptr(rank_out), _ptr(work), work.numel(),
+                                                _stream(stream))
+
+
+def rqrcp_tournament_config(ncols, bb, b, p, elem_bytes, group_cols=0) -> tuple[int, int]:
+    """(leaf group size, fan-in) that the tournament entry points use for one block."""
+    g, f = _i64(0), _i64(0)
+    _check(load().rqrcp_tournament_config(ncols, bb, b, p, elem_bytes, group_cols, ctypes.byref(g), ctypes.byref(f)),
+           "rqrcp_tournament_config")
+    return int(g.value), int(f.value)
+
+
 def rqrcp_read_status(work, stream=None) -> tuple[int, int]:
     rank = _i64(0)
     code = load().rqrcp_read_status(_ptr(work), ctypes.byref(rank), _stream(stream))
@@ -385,7 +417,8 @@ class Factorization:
     k: int
 
 
-def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETCH_BF16, formula=RQRCP_UPDATE_EQ4):
+def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETCH_BF16, formula=RQRCP_UPDATE_EQ4,
+                tournament=None):
     import torch
     m, n = A.shape
     dev = A.device
@@ -396,7 +429,13 @@ def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETC
         raise ValueError("invalid factorization arguments")
     if work is None or work.numel() < need:
         work = workspace(need, dev)
-    if mixed:
+    if tournament is not None:
+        if mixed:
+            code = rqrcp_factor_mixed_tournament(A, k, b, p, seed, sketch, tournament, jpvt, tau, work, stream,
+                                                 Omega=omega)
+        else:
+            code = rqrcp_factor_tournament(A, k, b, p, seed, omega, tournament, jpvt, tau, work, stream)
+    elif mixed:
         code = rqrcp_factor_mixed_ex(A, k, b, p, seed, sketch, jpvt, tau, work, stream, Omega=omega)
     elif formula != RQRCP_UPDATE_EQ4:
         code = rqrcp_factor_ex(A, k, b, p, seed, omega, formula, jpvt, tau, work, stream)
@@ -411,10 +450,12 @@ def _run_factor(A, k, b, p, seed, omega, mixed, work, stream, sketch=RQRCP_SKETC
 
 
 def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=None, stream=None,
-           overwrite: bool = False, formula: int = 4) -> Factorization:
+           overwrite: bool = False, formula: int = 4, tournament=None) -> Factorization:
     """Randomized QRCP of a float64 CUDA matrix (plain FP64 form).  ``omega`` (row-major
     (b+p) x m float64 CUDA tensor) replaces the seeded sketch when given.  ``formula``: 4 updates
-    the sketch between blocks with Eq. (4) (Duersch-Gu), 5 with Eq. (5) (Martinsson et al.)."""
+    the sketch between blocks with Eq. (4) (Duersch-Gu), 5 with Eq. (5) (Martinsson et al.).
+    ``tournament``: None for Alg. 2's partial QRCP on B, else QR with tournament pivoting on B
+    with that leaf group size (0: automatic; rqrcp_factor_tournament)."""
     import torch
     if A.dtype != torch.float64:
         raise TypeError("factor expects float64; use factor_mixed for float32")
@@ -423,7 +464,9 @@ def factor(A, k: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, work=N
         Acm = Acm.t().clone().t()
     if formula not in (RQRCP_UPDATE_EQ4, RQRCP_UPDATE_EQ5):
         raise ValueError("formula must be 4 or 5")
-    return _run_factor(Acm, k, b, p, seed, omega, False, work, stream, formula=formula)
+    if tournament is not None and formula != RQRCP_UPDATE_EQ4:
+        raise ValueError("tournament pivoting runs with Eq. (4) only")
+    return _run_factor(Acm, k, b, p, seed, omega, False, work, stream, formula=formula, tournament=tournament)
 
 
 class SRQRFactorization:
@@ -461,11 +504,12 @@ def srqr(A, l: int, b: int = 64, p: int = 8, seed: int = 0, omega=None, g: float
 
 
 def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, stream=None,
-                 overwrite: bool = False, sketch: str = "bf16", omega=None) -> Factorization:
+                 overwrite: bool = False, sketch: str = "bf16", omega=None, tournament=None) -> Factorization:
     """Randomized QRCP of a float32 CUDA matrix (mixed form, FP64 reflectors).
 
     sketch: "bf16" (operands rounded to BF16, FP32 accumulation) or "fp32" (FP32-level sketch).
     omega: optional row-major (b+p) x m float32 CUDA tensor replacing the seeded sketch.
+    tournament: None, or the leaf group size of QR with tournament pivoting on B (0: automatic).
     """
     import torch
     if A.dtype != torch.float32:
@@ -476,7 +520,7 @@ def factor_mixed(A, k: int, b: int = 64, p: int = 16, seed: int = 0, work=None, 
     if not overwrite:
         Acm = Acm.t().clone().t()
     return _run_factor(Acm, k, b, p, seed, omega, True, work, stream,
-                       RQRCP_SKETCH_BF16 if sketch == "bf16" else RQRCP_SKETCH_FP32)
+                       RQRCP_SKETCH_BF16 if sketch == "bf16" else RQRCP_SKETCH_FP32, tournament=tournament)
 
 
 def lowrank(f: Factorization, stream=None):

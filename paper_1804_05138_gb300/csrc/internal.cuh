@@ -245,6 +245,18 @@ cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb,
                          int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s);
 size_t pivot_cand_bytes(int l);
 
+// QR with tournament pivoting on B(:, i:n) in place of the partial QRCP (the same outputs as
+// launch_pivot: B transformed and permuted, jpvt, piv, the swap map).  tournament_config gives the
+// leaf group size and the fan-in for a block with ncols trailing columns (group_cols 0: automatic;
+// > 0: that size, at least b), or false when the block does not fit one SM.  ws: tournament_ws_bytes.
+bool tournament_config(int64_t ncols, int bb, int64_t b, int l, int elem_bytes, int64_t group_cols, int64_t* gs_out,
+                       int* fanin_out);
+size_t tournament_ws_bytes(int64_t n, int l, int64_t b, int elem_bytes);
+template <typename T>
+cudaError_t launch_tournament(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int64_t b, int64_t gs,
+                              int fanin, int32_t* jpvt, int32_t* piv, void* ws, long long* swapmap, T* tmp,
+                              double guard_rel2, Status* st, cudaStream_t s);
+
 // Column swaps of A following the net column map written by the pivot kernel
 // (swapmap[0] = count, then (destination, source) position pairs); tmp holds 2*bb columns.
 template <typename T>

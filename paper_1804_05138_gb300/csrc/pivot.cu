@@ -15,42 +15,13 @@
 // applies the transpositions to jpvt and records the net column map used to swap A.
 // Rank guard: if the best remaining norm^2 is not above guard_rel2 * (largest initial
 // sketch norm^2), pivoting stops for good at this step.
-#include <climits>
-
-#include "internal.cuh"
+#include "pivot_common.cuh"
 
 namespace rq {
 namespace {
 
 constexpr int kMaxCand = 1024;  // maximum blocks of the cooperative launch
-
-// Order key of a squared norm: non-negative doubles order as their bit patterns read as signed
-// 64-bit integers, and every negative value (the "no candidate" -1.0) maps below them.  Integer
-// compares keep the argmax off the FP64 pipe; the order is that of the values.
-__device__ __forceinline__ long long norm_key(double v)
-{
-    const long long b = __double_as_longlong(v);
-    return b < 0 ? -1LL : b;
-}
-
-__device__ __forceinline__ bool better(double v1, long long p1, double v2, long long p2)
-{
-    const long long k1 = norm_key(v1), k2 = norm_key(v2);
-    return k1 > k2 || (k1 == k2 && p1 < p2);
-}
-
-// Warp-wide argmax over (value, position, index) triples by shuffles; every lane ends with the
-// warp's winner.
-__device__ __forceinline__ void warp_argmax(double& v, long long& p, int& idx)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const long long op = __shfl_xor_sync(0xffffffffu, p, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (better(ov, op, v, p)) { v = ov; p = op; idx = oi; }
-    }
-}
+constexpr int kMaxBB = 128;     // largest block size b the factorizations accept
 
 // Block-wide argmax: warp shuffles, then warp 0 reduces the warps' winners (slots 0..31 of the
 // shared arrays); the result goes through slot 32, which the next call writes only after its
@@ -70,14 +41,6 @@ __device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long
     }
     __syncthreads();
     v = sv[32]; p = sp[32]; idx = si[32];
-}
-
-// Per-column reduction over the TPC threads that share a column (adjacent lanes).
-template <typename T>
-__device__ __forceinline__ T column_sum(T v, int tpc)
-{
-    for (int o = 1; o < tpc; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 template <typename T>
@@ -111,7 +74,10 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     off += (size_t)bb * sizeof(long long);
     int* active = reinterpret_cast<int*>(smem_raw + off);
     off += (size_t)cpb * sizeof(int);
-    double* nus = reinterpret_cast<double*>(smem_raw + ((off + 7) & ~(size_t)7));
+    off = (off + 7) & ~(size_t)7;
+    double* nus = reinterpret_cast<double*>(smem_raw + off);
+    off += (size_t)cpb * sizeof(double);
+    void* fin_scr = smem_raw + off;  // finish_pivots scratch (block 0)
 
     __shared__ double red_v[33];
     __shared__ long long red_p[33];
@@ -274,31 +240,8 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     if (g == 0) {
         for (int t = steps + tid; t < bb; t += NTH) pivs[t] = i + t;
         __syncthreads();
-        for (int t = tid; t < bb; t += NTH) piv[t] = (int32_t)pivs[t];
-        if (tid == 0) {
-            // jpvt: apply the transpositions in order.  swapmap: net map of the moved positions
-            // (count, then pairs (destination position, source position)).
-            long long cnt = 0;
-            long long* mp = swapmap + 1;
-            for (int t = 0; t < bb; ++t) {
-                const long long a = i + t, b2 = pivs[t];
-                if (a == b2) continue;
-                const int32_t tj = jpvt[a];
-                jpvt[a] = jpvt[b2];
-                jpvt[b2] = tj;
-                long long ia = -1, ib = -1;
-                for (long long e = 0; e < cnt; ++e) {
-                    if (mp[2 * e] == a) ia = e;
-                    if (mp[2 * e] == b2) ib = e;
-                }
-                if (ia < 0) { mp[2 * cnt] = a; mp[2 * cnt + 1] = a; ia = cnt++; }
-                if (ib < 0) { mp[2 * cnt] = b2; mp[2 * cnt + 1] = b2; ib = cnt++; }
-                const long long tmp = mp[2 * ia + 1];
-                mp[2 * ia + 1] = mp[2 * ib + 1];
-                mp[2 * ib + 1] = tmp;
-            }
-            swapmap[0] = cnt;
-        }
+        // jpvt, piv and the net column map (count, then (destination, source) pairs)
+        finish_pivots(i, bb, pivs, jpvt, piv, swapmap, fin_scr);
     }
 }
 
@@ -318,6 +261,7 @@ size_t pivot_smem(int64_t cpb, int l, int bb)
     off += (size_t)bb * sizeof(long long) + (size_t)cpb * sizeof(int);
     off = (off + 7) & ~(size_t)7;
     off += (size_t)cpb * sizeof(double);
+    off += finish_scratch_bytes(bb);
     return off;
 }
 
@@ -334,7 +278,7 @@ bool pivot_fits(int64_t ncols, int l, int elem_bytes)
     const int64_t G = dev_info().sms;
     const int64_t cpb = (ncols + G - 1) / G;
     if (cpb > 1024) return false;
-    const size_t need = elem_bytes == 8 ? pivot_smem<double>(cpb, l, 1024) : pivot_smem<float>(cpb, l, 1024);
+    const size_t need = elem_bytes == 8 ? pivot_smem<double>(cpb, l, kMaxBB) : pivot_smem<float>(cpb, l, kMaxBB);
     return need <= (size_t)dev_info().max_smem_optin - 2048;
 }
 

@@ -91,7 +91,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, total;
+    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, tp, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
@@ -125,6 +125,8 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     }
     // FP32 form: the CholeskyQR2 panel's partial Grams, factors and Q1 (m x 64)
     L.cqr = take(esz == sizeof(float) ? cholqr_ws_bytes(m) : 0);
+    // QR with tournament pivoting: the tree's choices, the root's reflectors and R_hat columns
+    L.tp = take(tournament_ws_bytes(n, (int)l, b, (int)esz));
     L.total = off;
     return L;
 }
@@ -196,7 +198,7 @@ template <typename T>
 int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, int64_t p, uint64_t seed,
                 const T* Omega_user, int64_t ldo, int32_t* jpvt, double* tau, int64_t* rank_out, void* work,
                 size_t work_bytes, cudaStream_t s, int sketch_bf16 = 0, int formula = RQRCP_UPDATE_EQ4,
-                bool final_b = false)
+                bool final_b = false, int64_t tp_group = -1)
 {
     const int64_t l = b + p;
     const Layout L = make_layout(m, n, b, p, sizeof(T));
@@ -219,6 +221,17 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     T* Bc = reinterpret_cast<T*>(w + L.Bc);
     const bool eq5 = formula == RQRCP_UPDATE_EQ5;
     if (eq5 && sizeof(T) != sizeof(double)) return RQRCP_ERR_UNSUPPORTED;
+    // tp_group >= 0: QR with tournament pivoting on B (Eq. (4) only); every block must fit one SM
+    const bool tourn = tp_group >= 0;
+    if (tourn) {
+        if (eq5) return RQRCP_ERR_UNSUPPORTED;
+        for (int64_t i = 0; i < k; i += b) {
+            int64_t gs;
+            int fan;
+            if (!tournament_config(n - i, (int)(b < k - i ? b : k - i), b, (int)l, (int)sizeof(T), tp_group, &gs, &fan))
+                return RQRCP_ERR_UNSUPPORTED;
+        }
+    }
 
     RQ_CHECK(launch_init(st, k, jpvt, n, s));
     const double es = (double)sizeof(T);
@@ -266,8 +279,17 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     for (int64_t i = 0; i < k; i += b) {
         const int bb = (int)(b < k - i ? b : k - i);
         const double np = (double)(n - i);
-        RQ_LAUNCH(K_PIVOT, 4.0 * l * np * bb, 2.0 * l * np * es,
-                  launch_pivot<T>(B, l, (int)l, n, i, bb, jpvt, piv, cand, guard_rel2, st, s));
+        if (tourn) {
+            int64_t gs;
+            int fan;
+            tournament_config(n - i, bb, b, (int)l, (int)sizeof(T), tp_group, &gs, &fan);
+            RQ_LAUNCH(K_PIVOT, 4.0 * l * np * bb, 2.0 * l * np * es,
+                      launch_tournament<T>(B, l, (int)l, n, i, bb, b, gs, fan, jpvt, piv, w + L.tp,
+                                           const_cast<long long*>(swapmap), tmp, guard_rel2, st, s));
+        } else {
+            RQ_LAUNCH(K_PIVOT, 4.0 * l * np * bb, 2.0 * l * np * es,
+                      launch_pivot<T>(B, l, (int)l, n, i, bb, jpvt, piv, cand, guard_rel2, st, s));
+        }
         RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * m * es, launch_swaps<T>(A, lda, m, bb, swapmap, tmp, st, s));
         if (eq5 && i + bb < k)  // the same column moves on the untransformed sketch
             RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * l * es, launch_swaps<T>(Bc, l, l, bb, swapmap, tmp, st, s));
@@ -671,6 +693,58 @@ __attribute__((visibility("default"))) int rqrcp_factor_mixed_ex(int64_t m, int6
     if (sketch != RQRCP_SKETCH_BF16 && sketch != RQRCP_SKETCH_FP32) return -11;
     return factor_impl<float>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, rank_out,
                               work, work_bytes, (cudaStream_t)stream, sketch == RQRCP_SKETCH_BF16 ? 1 : 0);
+}
+
+__attribute__((visibility("default"))) int rqrcp_tournament_config(int64_t ncols, int64_t bb, int64_t b, int64_t p,
+                                                                   int elem_bytes, int64_t group_cols,
+                                                                   int64_t* group_out, int64_t* fanin_out)
+{
+    if (ncols < 1) return -1;
+    if (bb < 1 || bb > ncols) return -2;
+    if (b < bb || b > 128) return -3;
+    if (p < 0) return -4;
+    if (elem_bytes != 4 && elem_bytes != 8) return -5;
+    if (group_cols < 0) return -6;
+    if (group_out == nullptr) return -7;
+    if (fanin_out == nullptr) return -8;
+    int64_t gs;
+    int fan;
+    if (!tournament_config(ncols, (int)bb, b, (int)(b + p), elem_bytes, group_cols, &gs, &fan))
+        return RQRCP_ERR_UNSUPPORTED;
+    *group_out = gs;
+    *fanin_out = fan;
+    return RQRCP_OK;
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_tournament(int64_t m, int64_t n, double* A, int64_t lda,
+                                                                   int64_t k, int64_t b, int64_t p, uint64_t seed,
+                                                                   const double* Omega, int64_t ldo,
+                                                                   int64_t group_cols, int32_t* jpvt, double* tau,
+                                                                   int64_t* rank_out, void* work, size_t work_bytes,
+                                                                   void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 3 : e;
+    if (Omega != nullptr && ldo < m) return -10;
+    if (group_cols < 0) return -11;
+    return factor_impl<double>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, rank_out,
+                               work, work_bytes, (cudaStream_t)stream, 0, RQRCP_UPDATE_EQ4, false, group_cols);
+}
+
+__attribute__((visibility("default"))) int rqrcp_factor_mixed_tournament(int64_t m, int64_t n, float* A, int64_t lda,
+                                                                         int64_t k, int64_t b, int64_t p,
+                                                                         uint64_t seed, const float* Omega,
+                                                                         int64_t ldo, int sketch, int64_t group_cols,
+                                                                         int32_t* jpvt, double* tau,
+                                                                         int64_t* rank_out, void* work,
+                                                                         size_t work_bytes, void* stream)
+{
+    if (int e = validate_factor(m, n, A, lda, k, b, p, jpvt, tau)) return e <= -9 ? e - 4 : e;
+    if (Omega != nullptr && ldo < m) return -10;
+    if (sketch != RQRCP_SKETCH_BF16 && sketch != RQRCP_SKETCH_FP32) return -11;
+    if (group_cols < 0) return -12;
+    return factor_impl<float>(m, n, A, lda, k, b, p, seed, Omega, Omega != nullptr ? ldo : 0, jpvt, tau, rank_out,
+                              work, work_bytes, (cudaStream_t)stream, sketch == RQRCP_SKETCH_BF16 ? 1 : 0,
+                              RQRCP_UPDATE_EQ4, false, group_cols);
 }
 
 __attribute__((visibility("default"))) int rqrcp_read_status(const void* work, int64_t* rank, void* stream)

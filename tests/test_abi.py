@@ -88,6 +88,32 @@ def test_factor_argument_codes(lib):
     assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, None, None, None, 0, None) == -13
     assert x(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 5, fake, fake, None, None, 0, None) == 4  # no workspace
     assert x(5, 5, fake, 5, 2, 1, 0, 0, fake, 5, 4, fake, fake, None, None, 0, None) == 4
+    tf = lib.rqrcp_factor_tournament
+    #             m  n  A    lda k  b  p  seed Omega ldo group jpvt tau rank work bytes stream
+    assert tf(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 0, fake, fake, None, None, 0, None) == -10
+    assert tf(5, 5, fake, 5, 2, 1, 0, 0, None, 0, -1, fake, fake, None, None, 0, None) == -11
+    assert tf(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, None, fake, None, None, 0, None) == -12
+    assert tf(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, fake, None, None, None, 0, None) == -13
+    assert tf(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, fake, fake, None, None, 0, None) == 4  # no workspace
+    tm = lib.rqrcp_factor_mixed_tournament
+    #             m  n  A    lda k  b  p  seed Omega ldo sketch group jpvt tau rank work bytes stream
+    assert tm(5, 5, fake, 5, 2, 1, 0, 0, fake, 4, 0, 0, fake, fake, None, None, 0, None) == -10
+    assert tm(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 2, 0, fake, fake, None, None, 0, None) == -11
+    assert tm(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, -1, fake, fake, None, None, 0, None) == -12
+    assert tm(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, 0, None, fake, None, None, 0, None) == -13
+    assert tm(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 0, 0, fake, None, None, None, 0, None) == -14
+    assert tm(5, 5, fake, 5, 2, 1, 0, 0, None, 0, 1, 0, fake, fake, None, None, 0, None) == 4  # no workspace
+    tc = lib.rqrcp_tournament_config
+    g64, f64 = ctypes.c_int64(0), ctypes.c_int64(0)
+    #          ncols bb  b   p  bytes group  out
+    assert tc(0, 1, 1, 0, 8, 0, ctypes.byref(g64), ctypes.byref(f64)) == -1
+    assert tc(10, 11, 16, 0, 8, 0, ctypes.byref(g64), ctypes.byref(f64)) == -2
+    assert tc(10, 4, 2, 0, 8, 0, ctypes.byref(g64), ctypes.byref(f64)) == -3
+    assert tc(10, 4, 4, -1, 8, 0, ctypes.byref(g64), ctypes.byref(f64)) == -4
+    assert tc(10, 4, 4, 0, 2, 0, ctypes.byref(g64), ctypes.byref(f64)) == -5
+    assert tc(10, 4, 4, 0, 8, -1, ctypes.byref(g64), ctypes.byref(f64)) == -6
+    assert tc(10, 4, 4, 0, 8, 0, None, ctypes.byref(f64)) == -7
+    assert tc(10, 4, 4, 0, 8, 0, ctypes.byref(g64), None) == -8
     sr = lib.rqrcp_srqr
     #      m  n  A    lda l  b  p  seed Omega ldo g    d  seed_g swaps jpvt info work bytes stream
     assert sr(1, 5, fake, 5, 1, 1, 0, 0, None, 0, 5.0, 8, 0, 10, fake, None, None, 0, None) == -1
