@@ -240,10 +240,16 @@ cudaError_t launch_reduce_y(const double* P, int nsplit, int64_t ncols, int64_t 
 
 // Cooperative pivot search on B(:, i:n) (bb steps of QRCP on the sketch).  `cand` is
 // pivot_cand_bytes(l) of candidate buffers followed by the swap map (1 + 4*bb int64).
+// launch_index: the pivot search's position among the call's pivot searches (0, 1, 2, ...):
+// consecutive searches use the two arrival counters at the head of `cand` in turn.
 template <typename T>
 cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int32_t* jpvt,
-                         int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s);
+                         int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s,
+                         int launch_index);
 size_t pivot_cand_bytes(int l);
+// The head of `cand`: the pivot searches' arrival counters, which must be zero before a
+// factorization's first pivot search.
+size_t pivot_slot_bytes();
 
 // QR with tournament pivoting on B(:, i:n) in place of the partial QRCP (the same outputs as
 // launch_pivot: B transformed and permuted, jpvt, piv, the swap map).  tournament_config gives the

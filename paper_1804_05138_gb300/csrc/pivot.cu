@@ -6,7 +6,9 @@
 //   1. every block finds its best column by squared norm of rows t..l-1 (recomputed, Alg. 1
 //      "Update r_s"), ties to the smallest current position, and publishes the value, the
 //      position and the whole column into a double-buffered candidate slot;
-//   2. one bounded grid barrier;
+//   2. each block then adds one to this launch's arrival counter (a release add) and waits,
+//      bounded, until the counter shows all G blocks of this step (no separate barrier word, no
+//      generation flip: one round trip less than a grid barrier);
 //   3. every block reads all candidates, picks the same winner, regenerates the same
 //      Householder reflector (xLARFG convention, FP64) from the winner's column and applies
 //      it to its own columns.  The swap "c <-> winner" is pure bookkeeping: the slot that
@@ -21,6 +23,7 @@ namespace rq {
 namespace {
 
 constexpr int kMaxCand = 1024;  // maximum blocks of the cooperative launch
+constexpr int kCounterBytes = 256;  // two arrival counters (launches alternate), zeroed per call
 constexpr int kMaxBB = 128;     // largest block size b the factorizations accept
 
 // Block-wide argmax: warp shuffles, then warp 0 reduces the warps' winners (slots 0..31 of the
@@ -49,7 +52,8 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
                                                      int32_t* __restrict__ jpvt, int32_t* __restrict__ piv,
                                                      long long* __restrict__ swapmap,
                                                      double* __restrict__ cval, long long* __restrict__ cpos,
-                                                     T* __restrict__ ccol, double guard_rel2, Status* st)
+                                                     T* __restrict__ ccol, unsigned long long* __restrict__ ctrs,
+                                                     int parity, double guard_rel2, Status* st)
 {
     if (status_error(st)) return;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, NTH = blockDim.x;
@@ -75,8 +79,6 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     int* active = reinterpret_cast<int*>(smem_raw + off);
     off += (size_t)cpb * sizeof(int);
     off = (off + 7) & ~(size_t)7;
-    double* nus = reinterpret_cast<double*>(smem_raw + off);
-    off += (size_t)cpb * sizeof(double);
     void* fin_scr = smem_raw + off;  // finish_pivots scratch (block 0)
 
     __shared__ double red_v[33];
@@ -101,7 +103,11 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     const int sub = tid % tpc;
     const int slots_per_pass = NTH / tpc;
     const int my_slot0 = tid / tpc;
-    // initial squared norms of rows 0..l-1 (recomputed from the rows, Alg. 1 "Update r_s")
+    // initial squared norms of rows 0..l-1 (recomputed from the rows, Alg. 1 "Update r_s"); each
+    // column's first thread keeps the best of its columns for step 0
+    double lbv = -1.0;
+    long long lbp = LLONG_MAX;
+    int lbs = -1;
     for (int sl = my_slot0; sl - my_slot0 < ((nloc + slots_per_pass - 1) / slots_per_pass) * slots_per_pass;
          sl += slots_per_pass) {
         T part = T(0);
@@ -110,23 +116,25 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
             for (int r = sub; r < l; r += tpc) part = fma(col[r], col[r], part);
         }
         part = column_sum(part, tpc);
-        if (sl < nloc && sub == 0) nus[sl] = (double)part;
+        if (sl < nloc && sub == 0 && better((double)part, pos[sl], lbv, lbp)) {
+            lbv = (double)part;
+            lbp = pos[sl];
+            lbs = sl;
+        }
     }
-    __syncthreads();
+    unsigned long long* ctr = ctrs + parity;
+    if (g == 0 && tid == 0) ctrs[parity ^ 1] = 0;  // the next launch's counter (this call's launches alternate)
+    __shared__ int s_ok;
     const double guard = guard_rel2 * __longlong_as_double((long long)st->nu0bits);
 
     int steps = bb;
     for (int t = 0; t < bb; ++t) {
         const long long c = i + t;
         const int buf = t & 1;
-        // 1. local candidate from the norms of rows t..l-1
-        double myv = -1.0;
-        long long myp = LLONG_MAX;
-        int mys = -1;
-        for (int s = tid; s < nloc; s += NTH) {
-            if (!active[s]) continue;
-            if (better(nus[s], pos[s], myv, myp)) { myv = nus[s]; myp = pos[s]; mys = s; }
-        }
+        // 1. the block's candidate from its threads' bests (norms of rows t..l-1)
+        double myv = lbv;
+        long long myp = lbp;
+        int mys = lbs;
         block_argmax(myv, myp, mys, red_v, red_p, red_i);
         if (tid == 0) {
             cval[buf * kMaxCand + g] = myv;
@@ -135,8 +143,29 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         if (mys >= 0)
             for (int r = tid; r < l; r += NTH)
                 ccol[((size_t)buf * kMaxCand + g) * l + r] = cols[(size_t)mys * ldS + r];
-        // 2. barrier
-        if (!grid_barrier(st)) return;
+        // 2. arrive, then wait until all G blocks of this step have arrived
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+            const unsigned long long want = (unsigned long long)G * (unsigned long long)(t + 1);
+            const unsigned long long t0 = globaltimer_ns();
+            int ok = 1;
+            while (ld_acquire_gpu(ctr) < want) {
+                const unsigned long long dt = globaltimer_ns() - t0;
+                if (dt > kErrorWatchNs && status_error(st)) {
+                    ok = 0;
+                    break;
+                }
+                if (dt > kWaitLimitNs) {
+                    set_error(st, RQRCP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
         // 3. global winner (identical in every block): warp 0 reads the G candidates, eight
         //    per lane in flight at a time, and reduces them; slot 32 broadcasts the result
         if (tid < 32) {
@@ -195,6 +224,9 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         // 4. apply H to every remaining column, then the norms of rows t+1..l-1 for step t+1
         const T tauT = (T)sh_tau;
         const bool apply = sh_tau != 0.0;
+        lbv = -1.0;
+        lbp = LLONG_MAX;
+        lbs = -1;
         for (int sl = my_slot0; sl - my_slot0 < ((nloc + slots_per_pass - 1) / slots_per_pass) * slots_per_pass;
              sl += slots_per_pass) {
             const bool mine = sl < nloc;
@@ -224,7 +256,11 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
                     pos[sl] = c;
                 } else {
                     if (pos[sl] == c) pos[sl] = wp;  // the column displaced by the swap
-                    nus[sl] = (double)nu;
+                    if (active[sl] && better((double)nu, pos[sl], lbv, lbp)) {
+                        lbv = (double)nu;
+                        lbp = pos[sl];
+                        lbs = sl;
+                    }
                 }
             }
             if (winner)  // becomes column c of R_hat
@@ -260,16 +296,18 @@ size_t pivot_smem(int64_t cpb, int l, int bb)
     off += ((size_t)l * sizeof(T) + 15) & ~(size_t)15;
     off += (size_t)bb * sizeof(long long) + (size_t)cpb * sizeof(int);
     off = (off + 7) & ~(size_t)7;
-    off += (size_t)cpb * sizeof(double);
     off += finish_scratch_bytes(bb);
     return off;
 }
 
 }  // namespace
 
+size_t pivot_slot_bytes() { return kCounterBytes; }
+
 size_t pivot_cand_bytes(int l)
 {
-    return 2 * (size_t)kMaxCand * (sizeof(double) + sizeof(long long)) + 2 * (size_t)kMaxCand * l * sizeof(double);
+    return kCounterBytes + 2 * (size_t)kMaxCand * (sizeof(double) + sizeof(long long)) +
+           2 * (size_t)kMaxCand * l * sizeof(double);
 }
 
 bool pivot_fits(int64_t ncols, int l, int elem_bytes)
@@ -284,7 +322,8 @@ bool pivot_fits(int64_t ncols, int l, int elem_bytes)
 
 template <typename T>
 cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb, int32_t* jpvt,
-                         int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s)
+                         int32_t* piv, void* cand, double guard_rel2, Status* st, cudaStream_t s,
+                         int launch_index)
 {
     static DevFlag attr_set;
     if (!attr_set.done()) {
@@ -309,23 +348,28 @@ cudaError_t launch_pivot(T* B, int64_t ldb, int l, int64_t n, int64_t i, int bb,
     if ((int64_t)per_sm * dev_info().sms < G) return cudaErrorCooperativeLaunchTooLarge;
 
     char* cb = static_cast<char*>(cand);
+    unsigned long long* ctrs = reinterpret_cast<unsigned long long*>(cb);
+    cb += kCounterBytes;
     double* cval = reinterpret_cast<double*>(cb);
     long long* cpos = reinterpret_cast<long long*>(cb + 2 * (size_t)kMaxCand * sizeof(double));
     T* ccol = reinterpret_cast<T*>(cb + 2 * (size_t)kMaxCand * (sizeof(double) + sizeof(long long)));
     // the swap map lives right after the candidate columns
-    long long* swapmap = reinterpret_cast<long long*>(cb + pivot_cand_bytes(l));
+    long long* swapmap = reinterpret_cast<long long*>(static_cast<char*>(cand) + pivot_cand_bytes(l));
     int bbv = bb;
     int lv = l;
     int64_t ldbv = ldb, nv = n, iv = i, cpbv = cpb;
     int tpcv = tpc;
     double gr = guard_rel2;
-    void* args[] = {&B, &ldbv, &lv, &nv, &iv, &bbv, &cpbv, &tpcv, &jpvt, &piv, &swapmap, &cval, &cpos, &ccol, &gr, &st};
+    // launches of one call alternate between the two counters (the call zeroes both first)
+    int parity = launch_index & 1;
+    void* args[] = {&B,    &ldbv, &lv,  &nv,   &iv,     &bbv, &cpbv, &tpcv, &jpvt,
+                    &piv,  &swapmap, &cval, &cpos, &ccol, &ctrs, &parity, &gr, &st};
     return cudaLaunchCooperativeKernel((const void*)pivot_kernel<T>, dim3((unsigned)G), dim3(threads), args, smem, s);
 }
 
 template cudaError_t launch_pivot<double>(double*, int64_t, int, int64_t, int64_t, int, int32_t*, int32_t*,
-                                          void*, double, Status*, cudaStream_t);
+                                          void*, double, Status*, cudaStream_t, int);
 template cudaError_t launch_pivot<float>(float*, int64_t, int, int64_t, int64_t, int, int32_t*, int32_t*,
-                                         void*, double, Status*, cudaStream_t);
+                                         void*, double, Status*, cudaStream_t, int);
 
 }  // namespace rq

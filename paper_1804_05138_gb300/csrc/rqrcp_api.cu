@@ -234,6 +234,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     }
 
     RQ_CHECK(launch_init(st, k, jpvt, n, s));
+    RQ_CHECK(cudaMemsetAsync(cand, 0, pivot_slot_bytes(), s));
     const double es = (double)sizeof(T);
     const T* Omega = Omega_user;
     if (Omega == nullptr) {
@@ -288,7 +289,7 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
                                            const_cast<long long*>(swapmap), tmp, guard_rel2, st, s));
         } else {
             RQ_LAUNCH(K_PIVOT, 4.0 * l * np * bb, 2.0 * l * np * es,
-                      launch_pivot<T>(B, l, (int)l, n, i, bb, jpvt, piv, cand, guard_rel2, st, s));
+                      launch_pivot<T>(B, l, (int)l, n, i, bb, jpvt, piv, cand, guard_rel2, st, s, (int)(i / b)));
         }
         RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * m * es, launch_swaps<T>(A, lda, m, bb, swapmap, tmp, st, s));
         if (eq5 && i + bb < k)  // the same column moves on the untransformed sketch
