@@ -239,8 +239,14 @@ __global__ void sketch_reduce_kernel(const double* __restrict__ P, int nsplit, i
 
 // One block per row r of T.  The rows of the forward columnwise recurrence are independent:
 // T(r,r) = tau_r and T(r,j) = -tau_j sum_{q=r}^{j-1} T(r,q) G(q,j), G = V^T V.  The block sums
-// G(r:bb, r:bb) from the split-K partials into shared memory; warp 0 runs the recurrence.
-__global__ void tform_kernel(const double* __restrict__ P, int nsplit, int64_t ncols, int bb,
+// G(r:bb, r:bb) from the split-K partials into shared memory (each thread keeps kTfEnt entries in
+// flight, the splits outermost, so a pass costs one memory round trip per split); warp 0 runs the
+// recurrence column by column: lane j mod 32 owns column j, finishes T(r,q)
+// at step q and broadcasts it, and every lane adds its terms to the columns it owns (one product,
+// one shuffle and one FMA per step).
+constexpr int kTfEnt = 16;      // G entries per thread in flight
+constexpr int kTfThreads = 256;
+__global__ void __launch_bounds__(kTfThreads) tform_kernel(const double* __restrict__ P, int nsplit, int64_t ncols, int bb,
                              const double* __restrict__ tau, double* __restrict__ Tm, const Status* st)
 {
     if (status_error(st)) return;
@@ -249,25 +255,51 @@ __global__ void tform_kernel(const double* __restrict__ P, int nsplit, int64_t n
     const int w = bb - r;
     double* Gs = sm;          // Gs[jj * w + qq] = G(r + qq, r + jj), qq < jj
     double* Tr = sm + w * w;  // T(r, r..bb-1)
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        const int qq = e % w, jj = e / w;
-        double s = 0.0;
-        if (qq < jj)
-            for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * ncols + r + jj) * bb + r + qq];
-        Gs[e] = s;
+    const int64_t stride = ncols * bb;
+    for (int e0 = 0; e0 < w * w; e0 += kTfEnt * (int)blockDim.x) {
+        double acc[kTfEnt];
+        int64_t off[kTfEnt];
+#pragma unroll
+        for (int u = 0; u < kTfEnt; ++u) {
+            const int e = e0 + u * (int)blockDim.x + (int)threadIdx.x;
+            const int qq = e % w, jj = e / w;
+            acc[u] = 0.0;
+            off[u] = (e < w * w && qq < jj) ? (int64_t)(r + jj) * bb + r + qq : -1;
+        }
+        for (int sp = 0; sp < nsplit; ++sp)
+#pragma unroll
+            for (int u = 0; u < kTfEnt; ++u)
+                if (off[u] >= 0) acc[u] += P[sp * stride + off[u]];
+#pragma unroll
+        for (int u = 0; u < kTfEnt; ++u) {
+            const int e = e0 + u * (int)blockDim.x + (int)threadIdx.x;
+            if (e < w * w) Gs[e] = acc[u];
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
+        constexpr int NJ = 4;  // columns per lane (bb <= 128)
         const int lane = threadIdx.x;
-        if (lane == 0) Tr[0] = tau[r];
-        __syncwarp();
-        for (int jj = 1; jj < w; ++jj) {
-            double s = 0.0;
-            for (int qq = lane; qq < jj; qq += 32) s += Tr[qq] * Gs[jj * w + qq];
+        double acc[NJ], tj[NJ];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) Tr[jj] = -tau[r + jj] * s;
-            __syncwarp();
+        for (int u = 0; u < NJ; ++u) {
+            const int jj = lane + 32 * u;
+            acc[u] = 0.0;
+            tj[u] = jj < w ? tau[r + jj] : 0.0;
+        }
+        for (int qq = 0; qq < w; ++qq) {
+            const int u0 = qq >> 5;
+            double x = 0.0;
+#pragma unroll
+            for (int u = 0; u < NJ; ++u)
+                if (u == u0) x = qq == 0 ? tj[u] : -tj[u] * acc[u];
+            x = __shfl_sync(0xffffffffu, x, qq & 31);
+            if (lane == (qq & 31)) Tr[qq] = x;
+#pragma unroll
+            for (int u = 0; u < NJ; ++u) {
+                const int jj = lane + 32 * u;
+                if (jj > qq && jj < w) acc[u] = fma(x, Gs[jj * w + qq], acc[u]);
+            }
         }
     }
     __syncthreads();
@@ -295,10 +327,19 @@ __global__ void reduce_y_kernel(const double* __restrict__ P, int nsplit, int64_
     double* Wc = Wsh + w * bb;
     for (int64_t c = (int64_t)blockIdx.x * nw + w; c < nc; c += (int64_t)gridDim.x * nw) {
         const int64_t col = c0 + c;
-        for (int q = lane; q < bb; q += 32) {
-            double s = 0.0;
-            for (int sp = 0; sp < nsplit; ++sp) s += P[((int64_t)sp * ncols + col) * bb + q];
-            Wc[q] = s;
+        for (int q = lane; q < bb; q += 32) {  // four partial sums in flight
+            const double* pe = P + col * bb + q;
+            const int64_t stride = ncols * bb;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int sp = 0;
+            for (; sp + 4 <= nsplit; sp += 4) {
+                s0 += pe[(sp + 0) * stride];
+                s1 += pe[(sp + 1) * stride];
+                s2 += pe[(sp + 2) * stride];
+                s3 += pe[(sp + 3) * stride];
+            }
+            for (; sp < nsplit; ++sp) s0 += pe[sp * stride];
+            Wc[q] = (s0 + s1) + (s2 + s3);
         }
         __syncwarp();
         for (int r = lane; r < bb; r += 32) {
@@ -333,7 +374,9 @@ __global__ void __launch_bounds__(256) reduce_y_f32c_kernel(const double* __rest
     float* Wl = Wh + 64 * ld;
     const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
     const int64_t cb = (int64_t)blockIdx.x * 64;
-    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {  // 16 entries per thread, all loads in flight
+        const int e = tid + 256 * u;
         const int r = e & 63, q = e >> 6;  // T column-major: T(a, b) = Tm[b * bb + a]
         double tv = 0.0;
         if (r < bb && q < bb) tv = transT ? Tm[r * bb + q] : Tm[q * bb + r];
@@ -341,16 +384,29 @@ __global__ void __launch_bounds__(256) reduce_y_f32c_kernel(const double* __rest
         Th[q * ld + r] = h;
         Tl[q * ld + r] = (float)(tv - (double)h);
     }
-    for (int e = tid; e < 64 * 64; e += blockDim.x) {
-        const int q = e & 63, c = e >> 6;  // P[sp][col][q]: q fastest, coalesced
-        double w = 0.0;
-        if (q < bb && cb + c < nc) {
-            const int64_t col = c0 + cb + c;
-            for (int sp = 0; sp < nsplit; ++sp) w += P[((int64_t)sp * ncols + col) * bb + q];
+    {  // W = sum of the split partials: 16 entries per thread, the splits outermost
+        double acc[16];
+        int64_t off[16];
+        const int64_t stride = ncols * bb;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = tid + 256 * u;
+            const int q = e & 63, c = e >> 6;  // P[sp][col][q]: q fastest, coalesced
+            acc[u] = 0.0;
+            off[u] = (q < bb && cb + c < nc) ? (c0 + cb + c) * bb + q : -1;
         }
-        const float h = (float)w;
-        Wh[q * ld + c] = h;
-        Wl[q * ld + c] = (float)(w - (double)h);
+        for (int sp = 0; sp < nsplit; ++sp)
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (off[u] >= 0) acc[u] += P[sp * stride + off[u]];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = tid + 256 * u;
+            const int q = e & 63, c = e >> 6;
+            const float h = (float)acc[u];
+            Wh[q * ld + c] = h;
+            Wl[q * ld + c] = (float)(acc[u] - (double)h);
+        }
     }
     __syncthreads();
     float sh[4][4], cp[4][4];
@@ -481,7 +537,7 @@ cudaError_t launch_tform(const double* P, int nsplit, int64_t ncols, int bb, con
         if (cudaError_t e = allow_max_dynamic_smem(tform_kernel)) return e;
         attr_set.set();
     }
-    tform_kernel<<<bb, 128, smem, s>>>(P, nsplit, ncols, bb, tau, Tm, st);
+    tform_kernel<<<bb, kTfThreads, smem, s>>>(P, nsplit, ncols, bb, tau, Tm, st);
     return cudaGetLastError();
 }
 

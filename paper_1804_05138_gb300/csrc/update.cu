@@ -53,7 +53,11 @@ __global__ void swap_scatter_kernel(T* __restrict__ A, int64_t lda, int64_t m,
 
 // One block per row r of Omega_hat_11 = R_hat11 R11^{-1}: the rows of the forward substitution
 // Omega_hat_11(r,j) = (R_hat11(r,j) - sum_{q=r}^{j-1} Omega_hat_11(r,q) R11(q,j)) / R11(j,j)
-// are independent.  R11(r:bb, r:bb) goes to shared memory; warp 0 runs the recurrence.
+// are independent.  R11(r:bb, r:bb) goes to shared memory; warp 0 runs the substitution column by
+// column: lane j mod 32 owns column j, finishes Omega_hat_11(r,q) at step q (a multiplication by the
+// reciprocal of R11(q,q), computed up front) and broadcasts it, and every lane subtracts its terms
+// from the columns it owns.  One product, one shuffle and one FMA per step: no reduction tree and no
+// division on the chain.
 template <typename T>
 __global__ void bsolve_kernel(const T* __restrict__ B, int64_t ldb, const T* __restrict__ A, int64_t lda,
                               int64_t i, int bb, double* __restrict__ What, const Status* st)
@@ -70,17 +74,29 @@ __global__ void bsolve_kernel(const T* __restrict__ B, int64_t ldb, const T* __r
     }
     __syncthreads();
     if (threadIdx.x < 32) {
+        constexpr int NJ = 4;  // columns per lane (bb <= 128)
         const int lane = threadIdx.x;
-        for (int jj = 0; jj < w; ++jj) {
-            double s = 0.0;
-            for (int qq = lane; qq < jj; qq += 32) s += Wr[qq] * Rs[jj * w + qq];
+        double acc[NJ], rinv[NJ];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                const double rjj = Rs[jj * w + jj];
-                Wr[jj] = (rjj == 0.0) ? 0.0 : ((double)B[(i + r + jj) * ldb + r] - s) / rjj;
+        for (int u = 0; u < NJ; ++u) {
+            const int jj = lane + 32 * u;
+            const double rjj = jj < w ? Rs[jj * w + jj] : 1.0;
+            acc[u] = jj < w ? (double)B[(i + r + jj) * ldb + r] : 0.0;
+            rinv[u] = rjj == 0.0 ? 0.0 : 1.0 / rjj;  // a zero diagonal gives a zero column
+        }
+        for (int qq = 0; qq < w; ++qq) {
+            const int u0 = qq >> 5;
+            double x = 0.0;
+#pragma unroll
+            for (int u = 0; u < NJ; ++u)
+                if (u == u0) x = acc[u] * rinv[u];
+            x = __shfl_sync(0xffffffffu, x, qq & 31);
+            if (lane == (qq & 31)) Wr[qq] = x;
+#pragma unroll
+            for (int u = 0; u < NJ; ++u) {
+                const int jj = lane + 32 * u;
+                if (jj > qq && jj < w) acc[u] = fma(-x, Rs[jj * w + qq], acc[u]);
             }
-            __syncwarp();
         }
     }
     __syncthreads();
