@@ -23,6 +23,7 @@
 // the panel is then left untouched and the cooperative Householder panel kernel launched after this
 // one factors it instead (it reads the flag and returns at once when the CholeskyQR2 result was
 // written).  No host synchronisation.
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace rq {
@@ -41,58 +42,6 @@ constexpr int kRedWarps = 8;
 // pass-1 pivot test: the Gram G1 is summed in FP32 (folded into pairs), so CholeskyQR2 is kept only
 // while kappa(P) stays below about 2^10
 constexpr float kCqrPass1Thr = 9.5367431640625e-07f;  // 2^-20
-
-// ---------------------------------------------------------------------------------- float pairs
-struct df {
-    float h, l;
-};
-__device__ __forceinline__ df df_two_sum(float a, float b)
-{
-    const float s = a + b;
-    const float z = s - a;
-    return {s, (a - (s - z)) + (b - z)};
-}
-__device__ __forceinline__ df df_quick(float a, float b)  // |a| >= |b|
-{
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ df df_add(df a, df b)
-{
-    const df s = df_two_sum(a.h, b.h);
-    return df_quick(s.h, s.l + a.l + b.l);
-}
-__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ df df_mul(df a, df b)
-{
-    const float p = a.h * b.h;
-    const float e = fmaf(a.h, b.h, -p);
-    return df_quick(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
-}
-// c - a b
-__device__ __forceinline__ df df_fms(df c, df a, df b) { return df_add(c, df_neg(df_mul(a, b))); }
-// 1 / a: FP32 reciprocal refined by one Newton step in pairs
-__device__ __forceinline__ df df_rcp(df a)
-{
-    const float r = 1.0f / a.h;
-    const df e = df_add({1.0f, 0.0f}, df_neg(df_mul(a, {r, 0.0f})));  // 1 - a r
-    return df_add({r, 0.0f}, df_mul({r, 0.0f}, e));
-}
-// a^{-1/2}: FP32 reciprocal square root refined by one Newton step in pairs
-__device__ __forceinline__ df df_rsqrt(df a)
-{
-    const float y = rsqrtf(a.h);
-    const float p = y * y;
-    const df yy = {p, fmaf(y, y, -p)};
-    const df e = df_add({1.0f, 0.0f}, df_neg(df_mul(a, yy)));  // 1 - a y^2
-    return df_add({y, 0.0f}, df_mul({0.5f * y, 0.0f}, e));
-}
-__device__ __forceinline__ df df_of(double x)
-{
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ double df_dbl(df a) { return (double)a.h + (double)a.l; }
 
 // --------------------------------------------------------------------------- index tables
 // packed upper-triangle index of (i, j), i <= j, row-major

@@ -17,6 +17,7 @@
 // applies the transpositions to jpvt and records the net column map used to swap A.
 // Rank guard: if the best remaining norm^2 is not above guard_rel2 * (largest initial
 // sketch norm^2), pivoting stops for good at this step.
+#include "df.cuh"
 #include "pivot_common.cuh"
 
 namespace rq {
@@ -44,6 +45,43 @@ __device__ void block_argmax(double& v, long long& p, int& idx, double* sv, long
     }
     __syncthreads();
     v = sv[32]; p = sp[32]; idx = si[32];
+}
+
+// FP32 form: one 64-bit key per candidate that orders as (norm, -position): the norm's bits
+// (non-negative floats order as their bit patterns, a NaN above every number), then kRelMax minus
+// the position relative to i, then a 10-bit index (the slot within the block, or the block within
+// the grid).  0 is "no candidate".  One 64-bit max per shuffle level replaces the three-part compare.
+constexpr unsigned long long kRelMax = 0x3FFFFFull;  // positions relative to i below 2^22
+__device__ __forceinline__ unsigned long long fkey(float v, long long relpos, int idx)
+{
+    if (v < 0.f) return 0ull;
+    return ((unsigned long long)(__float_as_uint(v) & 0x7FFFFFFFu) << 32) |
+           ((kRelMax - (unsigned long long)relpos) << 10) | (unsigned long long)idx;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, k, o);
+        k = x > k ? x : k;
+    }
+    return k;
+}
+// Block-wide maximum of the threads' keys (slot 32 of sk broadcasts it, written only after the
+// next call's first barrier).
+__device__ unsigned long long block_max_key(unsigned long long k, unsigned long long* sk)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    k = warp_max_key(k);
+    if (lane == 0) sk[w] = k;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long kk = lane < nw ? sk[lane] : 0ull;
+        kk = warp_max_key(kk);
+        if (lane == 0) sk[32] = kk;
+    }
+    __syncthreads();
+    return sk[32];
 }
 
 template <typename T>
@@ -84,7 +122,10 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     __shared__ double red_v[33];
     __shared__ long long red_p[33];
     __shared__ int red_i[33];
+    __shared__ unsigned long long red_k[33];
     __shared__ double sh_tau, sh_beta, sh_scal;
+    __shared__ float sh_scl;  // FP32 form: the low half of the float pair 1 / (alpha - beta)
+    constexpr bool F = sizeof(T) == 4;  // FP32 form: packed keys, float-pair reflector scalars
 
     const int64_t nprime = n - i;
     const int64_t s0 = (int64_t)g * cpb;
@@ -108,6 +149,7 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
     double lbv = -1.0;
     long long lbp = LLONG_MAX;
     int lbs = -1;
+    unsigned long long lk = 0ull;
     for (int sl = my_slot0; sl - my_slot0 < ((nloc + slots_per_pass - 1) / slots_per_pass) * slots_per_pass;
          sl += slots_per_pass) {
         T part = T(0);
@@ -116,10 +158,15 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
             for (int r = sub; r < l; r += tpc) part = fma(col[r], col[r], part);
         }
         part = column_sum(part, tpc);
-        if (sl < nloc && sub == 0 && better((double)part, pos[sl], lbv, lbp)) {
-            lbv = (double)part;
-            lbp = pos[sl];
-            lbs = sl;
+        if (sl < nloc && sub == 0) {
+            if constexpr (F) {
+                const unsigned long long k = fkey((float)part, pos[sl] - i, sl);
+                lk = k > lk ? k : lk;
+            } else if (better((double)part, pos[sl], lbv, lbp)) {
+                lbv = (double)part;
+                lbp = pos[sl];
+                lbs = sl;
+            }
         }
     }
     unsigned long long* ctr = ctrs + parity;
@@ -135,10 +182,18 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         double myv = lbv;
         long long myp = lbp;
         int mys = lbs;
-        block_argmax(myv, myp, mys, red_v, red_p, red_i);
-        if (tid == 0) {
-            cval[buf * kMaxCand + g] = myv;
-            cpos[buf * kMaxCand + g] = myp;
+        if constexpr (F) {  // one key: the slot in its low bits, replaced by the block index
+            const unsigned long long mk = block_max_key(lk, red_k);
+            mys = mk ? (int)(mk & 0x3FFull) : -1;
+            if (tid == 0)
+                reinterpret_cast<unsigned long long*>(cval)[buf * kMaxCand + g] =
+                    mk ? ((mk & ~0x3FFull) | (unsigned long long)g) : 0ull;
+        } else {
+            block_argmax(myv, myp, mys, red_v, red_p, red_i);
+            if (tid == 0) {
+                cval[buf * kMaxCand + g] = myv;
+                cpos[buf * kMaxCand + g] = myp;
+            }
         }
         if (mys >= 0)
             for (int r = tid; r < l; r += NTH)
@@ -168,7 +223,23 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         if (!s_ok) return;
         // 3. global winner (identical in every block): warp 0 reads the G candidates, eight
         //    per lane in flight at a time, and reduces them; slot 32 broadcasts the result
-        if (tid < 32) {
+        if (F && tid < 32) {
+            const unsigned long long* ck = reinterpret_cast<const unsigned long long*>(cval) + buf * kMaxCand;
+            unsigned long long wk = 0ull;
+            for (int h0 = tid; h0 < G; h0 += 8 * 32) {
+                unsigned long long kk[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) kk[u] = h0 + 32 * u < G ? ld_cg(&ck[h0 + 32 * u]) : 0ull;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) wk = kk[u] > wk ? kk[u] : wk;
+            }
+            wk = warp_max_key(wk);
+            if (tid == 0) {
+                red_v[32] = wk ? (double)__uint_as_float((unsigned)(wk >> 32)) : -1.0;
+                red_p[32] = wk ? i + (long long)(kRelMax - ((wk >> 10) & kRelMax)) : LLONG_MAX;
+                red_i[32] = wk ? (int)(wk & 0x3FFull) : -1;
+            }
+        } else if (!F && tid < 32) {
             double wv = -1.0;
             long long wp = LLONG_MAX;
             int wg = -1;
@@ -200,10 +271,43 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
             steps = t;
             break;
         }
-        for (int r = tid; r < l; r += NTH) xs[r] = (double)ld_cg(&ccol[((size_t)buf * kMaxCand + wg) * l + r]);
+        if constexpr (F) {
+            float* xf = reinterpret_cast<float*>(xs);
+            for (int r = tid; r < l; r += NTH) xf[r] = ld_cg(&ccol[((size_t)buf * kMaxCand + wg) * l + r]);
+        } else {
+            for (int r = tid; r < l; r += NTH) xs[r] = (double)ld_cg(&ccol[((size_t)buf * kMaxCand + wg) * l + r]);
+        }
         __syncthreads();
-        // Householder reflector from rows t..l-1 of the winner (xLARFG), warp 0, fixed order
-        if (tid < 32) {
+        // Householder reflector from rows t..l-1 of the winner (xLARFG), warp 0, fixed order.  FP32
+        // form: Dot2 sum of squares and float-pair square root and divisions (about 44 bits, no FP64
+        // instruction on the chain)
+        if (F && tid < 32) {
+            const float* xf = reinterpret_cast<const float*>(xs);
+            float qh = 0.f, ql = 0.f;
+            for (int r = t + 1 + tid; r < l; r += 32) dot2_add(qh, ql, xf[r], xf[r]);
+            df ssd = df_quick(qh, ql);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                ssd = df_add(ssd, {__shfl_xor_sync(0xffffffffu, ssd.h, o), __shfl_xor_sync(0xffffffffu, ssd.l, o)});
+            const float alpha = xf[t];
+            float tauf = 0.f, betaf = alpha;
+            df scal = {0.f, 0.f};
+            if (ssd.h != 0.f) {
+                const df nrm = df_sqrt(df_add(df_mul({alpha, 0.f}, {alpha, 0.f}), ssd));
+                const df beta = alpha >= 0.f ? df_neg(nrm) : nrm;
+                const df tau = df_mul(df_add(beta, {-alpha, 0.f}), df_rcp(beta));
+                scal = df_rcp(df_add({alpha, 0.f}, df_neg(beta)));
+                tauf = tau.h + tau.l;
+                betaf = beta.h + beta.l;
+            }
+            if (tid == 0) {
+                sh_tau = tauf;
+                sh_beta = betaf;
+                sh_scal = scal.h;
+                sh_scl = scal.l;
+                if (g == 0) pivs[t] = wp;
+            }
+        } else if (!F && tid < 32) {
             double ss = 0.0;
             for (int r = t + 1 + tid; r < l; r += 32) ss += xs[r] * xs[r];
 #pragma unroll
@@ -218,7 +322,16 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
             }
         }
         __syncthreads();
-        for (int r = t + 1 + tid; r < l; r += NTH) vT[r] = (T)(xs[r] * sh_scal);
+        if constexpr (F) {
+            const float* xf = reinterpret_cast<const float*>(xs);
+            const df sc = {(float)sh_scal, sh_scl};
+            for (int r = t + 1 + tid; r < l; r += NTH) {
+                const df v = df_mul({xf[r], 0.f}, sc);
+                vT[r] = v.h + v.l;
+            }
+        } else {
+            for (int r = t + 1 + tid; r < l; r += NTH) vT[r] = (T)(xs[r] * sh_scal);
+        }
         if (tid == 0) vT[t] = T(1);
         __syncthreads();
         // 4. apply H to every remaining column, then the norms of rows t+1..l-1 for step t+1
@@ -227,6 +340,7 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
         lbv = -1.0;
         lbp = LLONG_MAX;
         lbs = -1;
+        lk = 0ull;
         for (int sl = my_slot0; sl - my_slot0 < ((nloc + slots_per_pass - 1) / slots_per_pass) * slots_per_pass;
              sl += slots_per_pass) {
             const bool mine = sl < nloc;
@@ -256,7 +370,12 @@ __global__ void __launch_bounds__(1024) pivot_kernel(T* __restrict__ B, int64_t 
                     pos[sl] = c;
                 } else {
                     if (pos[sl] == c) pos[sl] = wp;  // the column displaced by the swap
-                    if (active[sl] && better((double)nu, pos[sl], lbv, lbp)) {
+                    if constexpr (F) {
+                        if (active[sl]) {
+                            const unsigned long long k = fkey((float)nu, pos[sl] - i, sl);
+                            lk = k > lk ? k : lk;
+                        }
+                    } else if (active[sl] && better((double)nu, pos[sl], lbv, lbp)) {
                         lbv = (double)nu;
                         lbp = pos[sl];
                         lbs = sl;
@@ -313,6 +432,7 @@ size_t pivot_cand_bytes(int l)
 bool pivot_fits(int64_t ncols, int l, int elem_bytes)
 {
     if (l > 1024) return false;
+    if (ncols >= (int64_t)kRelMax) return false;  // the FP32 form's keys hold positions in 22 bits
     const int64_t G = dev_info().sms;
     const int64_t cpb = (ncols + G - 1) / G;
     if (cpb > 1024) return false;
