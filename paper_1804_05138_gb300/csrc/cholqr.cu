@@ -15,9 +15,10 @@
 //           et al., "Reconstructing Householder vectors from tall-skinny QR", 2014).  The top bb rows
 //           of Q2 are formed and factored in one block; the rows below are V2 = Q1 (U R2)^{-1}, one
 //           row per thread.
-// The small factorizations run in float pairs (Dekker products by FMA, Knuth sums) because one SM
-// issues FP64 at a small fraction of its FP32 rate; their steps deal the trailing entries out evenly
-// over the block's threads from a table and take one barrier each.  CholeskyQR2 needs kappa(P) well
+// The two Cholesky factorizations run in float pairs (Dekker products by FMA, Knuth sums) because
+// one SM issues FP64 at a small fraction of its FP32 rate, the LU in FP32 (its factors become the
+// FP32 reflectors); their steps deal the trailing entries out evenly over the block's threads from
+// a table and take one barrier each.  CholeskyQR2 needs kappa(P) well
 // below the inverse square root of the Gram's precision: a pivot of G1 below 2^-20 of its diagonal
 // entry (kappa(P) beyond about 1e3; G1 is summed in FP32), or a pivot of G2 below 1/2, sets a flag;
 // the panel is then left untouched and the cooperative Householder panel kernel launched after this
@@ -392,41 +393,37 @@ __global__ void __launch_bounds__(kSmallThreads) cqr_small2_kernel(
         }
     }
     __syncthreads();
-    // LU of Q2top - S in pairs, right-looking: step j subtracts U(r, j) U(j, c) / piv_j from every
+    // LU of Q2top - S in FP32, right-looking: step j subtracts U(r, j) U(j, c) / piv_j from every
     // (r, c) with r, c > j (dealt out evenly through the shell table), one barrier per step; the
-    // pivots and the scaling of column j into L(:, j) are applied after the last step
+    // pivots and the scaling of column j into L(:, j) are applied after the last step.  Working
+    // precision suffices here (the reconstruction is stable with the LU in working precision,
+    // Ballard et al. 2014): L and U become the FP32 reflectors, tau and W, and R does not depend on
+    // them.  Every pivot has |piv| = |a| + 1 >= 1 (s_j = -sign(a)), so the LU needs no pivoting.
     for (int j = 0; j < bb; ++j) {
-        const df a = {S.UH[j][j], S.UL[j][j]};
-        const float s = a.h >= 0.f ? -1.f : 1.f;
-        const df piv = df_add(a, {-s, 0.f});
-        const df rp = df_rcp(piv);
+        const float a = S.UH[j][j];
+        const float s = a >= 0.f ? -1.f : 1.f;
+        const float piv = a - s;
+        const float rp = 1.f / piv;
         if (tid == 0) {
-            S.pvh[j] = piv.h;
-            S.pvl[j] = piv.l;
-            S.rph[j] = rp.h;
-            S.rpl[j] = rp.l;
+            S.pvh[j] = piv;
+            S.pvl[j] = 0.f;
+            S.rph[j] = rp;
+            S.rpl[j] = 0.f;
             S.sgn[j] = s;
         }
         for (int e = sq_start(j + 1, bb) + tid; e < nsq; e += kSmallThreads) {
             const uint16_t t = S.sq[e];
             const int r = tab_r(t), c = tab_c(t);
-            const df l = df_mul({S.UH[r][j], S.UL[r][j]}, rp);
-            const df v = df_fms({S.UH[r][c], S.UL[r][c]}, l, {S.UH[j][c], S.UL[j][c]});
-            S.UH[r][c] = v.h;
-            S.UL[r][c] = v.l;
+            S.UH[r][c] = fmaf(-(S.UH[r][j] * rp), S.UH[j][c], S.UH[r][c]);
         }
         __syncthreads();
     }
     if (tx < bb)
         for (int r = ty; r < bb; r += kSmallThreads / 64) {
-            if (r == tx) {
+            if (r == tx)
                 S.UH[r][tx] = S.pvh[tx];
-                S.UL[r][tx] = S.pvl[tx];
-            } else if (r > tx) {
-                const df v = df_mul({S.UH[r][tx], S.UL[r][tx]}, {S.rph[tx], S.rpl[tx]});
-                S.UH[r][tx] = v.h;
-                S.UL[r][tx] = v.l;
-            }
+            else if (r > tx)
+                S.UH[r][tx] *= S.rph[tx];
         }
     __syncthreads();
     // tau, the panel's top rows (R_house = S R2 R1 above, L1 below the diagonal) and W = U R2.
