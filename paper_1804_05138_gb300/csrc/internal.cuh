@@ -216,6 +216,26 @@ cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long 
                                   cudaStream_t s);
 bool tensor_cores_enabled();
 
+// General 3xTF32 tensor-core contraction (mm_tc.cu):
+//   D(r, dcol(c)) = alpha sum_q A(r, q) B(q, c) + beta D0(r, dcol(c)),  r < M, c < N, q < K,
+// dcol(c) = dmap ? dmap[c] : c.  A(r, q) = A[q lda + r] or, kmajor, A[r lda + q]; A must be
+// 16-byte aligned with lda % 4 == 0 (mm_tc_supported).  B is given as TF32 planes written by
+// launch_mm_planes (mm_planes_bytes(K, N), 16-byte aligned): B(q, c) = src[kq ldk + c ldn] with
+// kq = kmap ? kmap[q] : q, zero where kmap[q] < kmin.  nsplit > 1 splits K: split z writes its
+// partial product to D + z dz (beta must be 0); launch_mm_sum adds the splits.
+bool mm_tc_supported(const void* A, long long lda);
+size_t mm_planes_bytes(long long K, long long N);
+int mm_max_split();
+int mm_choose_split(long long M, long long N, long long K, int min_chunks);
+cudaError_t launch_mm_planes(const float* src, long long ldk, long long ldn, const int32_t* kmap, long long kmin,
+                             long long K, long long N, float* planes, const Status* st, cudaStream_t s);
+cudaError_t launch_mm_tc(bool kmajor, const float* A, long long lda, const float* planes, long long M, long long N,
+                         long long K, int nsplit, float alpha, float beta, const float* D0, long long ldd0, float* D,
+                         long long ldd, long long dz, const int32_t* dmap, Status* st, cudaStream_t s);
+// D(r, c) = D0(r, c) (if D0) + sum_{z < nz} P[z dz + c ldp + r], r < M, c < N.
+cudaError_t launch_mm_sum(const float* P, long long ldp, long long dz, int nz, long long M, long long N, const float* D0,
+                          long long ldd0, float* D, long long ldd, const Status* st, cudaStream_t s);
+
 // C(mr x nc) -= V(mr x kb) * Y(kb x nc).  maskV: V has the unit-lower reflector structure.
 // colmap (optional): column c of the product goes to column colmap[c] of C.
 template <typename T>

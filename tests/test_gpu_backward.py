@@ -136,3 +136,52 @@ def test_backward_fp32_4096_k256_vs_oracle(ag, orc):
     print(f"kappa(R11) = {kappa:.4e}, bar = {bar:.3e}, FP32 vs oracle {rel:.3e}, vs FP64 GPU {rel64:.3e}")
     assert rel <= bar, (rel, bar, kappa)
     assert rel64 <= bar, (rel64, bar, kappa)
+
+
+def _fp32_case(ag, orc, m, n, k, b, p, seed):
+    """FP32 forward + backward at m x n against the FP64 oracle gradient with the GPU's
+    permutation; returns (rel, bar, grad) with the bar of the 4096 case."""
+    import torch
+    A0 = inputs.spectrum_matrix(m, n, inputs.sigma_inverse_square(n), seed, seed + 1)
+    rng = np.random.default_rng(seed)
+    G1 = (rng.standard_normal((m, k)) * 1e-3).astype(np.float32)
+    G2 = (rng.standard_normal((k, n)) * 1e-3).astype(np.float32)
+    A = torch.from_numpy(A0.astype(np.float32)).cuda().requires_grad_(True)
+    Q1, R, jpvt = ag.rqrcp_truncated(A, k, b, p, 0)
+    loss = _loss_torch(A, Q1, R, jpvt, torch.from_numpy(G1).cuda(), torch.from_numpy(G2).cuda())
+    loss.backward()
+    got = A.grad.double().cpu().numpy()
+    jp = jpvt.cpu().numpy()
+    A32 = A0.astype(np.float32).astype(np.float64)
+    want = _oracle_grad(orc, A32, jp, k, G1.astype(np.float64), G2.astype(np.float64))
+    _, R11o, _ = orc.truncated_qr_forward(A32[:, jp], k)
+    bar = 0.25 * float(np.linalg.cond(R11o)) * 2.0 ** -24
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    return rel, bar, A.grad.detach().clone()
+
+
+@pytest.mark.parametrize("m,n,k,b,p", [
+    (1004, 903, 100, 32, 8),   # tensor-core path: ragged tiles, a 36-column leading solve block
+    (600, 300, 300, 64, 8),    # k = n: no trailing block
+    (2048, 1536, 200, 64, 8),  # tensor-core path, split contractions
+    (1001, 700, 70, 16, 8),    # lda % 4 != 0: the SIMT path
+])
+def test_backward_fp32_shapes_vs_oracle(ag, orc, m, n, k, b, p):
+    rel, bar, g = _fp32_case(ag, orc, m, n, k, b, p, 21)
+    print(f"{m}x{n} k={k}: FP32 vs oracle {rel:.3e}, bar {bar:.3e}")
+    assert rel <= bar, (rel, bar)
+
+
+def test_backward_fp32_deterministic(ag):
+    """Two backward calls on the same forward give bit-identical gradients (no atomics: split
+    partials are summed in a fixed order)."""
+    import torch
+    m, n, k = 1004, 903, 100
+    A0 = inputs.spectrum_matrix(m, n, inputs.sigma_inverse_square(n))
+    grads = []
+    for _ in range(2):
+        A = torch.from_numpy(A0.astype(np.float32)).cuda().requires_grad_(True)
+        Q1, R, jpvt = ag.rqrcp_truncated(A, k, 32, 8, 0)
+        ((Q1 * Q1).sum() + (R * R).sum()).backward()
+        grads.append(A.grad.clone())
+    assert torch.equal(grads[0], grads[1])
