@@ -222,17 +222,32 @@ bool tensor_cores_enabled();
 // 16-byte aligned with lda % 4 == 0 (mm_tc_supported).  B is given as TF32 planes written by
 // launch_mm_planes (mm_planes_bytes(K, N), 16-byte aligned): B(q, c) = src[kq ldk + c ldn] with
 // kq = kmap ? kmap[q] : q, zero where kmap[q] < kmin.  nsplit > 1 splits K: split z writes its
-// partial product to D + z dz (beta must be 0); launch_mm_sum adds the splits.
+// partial product to D + z dz (beta must be 0); launch_mm_sum adds the splits.  Masks for reflector
+// blocks V stored in place (unit lower, other data above the diagonal): amask 1 makes A = V or,
+// kmajor, A = V^T; planes mask 1 makes B unit lower, mask 2 upper (B(q, c) = 0 for q > c).
 bool mm_tc_supported(const void* A, long long lda);
 size_t mm_planes_bytes(long long K, long long N);
 int mm_max_split();
 int mm_choose_split(long long M, long long N, long long K, int min_chunks);
 cudaError_t launch_mm_planes(const float* src, long long ldk, long long ldn, const int32_t* kmap, long long kmin,
-                             long long K, long long N, float* planes, const Status* st, cudaStream_t s);
+                             long long K, long long N, float* planes, const Status* st, cudaStream_t s,
+                             int mask = 0);
 cudaError_t launch_mm_tc(bool kmajor, const float* A, long long lda, const float* planes, long long M, long long N,
                          long long K, int nsplit, float alpha, float beta, const float* D0, long long ldd0, float* D,
-                         long long ldd, long long dz, const int32_t* dmap, Status* st, cudaStream_t s);
-// D(r, c) = D0(r, c) (if D0) + sum_{z < nz} P[z dz + c ldp + r], r < M, c < N.
+                         long long ldd, long long dz, const int32_t* dmap, Status* st, cudaStream_t s,
+                         int amask = 0);
+// FP32 low-rank outputs on the tensor cores (lowrank.cu): Q1 = I(:, 0:k) - V T V1^T with all k
+// reflectors in one compact WY form (T^{-1} = diag(1 / tau) + striu(V^T V)), and, if L is not null,
+// L(:, jpvt[c]) = Q1 [R11 R12](:, c).  Usable when lowrank_f32_tc_ok (k <= 256, aligned operands);
+// work (256-byte aligned) needs lowrank_f32_tc_bytes(m, n, k) and gets its status block at the head.
+template <typename T>
+cudaError_t launch_eye(T* Q, int64_t ldq, int64_t m, int64_t k, cudaStream_t s);
+bool lowrank_f32_tc_ok(int64_t k, const float* Afact, int64_t ldaf, const float* Q1, int64_t ldq);
+size_t lowrank_f32_tc_bytes(int64_t m, int64_t n, int64_t k);
+int lowrank_f32_tc(int64_t m, int64_t n, int64_t k, const float* Afact, int64_t ldaf, const double* tau,
+                   const int32_t* jpvt, float* L, int64_t ldl, float* Q1, int64_t ldq, void* work, cudaStream_t s);
+
+// D(r, c) = D0(r, c) (if D0) + sum_{z < nz} P[z dz + c ldp + r], r < M, c < N (compensated sum).
 cudaError_t launch_mm_sum(const float* P, long long ldp, long long dz, int nz, long long M, long long N, const float* D0,
                           long long ldd0, float* D, long long ldd, const Status* st, cudaStream_t s);
 

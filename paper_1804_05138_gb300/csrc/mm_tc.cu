@@ -20,6 +20,7 @@
 // blocks share an SM, so one block's epilogue overlaps the other's MMAs.  Every wait is
 // bounded; on timeout the block records RQRCP_ERR_TIMEOUT, lets its copies land and frees its
 // tensor memory.
+#include "df.cuh"
 #include "tc_common.cuh"
 
 namespace rq {
@@ -42,10 +43,12 @@ long long mm_kp(long long K) { return (K + MM_KC - 1) / MM_KC * MM_KC; }
 long long mm_ntiles(long long N) { return (N + MM_BN - 1) / MM_BN; }
 
 // planes (see the file comment) of B(q, c) = src[kq * ldk + c * ldn], kq = kmap ? kmap[q] : q;
-// zero where q >= K, c >= N or kmap[q] < kmin.
+// zero where q >= K, c >= N or kmap[q] < kmin.  mask 1: B is unit lower (B(q, c) = 0 for q < c,
+// 1 for q == c, as the reflector block V); mask 2: B is upper (B(q, c) = 0 for q > c).
 __global__ void mm_planes_kernel(const float* __restrict__ src, long long ldk, long long ldn,
                                  const int32_t* __restrict__ kmap, long long kmin, long long K, long long N,
-                                 long long kp, long long ntiles, float* __restrict__ planes, const Status* st)
+                                 int mask, long long kp, long long ntiles, float* __restrict__ planes,
+                                 const Status* st)
 {
     if (status_error(st)) return;
     const long long total = ntiles * MM_BN * kp;
@@ -62,6 +65,11 @@ __global__ void mm_planes_kernel(const float* __restrict__ src, long long ldk, l
                 kq = kmap[q];
                 keep = kq >= kmin;
             }
+            if (mask == 1 && q <= c) {
+                keep = false;
+                if (q == c) h = 1.f;
+            }
+            if (mask == 2 && q > c) keep = false;
             if (keep) {
                 const float v = src[kq * ldk + c * ldn];
                 h = tf32_rn(v);
@@ -83,6 +91,7 @@ struct MmArgs {
     float* D;
     long long ldd, dz;     // split z writes D + z * dz
     const int32_t* dmap;   // column map of D and D0 (null: identity)
+    int amask;             // 1: A is a unit-lower reflector block (see mm_tc_kernel)
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&v)[16])
@@ -104,7 +113,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16])
 }
 
 // KMAJ: A(r, q) = A[r lda + q] (tile loaded as 128 lines of 32 values, 128-byte swizzle);
-// otherwise A(r, q) = A[q lda + r] (tile loaded as 32 columns of 128 rows).
+// otherwise A(r, q) = A[q lda + r] (tile loaded as 32 columns of 128 rows).  amask: the stored
+// matrix is a unit-lower reflector block V (V(i, j) = 0 for i < j, 1 for i == j; the strict upper
+// part holds other data): A = V (A(r, q) = V(r, q)) or, KMAJ, A = V^T (A(r, q) = V(q, r)).
 template <bool KMAJ>
 __global__ void __launch_bounds__(MM_THREADS, 2)
     mm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, MmArgs a,
@@ -231,6 +242,14 @@ __global__ void __launch_bounds__(MM_THREADS, 2)
 #pragma unroll
                 for (int u = 0; u < 16; ++u) v[u] = at[(16 * g + u) * MM_BM + row];
             }
+            if (a.amask) {
+                const long long rr = r0 + row, q0 = (jbeg + t) * MM_KC + 16 * g;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const long long i = KMAJ ? q0 + u : rr, j = KMAJ ? rr : q0 + u;  // V(i, j)
+                    if (i <= j) v[u] = (i == j) ? 1.f : 0.f;
+                }
+            }
             uint32_t hi[16], lo[16];
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
@@ -285,7 +304,7 @@ __global__ void __launch_bounds__(MM_THREADS, 2)
 
 size_t mm_smem_bytes() { return 1024 + (size_t)MM_NST * MM_STAGE; }
 
-// Sum of split partials: D(r, c) = D0(r, c) + sum_z P[z dz + c ldp + r] (r < M, c < N).
+// Sum of split partials: D(r, c) = D0(r, c) + sum_z P[z dz + c ldp + r] (r < M, c < N), a compensated sum.
 __global__ void mm_sum_kernel(const float* __restrict__ P, long long ldp, long long dz, int nz, long long M, long long N,
                               const float* __restrict__ D0, long long ldd0, float* __restrict__ D, long long ldd,
                               const Status* st)
@@ -295,15 +314,19 @@ __global__ void mm_sum_kernel(const float* __restrict__ P, long long ldp, long l
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const long long r = e % M, c = e / M;
-        float s = D0 != nullptr ? D0[c * ldd0 + r] : 0.f;
-        for (int z0 = 0; z0 < nz; z0 += 4) {  // four loads in flight per step, summed in order
+        float sh = D0 != nullptr ? D0[c * ldd0 + r] : 0.f, sl = 0.f;
+        for (int z0 = 0; z0 < nz; z0 += 4) {  // four loads in flight per step, compensated sum in order
             float pv[4];
 #pragma unroll
             for (int zz = 0; zz < 4; ++zz) pv[zz] = z0 + zz < nz ? P[(z0 + zz) * dz + c * ldp + r] : 0.f;
 #pragma unroll
-            for (int zz = 0; zz < 4; ++zz) s += pv[zz];
+            for (int zz = 0; zz < 4; ++zz) {
+                const df t = df_two_sum(sh, pv[zz]);
+                sh = t.h;
+                sl += t.l;
+            }
         }
-        D[c * ldd + r] = s;
+        D[c * ldd + r] = sh + sl;
     }
 }
 
@@ -350,7 +373,7 @@ int mm_choose_split(long long M, long long N, long long K, int min_chunks)
 }
 
 cudaError_t launch_mm_planes(const float* src, long long ldk, long long ldn, const int32_t* kmap, long long kmin,
-                             long long K, long long N, float* planes, const Status* st, cudaStream_t s)
+                             long long K, long long N, float* planes, const Status* st, cudaStream_t s, int mask)
 {
     if (K < 1 || N < 1) return cudaSuccess;
     if (((uintptr_t)planes % 16) != 0) return cudaErrorInvalidValue;
@@ -358,13 +381,13 @@ cudaError_t launch_mm_planes(const float* src, long long ldk, long long ldn, con
     const long long total = ntiles * MM_BN * kp;
     long long blocks = (total + 255) / 256;
     if (blocks > 8L * dev_info().sms) blocks = 8L * dev_info().sms;
-    mm_planes_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, ldk, ldn, kmap, kmin, K, N, kp, ntiles, planes, st);
+    mm_planes_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, ldk, ldn, kmap, kmin, K, N, mask, kp, ntiles, planes, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mm_tc(bool kmajor, const float* A, long long lda, const float* planes, long long M, long long N,
                          long long K, int nsplit, float alpha, float beta, const float* D0, long long ldd0, float* D,
-                         long long ldd, long long dz, const int32_t* dmap, Status* st, cudaStream_t s)
+                         long long ldd, long long dz, const int32_t* dmap, Status* st, cudaStream_t s, int amask)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K < 1 || (nsplit > 1 && beta != 0.f) || (beta != 0.f && D0 == nullptr)) return cudaErrorInvalidValue;
@@ -387,6 +410,7 @@ cudaError_t launch_mm_tc(bool kmajor, const float* A, long long lda, const float
     a.ldd = ldd;
     a.dz = S > 1 ? dz : 0;
     a.dmap = dmap;
+    a.amask = amask;
     CUtensorMap mapA, mapB;
     const bool okA = kmajor ? tc_encode_2d(&mapA, A, K, M, lda, MM_KC, MM_BM, true)
                             : tc_encode_2d(&mapA, A, M, K, lda, MM_BM, MM_KC, false);

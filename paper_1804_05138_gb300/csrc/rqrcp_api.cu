@@ -438,6 +438,10 @@ int lowrank_impl(int64_t m, int64_t n, int64_t k, const T* Afact, int64_t ldaf, 
     const size_t need = rqrcp_lowrank_workspace_size(m, n, k);
     if (int e = check_work(work, work_bytes, need)) return e;
     cudaStream_t s = (cudaStream_t)stream;
+    if (sizeof(T) == 4 && lowrank_f32_tc_ok(k, reinterpret_cast<const float*>(Afact), ldaf,
+                                            reinterpret_cast<const float*>(Q1), ldq))
+        return lowrank_f32_tc(m, n, k, reinterpret_cast<const float*>(Afact), ldaf, tau, jpvt,
+                              reinterpret_cast<float*>(L), ldl, reinterpret_cast<float*>(Q1), ldq, work, s);
     const int64_t bb = 64;
     char* w = static_cast<char*>(work);
     size_t off = 0;
@@ -773,7 +777,8 @@ __attribute__((visibility("default"))) size_t rqrcp_lowrank_workspace_size(int64
     off = align_up(off + (size_t)kMaxSplit * (size_t)(k > bb ? k : bb) * bb * sizeof(double));  // P
     off = align_up(off + (size_t)bb * bb * sizeof(double));                                        // Tm
     off = align_up(off + (size_t)k * (size_t)(n > bb ? n : bb) * sizeof(double));                 // Y / Rk
-    return off;
+    const size_t tc = lowrank_f32_tc_bytes(m, n, k);  // the FP32 tensor-core form
+    return off > tc ? off : tc;
 }
 
 __attribute__((visibility("default"))) int rqrcp_lowrank(int64_t m, int64_t n, int64_t k, const double* Afact,
