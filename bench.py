@@ -652,7 +652,9 @@ def run_diff_steps(args, w, A0, stream):
         A.copy_(A0)
         Ag = A.detach().requires_grad_(True)
         Q1, R, jp = rq_autograd.rqrcp_truncated(Ag, k, b, p, 0)
-        E = Ag[:, jp.long()] - Q1 @ R
+        # A Pi as index_select: its backward is one index_add (each gradient column receives one
+        # column), where advanced indexing's backward sorts all m n indices (3-4 ms here)
+        E = Ag.index_select(1, jp.long()) - Q1 @ R
         ((E * E).sum() + (gq * Q1).sum() + (gr * R).sum()).backward()
 
     for _ in range(args.warmup):
@@ -705,7 +707,7 @@ def run_e2e(args, w, A0, dev, stream, world, F, diff, form):
         if diff:
             Ag = A.detach().requires_grad_(True)
             Q1, R, jp = rq_autograd.rqrcp_truncated(Ag, k, b, p, 0)
-            E = Ag[:, jp.long()] - Q1 @ R
+            E = Ag.index_select(1, jp.long()) - Q1 @ R
             ((E * E).sum() + (gq * Q1).sum() + (gr * R).sum()).backward()
             ev[2].record(stream)
             host_out.copy_(Ag.grad.t(), non_blocking=True)
