@@ -210,10 +210,17 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
 // 16-byte aligned with ldc % 4 == 0 (tc_update_supported); ys (16-byte aligned,
 // tc_update_ws_bytes(nt)) receives the TF32 parts of Y.
 bool tc_update_supported(long long kb, long long ldc, const void* C);
-size_t tc_update_ws_bytes(long long nt);
+size_t tc_update_ws_bytes(long long nt, int kp = 64);
 cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long long ldv, const double* Y, long long ldy,
                                   long long mr, long long nt, int kb, long long maskV, float* ys, const Status* st,
                                   cudaStream_t s);
+// Two blocks in one pass: C(mr x nt) -= V(mr x kb) [Y; Y2], kb <= 128, rows 0..kb1-1 of the
+// contraction from Y (ldy) and kb1..kb-1 from Y2 (ldy2); V's columns j >= maskC0 carry the unit-lower
+// structure relative to column maskC0 in rows r < maskV.  ys needs tc_update_ws_bytes(nt, 128).
+bool tc_update2_supported(long long ldc, const void* C);
+cudaError_t launch_gemm_update_tc2(float* C, long long ldc, const float* V, long long ldv, const double* Y,
+                                   long long ldy, const double* Y2, long long ldy2, int kb1, long long mr, long long nt,
+                                   int kb, long long maskV, int maskC0, float* ys, const Status* st, cudaStream_t s);
 bool tensor_cores_enabled();
 
 // General 3xTF32 tensor-core contraction (mm_tc.cu):
@@ -303,6 +310,12 @@ cudaError_t launch_tournament(T* B, int64_t ldb, int l, int64_t n, int64_t i, in
 template <typename T>
 cudaError_t launch_swaps(T* A, int64_t lda, int64_t m, int bb, const long long* swapmap, T* tmp,
                          const Status* st, cudaStream_t s);
+
+// Correction split of a paired block step (update.cu): Pc[(c0 + c) bb + r] = -(Gx Y0(:, cy0 + c))(r)
+// for c < nt, r < bb <= 64, Gx(r, q) = sum_sp P2[(sp bb + q) bb + r], Y0 column-major (ldy).  P2's
+// splits are summed into its first split in place.
+cudaError_t launch_wy_corr(const double* P2, int ns2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt,
+                           int64_t c0, double* Pc, const Status* st, cudaStream_t s);
 
 // Status block reset (rank = k) and jpvt = 0..n-1.
 cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s);

@@ -69,6 +69,17 @@ bool tensor_cores_enabled()
     }
     return v == 1;
 }
+// RQRCP_PAIRED=0 in the environment gives every block of the FP32 form its own trailing update
+// (instead of one update pass for two blocks), for A/B timing.
+bool paired_enabled()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("RQRCP_PAIRED");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
 // RQRCP_PANEL=householder in the environment keeps the FP32 form on the cooperative Householder
 // panel (one grid-wide step per column) instead of the CholeskyQR2 panel, for A/B timing.
 bool cholqr_enabled()
@@ -91,7 +102,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, tp, total;
+    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, tp, P2, Y2, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
@@ -109,7 +120,8 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     L.B = take((size_t)l * n * esz);
     // FP64 form: the untransformed copy of the sketch that Eq. (5) updates
     L.Bc = take(esz == sizeof(double) ? (size_t)l * n * esz : 0);
-    L.P = take((size_t)kMaxSplit * n * (size_t)(l > b ? l : b) * sizeof(double));
+    // one split more than the contractions use: a paired block step's correction (FP32 form)
+    L.P = take((size_t)(kMaxSplit + 1) * n * (size_t)(l > b ? l : b) * sizeof(double));
     // Y holds T^T W for the trailing columns, and for the l columns of Omega_bar^T under Eq. (5)
     L.Y = take((size_t)b * (size_t)(n > l ? n : l) * sizeof(double));
     L.Tm = take((size_t)b * b * sizeof(double));
@@ -120,13 +132,16 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     L.tmp = take((size_t)2 * b * (size_t)(m > l ? m : l) * esz);  // 2b columns of A, or of the sketch
     {
         // TF32 parts of Omega / V (contraction) and of Y (update); used one after the other
-        const size_t xs = tc_xsplit_bytes(l > b ? l : b, m), ys = tc_update_ws_bytes(n);
+        const size_t xs = tc_xsplit_bytes(l > b ? l : b, m), ys = tc_update_ws_bytes(n, 128);
         L.xs = take(esz == sizeof(float) ? (xs > ys ? xs : ys) : 0);
     }
     // FP32 form: the CholeskyQR2 panel's partial Grams, factors and Q1 (m x 64)
     L.cqr = take(esz == sizeof(float) ? cholqr_ws_bytes(m) : 0);
     // QR with tournament pivoting: the tree's choices, the root's reflectors and R_hat columns
     L.tp = take(tournament_ws_bytes(n, (int)l, b, (int)esz));
+    // FP32 form, paired block steps: the partials of V1^T V0 and block i+1's Y
+    L.P2 = take(esz == sizeof(float) ? (size_t)kMaxSplit * b * b * sizeof(double) : 0);
+    L.Y2 = take(esz == sizeof(float) ? (size_t)b * n * sizeof(double) : 0);
     L.total = off;
     return L;
 }
@@ -277,8 +292,8 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
     const double gtol = (sizeof(T) == 4 && sketch_bf16) ? ldexp(1.0, -6)
                                                         : 10.0 * (sizeof(T) == 8 ? mn : sqrt(mn)) * Prec<T>::unit_roundoff;
     const double guard_rel2 = gtol * gtol;
-    for (int64_t i = 0; i < k; i += b) {
-        const int bb = (int)(b < k - i ? b : k - i);
+    // pivots on the sketch (Alg. 2: partial QRCP on B(:, i:n)) and the column swaps of A
+    auto pivot_swap = [&](int64_t i, int bb) -> int {
         const double np = (double)(n - i);
         if (tourn) {
             int64_t gs;
@@ -294,6 +309,10 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * m * es, launch_swaps<T>(A, lda, m, bb, swapmap, tmp, st, s));
         if (eq5 && i + bb < k)  // the same column moves on the untransformed sketch
             RQ_LAUNCH(K_SWAP, 0, 4.0 * bb * l * es, launch_swaps<T>(Bc, l, l, bb, swapmap, tmp, st, s));
+        return RQRCP_OK;
+    };
+    // unpivoted QR of the panel A(i:m, i:i+bb)
+    auto panel = [&](int64_t i, int bb) -> int {
         T* Vp = A + i * lda + i;
         const int64_t mr = m - i;
         if (sizeof(T) == 4 && cholqr_enabled() && cholqr_supported(bb)) {
@@ -310,11 +329,14 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
             RQ_LAUNCH(K_PANEL, 2.0 * mr * bb * bb - 2.0 * bb * bb * bb / 3.0, 2.0 * mr * bb * es,
                       launch_panel<T>(Vp, lda, mr, bb, tau + i, part, st, s));
         }
-        const int64_t nt = n - i - bb;
-        if (nt <= 0) continue;
-        int ns;
+        return RQRCP_OK;
+    };
+    // [V^T V | V^T C] over rows i..m-1 and columns i..n-1 into the split partials P (ns splits)
+    auto gram = [&](int64_t i, int bb, bool tc, int& ns) -> int {
+        T* Vp = A + i * lda + i;
+        const int64_t mr = m - i;
+        const double np = (double)(n - i);
         int64_t kc;
-        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(bb, lda, (const void*)Vp);
         if (tc) {
             kc = tc_kchunk(n - i, mr, ns, 0, bb);
             RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
@@ -325,44 +347,115 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
             RQ_LAUNCH(K_WY_GEMM, 2.0 * bb * mr * np, (double)mr * np * es,
                       launch_gemm_tn<T>(Vp, lda, Vp, lda, bb, n - i, mr, kc, P, 1, bb, st, s));
         }
+        return RQRCP_OK;
+    };
+    for (int64_t i = 0; i < k; i += b) {
+        const int bb = (int)(b < k - i ? b : k - i);
+        if (int e = pivot_swap(i, bb)) return e;
+        if (int e = panel(i, bb)) return e;
+        T* Vp = A + i * lda + i;
+        const int64_t mr = m - i;
+        const int64_t nt = n - i - bb;
+        if (nt <= 0) continue;
+        const bool tc = sizeof(T) == 4 && tensor_cores_enabled() && tc_gemm_supported(bb, lda, (const void*)Vp);
+        int ns;
+        if (int e = gram(i, bb, tc, ns)) return e;
         RQ_LAUNCH(K_TFORM, (double)bb * bb * bb / 3.0, (double)ns * bb * bb * 8,
                   launch_tform(P, ns, n - i, bb, tau + i, Tm, st, s));
         RQ_LAUNCH(K_REDUCE_Y, (double)bb * bb * nt, ((double)ns + 1.0) * bb * nt * 8,
                   launch_reduce_y(P, ns, n - i, bb, bb, Tm, 1, Y, nt, st, s, sizeof(T) == 4 ? 1 : 0));
-        if (sizeof(T) == 4 && tensor_cores_enabled() && tc_update_supported(bb, lda, Vp + (int64_t)bb * lda))
-            RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
-                      launch_gemm_update_tc((float*)(Vp + (int64_t)bb * lda), lda, (const float*)Vp, lda, Y, bb, mr, nt,
-                                            bb, bb, reinterpret_cast<float*>(w + L.xs), st, s));
-        else
-            RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
-                      launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st, s));
-        // final_b: also after the last block, so that B sketches R22 (Alg. 3 reads its norms)
-        if ((i + bb < k || final_b) && !eq5)
-            RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
-                      launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));
-        if (i + bb < k && eq5) {
-            // Eq. (5): Omega_bar <- Omega_bar Q_tilde, i.e. Omega_bar^T(i:m, :) <- Q_tilde^T
-            // Omega_bar^T(i:m, :), the compact-WY update of the trailing matrix with C the m x l
-            // column-major view of the row-major Omega_bar; then B2 <- B2 - Omega_bar_1 R12.
-            T* OmT = Om + i;
-            int ns2;
-            int64_t kc2;
-            // only bb x l outputs (two 64-wide tiles): more K splits than kMaxSplit, as many as
-            // the partial buffer (kMaxSplit * n * max(l, b) doubles) holds, keep the GPU busy
-            const int64_t pcap = (int64_t)kMaxSplit * n * (l > b ? l : b);
-            choose_split(bb, l, mr, ns2, kc2, (int)sizeof(T), pcap / ((int64_t)bb * l));
-            RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, (double)mr * l * es,
-                      launch_gemm_tn<T>(Vp, lda, OmT, m, bb, l, mr, kc2, P, 1, 0, st, s));
-            RQ_LAUNCH(K_BUPDATE, (double)bb * bb * l, ((double)ns2 + 1.0) * bb * l * 8,
-                      launch_reduce_y(P, ns2, l, 0, bb, Tm, 1, Y, l, st, s));
-            RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, 2.0 * mr * l * es,
-                      launch_gemm_update<T>(OmT, m, Vp, lda, Y, bb, mr, l, bb, 1, nullptr, st, s));
-            choose_split(l, nt, bb, ns2, kc2, (int)sizeof(T));
-            RQ_LAUNCH(K_BUPDATE, 2.0 * l * bb * nt, (double)bb * nt * es + (double)l * bb * es,
-                      launch_gemm_tn<T>(OmT, m, Vp + (int64_t)bb * lda, lda, l, nt, bb, kc2, P, 0, 0, st, s));
-            RQ_LAUNCH(K_BUPDATE, 0, (double)ns2 * l * nt * 8 + 3.0 * l * nt * es,
-                      launch_bfinish<T>(B, Bc, (int)l, i + bb, nt, P, ns2, st, s));
+        // FP32 form: blocks i and i + 1 share one pass of the trailing update.  Block i updates now
+        // only what block i + 1 needs (its R12 rows for Eq. (4), then, after block i + 1's pivots,
+        // the panel's columns); block i + 1's Gram is taken from the trailing matrix before block i's
+        // update and corrected by (V1^T V0) Y0; then C -= [V0 V1] [Y0; Y1] in one pass (K = 2b).
+        const int64_t j = i + bb;
+        const bool pair = sizeof(T) == 4 && tc && !eq5 && paired_enabled() && bb == b && b <= 64 && j + b <= k &&
+                          n - j - b > 0 && tc_update_supported(bb, lda, (const void*)(Vp + (int64_t)bb * lda)) &&
+                          tc_update_supported(bb, lda, (const void*)(A + j * lda + j)) &&
+                          tc_update2_supported(lda, (const void*)(A + (j + b) * lda + j)) &&
+                          tc_gemm_supported(b, lda, (const void*)(A + j * lda + j));
+        if (!pair) {
+            if (sizeof(T) == 4 && tensor_cores_enabled() && tc_update_supported(bb, lda, Vp + (int64_t)bb * lda))
+                RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
+                          launch_gemm_update_tc((float*)(Vp + (int64_t)bb * lda), lda, (const float*)Vp, lda, Y, bb, mr,
+                                                nt, bb, bb, reinterpret_cast<float*>(w + L.xs), st, s));
+            else
+                RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr * nt, 2.0 * mr * nt * es + (double)mr * bb * es,
+                          launch_gemm_update<T>(Vp + (int64_t)bb * lda, lda, Vp, lda, Y, bb, mr, nt, bb, 1, nullptr, st,
+                                                s));
+            // final_b: also after the last block, so that B sketches R22 (Alg. 3 reads its norms)
+            if ((i + bb < k || final_b) && !eq5)
+                RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
+                          launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));
+            if (i + bb < k && eq5) {
+                // Eq. (5): Omega_bar <- Omega_bar Q_tilde, i.e. Omega_bar^T(i:m, :) <- Q_tilde^T
+                // Omega_bar^T(i:m, :), the compact-WY update of the trailing matrix with C the m x l
+                // column-major view of the row-major Omega_bar; then B2 <- B2 - Omega_bar_1 R12.
+                T* OmT = Om + i;
+                int ns2;
+                int64_t kc2;
+                // only bb x l outputs (two 64-wide tiles): more K splits than kMaxSplit, as many as
+                // the partial buffer (kMaxSplit * n * max(l, b) doubles) holds, keep the GPU busy
+                const int64_t pcap = (int64_t)kMaxSplit * n * (l > b ? l : b);
+                choose_split(bb, l, mr, ns2, kc2, (int)sizeof(T), pcap / ((int64_t)bb * l));
+                RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, (double)mr * l * es,
+                          launch_gemm_tn<T>(Vp, lda, OmT, m, bb, l, mr, kc2, P, 1, 0, st, s));
+                RQ_LAUNCH(K_BUPDATE, (double)bb * bb * l, ((double)ns2 + 1.0) * bb * l * 8,
+                          launch_reduce_y(P, ns2, l, 0, bb, Tm, 1, Y, l, st, s));
+                RQ_LAUNCH(K_BUPDATE, 2.0 * bb * mr * l, 2.0 * mr * l * es,
+                          launch_gemm_update<T>(OmT, m, Vp, lda, Y, bb, mr, l, bb, 1, nullptr, st, s));
+                choose_split(l, nt, bb, ns2, kc2, (int)sizeof(T));
+                RQ_LAUNCH(K_BUPDATE, 2.0 * l * bb * nt, (double)bb * nt * es + (double)l * bb * es,
+                          launch_gemm_tn<T>(OmT, m, Vp + (int64_t)bb * lda, lda, l, nt, bb, kc2, P, 0, 0, st, s));
+                RQ_LAUNCH(K_BUPDATE, 0, (double)ns2 * l * nt * 8 + 3.0 * l * nt * es,
+                          launch_bfinish<T>(B, Bc, (int)l, i + bb, nt, P, ns2, st, s));
+            }
+            continue;
         }
+        float* xs = reinterpret_cast<float*>(w + L.xs);
+        double* P2 = reinterpret_cast<double*>(w + L.P2);
+        double* Y1 = reinterpret_cast<double*>(w + L.Y2);
+        // block i: its R12 rows (rows i..j-1 of the trailing columns), then Eq. (4)
+        RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * bb * nt, 2.0 * bb * nt * es,
+                  launch_gemm_update_tc((float*)(Vp + (int64_t)bb * lda), lda, (const float*)Vp, lda, Y, bb, bb, nt, bb,
+                                        bb, xs, st, s));
+        RQ_LAUNCH(K_BUPDATE, (double)bb * bb * bb / 3.0 + (double)bb * bb * nt, 2.0 * bb * nt * es,
+                  launch_bupdate<T>(B, l, A, lda, i, bb, n, What, st, s));
+        // block i + 1: pivots and swaps (Y0's columns follow A's), then its panel's columns take block
+        // i's update (rows j..m-1) before the panel is factored
+        if (int e = pivot_swap(j, b)) return e;
+        RQ_LAUNCH(K_SWAP, 0, 4.0 * b * bb * 8,
+                  launch_swaps<double>(Y - j * bb, bb, bb, b, swapmap, reinterpret_cast<double*>(tmp), st, s));
+        const int64_t mr1 = m - j, nt1 = n - j - b;
+        float* const A0low = (float*)(A + i * lda + j);  // V0's rows j..m-1 (below its triangle)
+        RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr1 * b, 2.0 * mr1 * b * es + (double)mr1 * bb * es,
+                  launch_gemm_update_tc((float*)(A + j * lda + j), lda, A0low, lda, Y, bb, mr1, b, bb, 0, xs, st, s));
+        if (int e = panel(j, b)) return e;
+        // block i + 1's Gram over the trailing matrix before block i's update, and V1^T V0low
+        int ns1;
+        if (int e = gram(j, b, true, ns1)) return e;
+        {
+            int ns2;
+            const int64_t kc2 = tc_kchunk(bb, mr1, ns2, 0, b);
+            RQ_LAUNCH(K_WY_GEMM, 2.0 * b * mr1 * bb, (double)mr1 * bb * es,
+                      launch_gemm_tn_tc((const float*)(A + j * lda + j), lda, A0low, lda, b, bb, mr1, kc2, P2, b, 0, xs,
+                                        st, s));
+            RQ_LAUNCH(K_TFORM, (double)b * b * b / 3.0, (double)ns1 * b * b * 8,
+                      launch_tform(P, ns1, n - j, b, tau + j, Tm, st, s));
+            // the correction -(V1^T V0low) Y0 as split ns1, then Y1 = T1^T (W1 + correction)
+            RQ_LAUNCH(K_REDUCE_Y, 2.0 * b * bb * nt1, (double)bb * nt1 * 8 * 2,
+                      launch_wy_corr(P2, ns2, b, Y, bb, b, nt1, b, P + (size_t)ns1 * (n - j) * b, st, s));
+            RQ_LAUNCH(K_REDUCE_Y, (double)b * b * nt1, ((double)ns1 + 2.0) * b * nt1 * 8,
+                      launch_reduce_y(P, ns1 + 1, n - j, b, b, Tm, 1, Y1, nt1, st, s, 1));
+        }
+        // the trailing matrix of block i + 1, rows j..m-1: C -= [V0low V1] [Y0(:, b:); Y1]
+        RQ_LAUNCH(K_WY_UPDATE, 2.0 * (bb + b) * mr1 * nt1, 2.0 * mr1 * nt1 * es + (double)mr1 * (bb + b) * es,
+                  launch_gemm_update_tc2((float*)(A + (j + b) * lda + j), lda, A0low, lda, Y + (int64_t)b * bb, bb, Y1,
+                                         b, bb, mr1, nt1, bb + b, b, bb, xs, st, s));
+        if (j + b < k || final_b)
+            RQ_LAUNCH(K_BUPDATE, (double)b * b * b / 3.0 + (double)b * b * nt1, 2.0 * b * nt1 * es,
+                      launch_bupdate<T>(B, l, A, lda, j, b, n, What, st, s));
+        i += b;  // block i + 1 is done
     }
     if (rank_out != nullptr)
         RQ_CHECK(cudaMemcpyAsync(rank_out, &st->rank, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));

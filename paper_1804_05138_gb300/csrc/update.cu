@@ -191,7 +191,65 @@ __global__ void bfinish_kernel(T* __restrict__ B, T* __restrict__ Bc, int l, int
     }
 }
 
+// Two blocks in one trailing update: block i+1's Gram is taken from the trailing matrix before block
+// i's update, V1^T C, and corrected by V1^T (V0 Y0) = Gx Y0.  This writes the correction as one more
+// split of the partial buffer: Pc[(c0 + c) * bb + r] = -sum_q Gx(r, q) Y0(q, cy0 + c) for c < nt,
+// r < bb, with Gx(r, q) = P2[q * bb + r] (V1^T V0 over the rows of V0 below its triangle, its splits
+// already summed).  FP32 products (the Gram itself is FP32-accurate); 64 columns per block.
+__global__ void __launch_bounds__(256) wy_corr_kernel(const double* __restrict__ P2, int bb,
+                                                      const double* __restrict__ Y0, int64_t ldy, int64_t cy0,
+                                                      int64_t nt, int64_t c0, double* __restrict__ Pc,
+                                                      const Status* st)
+{
+    if (status_error(st)) return;
+    __shared__ float Gs[64][65], Ys[64][65];
+    const int tid = threadIdx.x;
+    const int64_t cb = (int64_t)blockIdx.x * 64;
+    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+        const int r = e % 64, q = e / 64;
+        Gs[r][q] = (r < bb && q < bb) ? (float)P2[(int64_t)q * bb + r] : 0.f;
+        const int64_t c = cb + q;  // here q runs over the block's columns and r over Y0's rows
+        Ys[q][r] = (r < bb && c < nt) ? (float)Y0[(cy0 + c) * ldy + r] : 0.f;
+    }
+    __syncthreads();
+    const int r = tid & 63;
+    if (r >= bb) return;
+    for (int cc = tid >> 6; cc < 64; cc += 4) {
+        const int64_t c = cb + cc;
+        if (c >= nt) break;
+        float acc = 0.f;
+#pragma unroll 16
+        for (int q = 0; q < 64; ++q) acc = fmaf(Gs[r][q], Ys[cc][q], acc);
+        Pc[(c0 + c) * bb + r] = -(double)acc;
+    }
+}
+
+// P2[e] = sum_sp P2[sp * len + e] for e < len: the splits summed into the first (each entry read
+// before it is written, by the same thread).
+__global__ void split_sum_kernel(double* __restrict__ P2, int ns, int64_t len, const Status* st)
+{
+    if (status_error(st)) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        double g = 0.0;
+        for (int sp = 0; sp < ns; ++sp) g += P2[sp * len + e];
+        P2[e] = g;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wy_corr(const double* P2, int ns2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt,
+                           int64_t c0, double* Pc, const Status* st, cudaStream_t s)
+{
+    if (nt <= 0) return cudaSuccess;
+    if (bb < 1 || bb > 64) return cudaErrorInvalidValue;
+    if (ns2 > 1) {
+        split_sum_kernel<<<16, 256, 0, s>>>(const_cast<double*>(P2), ns2, (int64_t)bb * bb, st);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    wy_corr_kernel<<<(unsigned)((nt + 63) / 64), 256, 0, s>>>(P2, bb, Y0, ldy, cy0, nt, c0, Pc, st);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s)
 {

@@ -1,6 +1,6 @@
 // update_tc.cu -- tensor-core (tcgen05, kind::tf32) form of the compact-WY trailing update of the
 // FP32 form (Alg. 2's block step, the Householder block applied as I - V T V^T):
-//   C(mr x nt) -= V(mr x kb) Y(kb x nt),  kb <= 64,
+//   C(mr x nt) -= V(mr x kb) Y(kb x nt),  kb <= KP (64, or 128 for two blocks applied in one pass),
 // with Y = T^T W coming from the FP64 reduction.  Both operands are split into TF32 parts
 // (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)) and V Y = V_hi [Y_hi Y_lo] + V_lo [Y_hi Y_lo].
 //
@@ -25,50 +25,62 @@ constexpr int UT_WORKERS = 32 * UT_WARPS_W;
 constexpr int UT_THREADS = 64 + UT_WORKERS;  // + TMA producer warp + MMA warp
 constexpr int UT_BM = 128;                   // rows of C per band (MMA M)
 constexpr int UT_BN = 64;                    // columns of C per tile (MMA N = 2 UT_BN)
-constexpr int UT_KP = 64;                    // contraction length padded (kb <= 64)
-constexpr int UT_NST = 3;                    // pipeline stages
-constexpr int UT_TILE_Y = 2 * UT_BN * UT_KP * 4;  // 32 KB: two K halves of 128 rows x 128 bytes
+constexpr int UT_KSUB = 2 * UT_BN * 128;     // bytes of one 32-long K slice of the Y tile (128 lines)
 constexpr int UT_TILE_C = UT_BM * UT_BN * 4;      // 32 KB: [column][row]
-constexpr int UT_STAGE = UT_TILE_Y + UT_TILE_C;
-constexpr unsigned UT_TMEM_COLS = 512;       // D0 (0..127), D1 (128..255), A hi (256..319), A lo (320..383)
+constexpr unsigned UT_TMEM_COLS = 512;  // D0 (0..127), D1 (128..255), A hi (256..256+KP-1), A lo (256+KP..)
 
-// Y (kb x nt FP64, column c at Y + c * ldy) -> ys: for tile t = c / 64, j = c % 64, line t * 128 + j
-// holds tf32(y(:, c)) and line t * 128 + 64 + j holds tf32(y - tf32(y)), 64 values per line (zero
-// for k >= kb and for c >= nt).
-__global__ void ysplit_kernel(const double* __restrict__ Y, long long ldy, int kb, long long nt, long long ntiles,
-                              float* __restrict__ ys, const Status* st)
+// KP: contraction length padded (kb <= KP); pipeline stages; Y tile (KP / 32 slices of 128 lines x
+// 128 bytes); stage bytes.
+template <int KP> struct UtCfg {
+    static constexpr int NST = KP == 64 ? 3 : 2;
+    static constexpr int TILE_Y = 2 * UT_BN * KP * 4;
+    static constexpr int STAGE = TILE_Y + UT_TILE_C;
+};
+
+// Y (kb x nt FP64: row k < kb1 of column c at Y[c * ldy + k], row k >= kb1 at Y2[c * ldy2 + k - kb1])
+// -> ys: for tile t = c / 64, j = c % 64, line t * 128 + j holds tf32(y(:, c)) and line
+// t * 128 + 64 + j holds tf32(y - tf32(y)), KP values per line (zero for k >= kb and for c >= nt).
+template <int KP>
+__global__ void ysplit_kernel(const double* __restrict__ Y, long long ldy, const double* __restrict__ Y2,
+                              long long ldy2, int kb1, int kb, long long nt, long long ntiles, float* __restrict__ ys,
+                              const Status* st)
 {
     if (status_error(st)) return;
-    const long long total = ntiles * UT_BN * UT_KP;
+    const long long total = ntiles * UT_BN * KP;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % UT_KP);
-        const long long c = e / UT_KP;
+        const int k = (int)(e % KP);
+        const long long c = e / KP;
         const long long t = c / UT_BN;
         const int j = (int)(c % UT_BN);
         float h = 0.f, l = 0.f;
         if (c < nt && k < kb) {
-            const double y = Y[c * ldy + k];
+            const double y = k < kb1 ? Y[c * ldy + k] : Y2[c * ldy2 + (k - kb1)];
             h = tf32_rn((float)y);
             l = tf32_rn((float)(y - (double)h));
         }
-        ys[(t * 2 * UT_BN + j) * UT_KP + k] = h;
-        ys[(t * 2 * UT_BN + UT_BN + j) * UT_KP + k] = l;
+        ys[(t * 2 * UT_BN + j) * KP + k] = h;
+        ys[(t * 2 * UT_BN + UT_BN + j) * KP + k] = l;
     }
 }
 
 struct UtArgs {
     long long mr, nt;      // rows and columns of C
-    int kb, ksteps;        // contraction length (<= 64), MMA k-steps ceil(kb / 8)
-    long long maskV;       // rows r < maskV of V carry the unit-lower structure
+    int kb, ksteps;        // contraction length (<= KP), MMA k-steps ceil(kb / 8)
+    long long maskV;       // rows r < maskV of V's columns j >= maskC0 carry the unit-lower structure
+    int maskC0;            // (relative to column maskC0: V(r, j) = 0 for r < j - maskC0, 1 for r == j - maskC0)
     long long ntiles;      // 64-column tiles per band
     long long total;       // bands * ntiles
 };
 
+template <int KP>
 __global__ void __launch_bounds__(UT_THREADS, 1)
     update_tc_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapY,
                      const float* __restrict__ V, long long ldv, UtArgs a, Status* st)
 {
+    constexpr int UT_NST = UtCfg<KP>::NST;
+    constexpr int UT_TILE_Y = UtCfg<KP>::TILE_Y;
+    constexpr int UT_STAGE = UtCfg<KP>::STAGE;
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = status_error(st);
     __syncthreads();
@@ -130,8 +142,9 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                 px[s] = (int)(band * UT_BM);
                 py[s] = (int)(ct * UT_BN);
                 mbar_expect_tx(&full[s], UT_STAGE);
-                tma_load_2d(sp, &mapY, 0, (int)(ct * 2 * UT_BN), &full[s]);
-                tma_load_2d(sp + UT_TILE_Y / 2, &mapY, 32, (int)(ct * 2 * UT_BN), &full[s]);
+#pragma unroll
+                for (int u = 0; u < KP / 32; ++u)
+                    tma_load_2d(sp + u * UT_KSUB, &mapY, 32 * u, (int)(ct * 2 * UT_BN), &full[s]);
                 tma_load_2d(sp + UT_TILE_Y, &mapC, px[s], py[s], &full[s]);
             }
             if (ok) {
@@ -175,10 +188,10 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                 const unsigned char* yt = stage_ptr(s);
                 const uint32_t td = tmem + (uint32_t)(b * 2 * UT_BN);
                 for (int kk = 0; kk < a.ksteps; ++kk)
-                    mma_tf32_ts(td, tA + 64 + 8 * kk, umma_desc(yt + (kk >> 2) * (UT_TILE_Y / 2) + (kk & 3) * 32), idesc,
+                    mma_tf32_ts(td, tA + KP + 8 * kk, umma_desc(yt + (kk >> 2) * UT_KSUB + (kk & 3) * 32), idesc,
                                 kk > 0 ? 1 : 0);
                 for (int kk = 0; kk < a.ksteps; ++kk)
-                    mma_tf32_ts(td, tA + 8 * kk, umma_desc(yt + (kk >> 2) * (UT_TILE_Y / 2) + (kk & 3) * 32), idesc, 1);
+                    mma_tf32_ts(td, tA + 8 * kk, umma_desc(yt + (kk >> 2) * UT_KSUB + (kk & 3) * 32), idesc, 1);
                 mma_commit(&accfull[b]);
                 issued = t + 1;
             }
@@ -196,38 +209,44 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
         for (long long g = g0; g < g1; ++g, ++t) {
             const long long band = g / a.ntiles;
             if (band != prev_band) {
-                // A <- V's band: row band * 128 + row, columns 16h .. 16h + 15 (every MMA of the
-                // previous band has completed: this thread drained its last accumulator)
+                // A <- V's band: row band * 128 + row, columns 16h + 64p .. 16h + 64p + 15 (every MMA
+                // of the previous band has completed: this thread drained its last accumulator)
                 const long long r = band * UT_BM + row;
-                uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int j = 16 * h + u;
-                    float v = 0.f;
-                    if (r < a.mr && j < a.kb) {
-                        v = V[(long long)j * ldv + r];
-                        if (r < a.maskV) {
-                            if (r < j) v = 0.f;
-                            else if (r == j) v = 1.f;
+                for (int part = 0; part < KP / 64; ++part) {
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int j = 16 * h + 64 * part + u;
+                        float v = 0.f;
+                        if (r < a.mr && j < a.kb) {
+                            v = V[(long long)j * ldv + r];
+                            const int jm = j - a.maskC0;
+                            if (r < a.maskV && jm >= 0) {
+                                if (r < jm) v = 0.f;
+                                else if (r == jm) v = 1.f;
+                            }
                         }
+                        const float hv = tf32_rn(v);
+                        hi[u] = __float_as_uint(hv);
+                        lo[u] = __float_as_uint(tf32_rn(v - hv));
                     }
-                    const float hv = tf32_rn(v);
-                    hi[u] = __float_as_uint(hv);
-                    lo[u] = __float_as_uint(tf32_rn(v - hv));
+                    const uint32_t ta = tA + lane_base + (uint32_t)(16 * h + 64 * part);
+                    asm volatile(
+                        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                            ta),
+                        "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]),
+                        "r"(hi[8]), "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]),
+                        "r"(hi[15])
+                        : "memory");
+                    asm volatile(
+                        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                            ta + KP),
+                        "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+                        "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]),
+                        "r"(lo[15])
+                        : "memory");
                 }
-                const uint32_t ta = tA + lane_base + (uint32_t)(16 * h);
-                asm volatile(
-                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-                        ta),
-                    "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]),
-                    "r"(hi[8]), "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]), "r"(hi[15])
-                    : "memory");
-                asm volatile(
-                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-                        ta + 64),
-                    "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
-                    "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]), "r"(lo[15])
-                    : "memory");
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 fence_before();
                 __syncwarp();
@@ -278,64 +297,100 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
     if (warp == 1) tmem_dealloc(tmem, UT_TMEM_COLS);
 }
 
-size_t ut_smem_bytes() { return 1024 + (size_t)UT_NST * UT_STAGE; }
-
-}  // namespace
-
-bool tc_update_supported(long long kb, long long ldc, const void* C)
+template <int KP>
+size_t ut_smem_bytes()
 {
-    if (!(kb >= 1 && kb <= UT_KP && (ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tc_encoder_available())) return false;
+    return 1024 + (size_t)UtCfg<KP>::NST * UtCfg<KP>::STAGE;
+}
+
+template <int KP>
+bool ut_fits()
+{
     static int fits = -1;
     if (fits < 0) {
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, (const void*)update_tc_kernel) != cudaSuccess) {
+        if (cudaFuncGetAttributes(&fa, (const void*)update_tc_kernel<KP>) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        fits = ut_smem_bytes() + fa.sharedSizeBytes <= (size_t)dev_info().max_smem_optin ? 1 : 0;
+        fits = ut_smem_bytes<KP>() + fa.sharedSizeBytes <= (size_t)dev_info().max_smem_optin ? 1 : 0;
     }
     return fits == 1;
 }
 
-size_t tc_update_ws_bytes(long long nt)
-{
-    return (size_t)((nt + UT_BN - 1) / UT_BN) * 2 * UT_BN * UT_KP * sizeof(float);
-}
-
-cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long long ldv, const double* Y, long long ldy,
-                                  long long mr, long long nt, int kb, long long maskV, float* ys, const Status* st,
-                                  cudaStream_t s)
+// C -= V [Y; Y2] with rows 0..kb1-1 of the contraction from Y and kb1..kb-1 from Y2 (Y2 may be null
+// when kb1 == kb).
+template <int KP>
+cudaError_t launch_update_tc_impl(float* C, long long ldc, const float* V, long long ldv, const double* Y,
+                                  long long ldy, const double* Y2, long long ldy2, int kb1, long long mr, long long nt,
+                                  int kb, long long maskV, int maskC0, float* ys, const Status* st, cudaStream_t s)
 {
     if (mr <= 0 || nt <= 0) return cudaSuccess;
-    if (((uintptr_t)ys % 16) != 0) return cudaErrorInvalidValue;
+    if (((uintptr_t)ys % 16) != 0 || kb < 1 || kb > KP || kb1 < 0 || kb1 > kb || (kb1 < kb && Y2 == nullptr))
+        return cudaErrorInvalidValue;
     const long long ntiles = (nt + UT_BN - 1) / UT_BN;
     {
-        const long long total = ntiles * UT_BN * UT_KP;
+        const long long total = ntiles * UT_BN * KP;
         long long blocks = (total + 255) / 256;
         if (blocks > 4L * dev_info().sms) blocks = 4L * dev_info().sms;
-        ysplit_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, ldy, kb, nt, ntiles, ys, st);
+        ysplit_kernel<KP><<<(unsigned)blocks, 256, 0, s>>>(Y, ldy, Y2, ldy2, kb1, kb, nt, ntiles, ys, st);
         if (cudaError_t e = cudaGetLastError()) return e;
     }
     CUtensorMap mapC, mapY;
     if (!tc_encode_2d(&mapC, C, mr, nt, ldc, UT_BM, UT_BN, false)) return cudaErrorInvalidValue;
-    if (!tc_encode_2d(&mapY, ys, UT_KP, ntiles * 2 * UT_BN, UT_KP, 32, 2 * UT_BN, true)) return cudaErrorInvalidValue;
+    if (!tc_encode_2d(&mapY, ys, KP, ntiles * 2 * UT_BN, KP, 32, 2 * UT_BN, true)) return cudaErrorInvalidValue;
     UtArgs a;
     a.mr = mr;
     a.nt = nt;
     a.kb = kb;
     a.ksteps = (kb + 7) / 8;
     a.maskV = maskV;
+    a.maskC0 = maskC0;
     a.ntiles = ntiles;
     a.total = ((mr + UT_BM - 1) / UT_BM) * ntiles;
     static DevFlag attr_set;
     if (!attr_set.done()) {
-        if (cudaError_t e = allow_max_dynamic_smem(update_tc_kernel)) return e;
+        if (cudaError_t e = allow_max_dynamic_smem(update_tc_kernel<KP>)) return e;
         attr_set.set();
     }
     long long grid = dev_info().sms;
     if (grid > a.total) grid = a.total;
-    update_tc_kernel<<<(unsigned)grid, UT_THREADS, ut_smem_bytes(), s>>>(mapC, mapY, V, ldv, a, const_cast<Status*>(st));
+    update_tc_kernel<KP><<<(unsigned)grid, UT_THREADS, ut_smem_bytes<KP>(), s>>>(mapC, mapY, V, ldv, a,
+                                                                               const_cast<Status*>(st));
     return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_update_supported(long long kb, long long ldc, const void* C)
+{
+    if (!(kb >= 1 && kb <= 64 && (ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tc_encoder_available())) return false;
+    return ut_fits<64>();
+}
+
+bool tc_update2_supported(long long ldc, const void* C)
+{
+    if (!((ldc % 4) == 0 && ((uintptr_t)C % 16) == 0 && tc_encoder_available())) return false;
+    return ut_fits<128>();
+}
+
+size_t tc_update_ws_bytes(long long nt, int kp)
+{
+    return (size_t)((nt + UT_BN - 1) / UT_BN) * 2 * UT_BN * (size_t)kp * sizeof(float);
+}
+
+cudaError_t launch_gemm_update_tc(float* C, long long ldc, const float* V, long long ldv, const double* Y, long long ldy,
+                                  long long mr, long long nt, int kb, long long maskV, float* ys, const Status* st,
+                                  cudaStream_t s)
+{
+    return launch_update_tc_impl<64>(C, ldc, V, ldv, Y, ldy, nullptr, 0, kb, mr, nt, kb, maskV, 0, ys, st, s);
+}
+
+cudaError_t launch_gemm_update_tc2(float* C, long long ldc, const float* V, long long ldv, const double* Y,
+                                   long long ldy, const double* Y2, long long ldy2, int kb1, long long mr, long long nt,
+                                   int kb, long long maskV, int maskC0, float* ys, const Status* st, cudaStream_t s)
+{
+    return launch_update_tc_impl<128>(C, ldc, V, ldv, Y, ldy, Y2, ldy2, kb1, mr, nt, kb, maskV, maskC0, ys, st, s);
 }
 
 }  // namespace rq
