@@ -187,11 +187,18 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                 fence_after();
                 const unsigned char* yt = stage_ptr(s);
                 const uint32_t td = tmem + (uint32_t)(b * 2 * UT_BN);
-                for (int kk = 0; kk < a.ksteps; ++kk)
+                // K = 128 (two blocks): the second block's k-steps first.  Its products are of the size
+                // of the trailing matrix after the first block's update, which can be far smaller than
+                // the first block's; accumulated first, they are not rounded against the large sum.
+                for (int kx = 0; kx < a.ksteps; ++kx) {
+                    const int kk = KP == 128 ? a.ksteps - 1 - kx : kx;
                     mma_tf32_ts(td, tA + KP + 8 * kk, umma_desc(yt + (kk >> 2) * UT_KSUB + (kk & 3) * 32), idesc,
-                                kk > 0 ? 1 : 0);
-                for (int kk = 0; kk < a.ksteps; ++kk)
+                                kx > 0 ? 1 : 0);
+                }
+                for (int kx = 0; kx < a.ksteps; ++kx) {
+                    const int kk = KP == 128 ? a.ksteps - 1 - kx : kx;
                     mma_tf32_ts(td, tA + 8 * kk, umma_desc(yt + (kk >> 2) * UT_KSUB + (kk & 3) * 32), idesc, 1);
+                }
                 mma_commit(&accfull[b]);
                 issued = t + 1;
             }
