@@ -69,16 +69,19 @@ bool tensor_cores_enabled()
     }
     return v == 1;
 }
-// RQRCP_PAIRED=0 in the environment gives every block of the FP32 form its own trailing update
-// (instead of one update pass for two blocks), for A/B timing.
-bool paired_enabled()
+// Paired block steps of the FP32 form (two blocks, one update pass) run where the trailing matrix is
+// larger than about this part's L2 (129 MB): below that the pass they save is served from L2 and
+// their extra launches cost more.  RQRCP_PAIRED=0 in the environment turns them off, =1 uses them at
+// every size (for A/B timing and tests).
+constexpr double kPairMinBytes = 128.0 * 1024 * 1024;
+int paired_mode()  // 0 off, 1 always, 2 by size
 {
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("RQRCP_PAIRED");
-        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+        v = (e != nullptr && e[0] == '0') ? 0 : (e != nullptr && e[0] == '1') ? 1 : 2;
     }
-    return v == 1;
+    return v;
 }
 // RQRCP_PANEL=householder in the environment keeps the FP32 form on the cooperative Householder
 // panel (one grid-wide step per column) instead of the CholeskyQR2 panel, for A/B timing.
@@ -369,7 +372,10 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         // the panel's columns); block i + 1's Gram is taken from the trailing matrix before block i's
         // update and corrected by (V1^T V0) Y0; then C -= [V0 V1] [Y0; Y1] in one pass (K = 2b).
         const int64_t j = i + bb;
-        const bool pair = sizeof(T) == 4 && tc && !eq5 && paired_enabled() && bb == b && b <= 64 && j + b <= k &&
+        const int pmode = paired_mode();
+        const bool big = (double)(m - j) * (double)(n - j - b) * sizeof(float) >= kPairMinBytes;
+        const bool pair = sizeof(T) == 4 && tc && !eq5 && (pmode == 1 || (pmode == 2 && big)) && bb == b && b <= 64 &&
+                          j + b <= k &&
                           n - j - b > 0 && tc_update_supported(bb, lda, (const void*)(Vp + (int64_t)bb * lda)) &&
                           tc_update_supported(bb, lda, (const void*)(A + j * lda + j)) &&
                           tc_update2_supported(lda, (const void*)(A + (j + b) * lda + j)) &&
