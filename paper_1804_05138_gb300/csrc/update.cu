@@ -6,7 +6,6 @@
 //    from the forward substitution Omega_hat_11 R11 = R_hat11 (both upper triangular);
 //  * the last step of Eq. (5): B(:, i+bb:n) <- B2 - Omega_bar_1 R12 from the split-K partials of
 //    Omega_bar_1 R12.
-#include "df.cuh"
 #include "internal.cuh"
 
 namespace rq {
@@ -196,10 +195,9 @@ __global__ void bfinish_kernel(T* __restrict__ B, T* __restrict__ Bc, int l, int
 // i's update, V1^T C, and corrected by V1^T (V0 Y0) = Gx Y0.  This writes the correction as one more
 // split of the partial buffer: Pc[(c0 + c) * bb + r] = -sum_q Gx(r, q) Y0(q, cy0 + c) for c < nt,
 // r < bb, with Gx(r, q) = P2[q * bb + r] (V1^T V0 over the rows of V0 below its triangle, its splits
-// already summed).  The two terms nearly cancel where the trailing matrix shrinks much under block
-// i's update, so the product runs in float pairs: Gx and Y0 as pairs, Dot2 sums (the exact product
-// of the leading parts, the cross terms in FP32).  kCorrCols columns per block.
-constexpr int kCorrCols = 16;
+// already summed).  FP32 products and sums (the Gram itself is FP32-accurate; float-pair sums here
+// measured no better); kCorrCols columns per block, sixteen per thread advanced together.
+constexpr int kCorrCols = 64;
 
 __global__ void __launch_bounds__(256) wy_corr_kernel(const double* __restrict__ P2, int bb,
                                                       const double* __restrict__ Y0, int64_t ldy, int64_t cy0,
@@ -207,35 +205,35 @@ __global__ void __launch_bounds__(256) wy_corr_kernel(const double* __restrict__
                                                       const Status* st)
 {
     if (status_error(st)) return;
-    __shared__ float Gh[64][65], Gl[64][65], Yh[kCorrCols][65], Yl[kCorrCols][65];
+    __shared__ float Gs[64][65], Ys[kCorrCols][65];
     const int tid = threadIdx.x;
     const int64_t cb = (int64_t)blockIdx.x * kCorrCols;
     for (int e = tid; e < 64 * 64; e += blockDim.x) {
         const int r = e % 64, q = e / 64;
-        const double g = (r < bb && q < bb) ? P2[(int64_t)q * bb + r] : 0.0;
-        Gh[r][q] = (float)g;
-        Gl[r][q] = (float)(g - (double)(float)g);
+        Gs[r][q] = (r < bb && q < bb) ? (float)P2[(int64_t)q * bb + r] : 0.f;
     }
     for (int e = tid; e < 64 * kCorrCols; e += blockDim.x) {
         const int r = e % 64, cc = e / 64;
         const int64_t c = cb + cc;
-        const double y = (r < bb && c < nt) ? Y0[(cy0 + c) * ldy + r] : 0.0;
-        Yh[cc][r] = (float)y;
-        Yl[cc][r] = (float)(y - (double)(float)y);
+        Ys[cc][r] = (r < bb && c < nt) ? (float)Y0[(cy0 + c) * ldy + r] : 0.f;
     }
     __syncthreads();
-    const int r = tid & 63;
+    const int r = tid & 63, cg = tid >> 6;
     if (r >= bb) return;
-    for (int cc = tid >> 6; cc < kCorrCols; cc += 4) {
-        const int64_t c = cb + cc;
-        if (c >= nt) break;
-        float sh = 0.f, sl = 0.f;
-#pragma unroll 8
-        for (int q = 0; q < 64; ++q) {
-            dot2_add(sh, sl, Gh[r][q], Yh[cc][q]);
-            sl = fmaf(Gh[r][q], Yl[cc][q], fmaf(Gl[r][q], Yh[cc][q], sl));
-        }
-        Pc[(c0 + c) * bb + r] = -((double)sh + (double)sl);
+    constexpr int NU = kCorrCols / 4;
+    float acc[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) acc[u] = 0.f;
+#pragma unroll 4
+    for (int q = 0; q < 64; ++q) {
+        const float g = Gs[r][q];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) acc[u] = fmaf(g, Ys[cg + 4 * u][q], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int64_t c = cb + cg + 4 * u;
+        if (c < nt) Pc[(c0 + c) * bb + r] = -(double)acc[u];
     }
 }
 
@@ -262,8 +260,7 @@ cudaError_t launch_wy_corr(const double* P2, int ns2, int bb, const double* Y0, 
         split_sum_kernel<<<16, 256, 0, s>>>(const_cast<double*>(P2), ns2, (int64_t)bb * bb, st);
         if (cudaError_t e = cudaGetLastError()) return e;
     }
-    wy_corr_kernel<<<(unsigned)((nt + kCorrCols - 1) / kCorrCols), 256, 0, s>>>(P2, bb, Y0, ldy, cy0, nt, c0, Pc,
-                                                                                st);
+    wy_corr_kernel<<<(unsigned)((nt + kCorrCols - 1) / kCorrCols), 256, 0, s>>>(P2, bb, Y0, ldy, cy0, nt, c0, Pc, st);
     return cudaGetLastError();
 }
 

@@ -29,12 +29,15 @@ constexpr int UT_KSUB = 2 * UT_BN * 128;     // bytes of one 32-long K slice of 
 constexpr int UT_TILE_C = UT_BM * UT_BN * 4;      // 32 KB: [column][row]
 constexpr unsigned UT_TMEM_COLS = 512;  // D0 (0..127), D1 (128..255), A hi (256..256+KP-1), A lo (256+KP..)
 
-// KP: contraction length padded (kb <= KP); pipeline stages; Y tile (KP / 32 slices of 128 lines x
-// 128 bytes); stage bytes.
+// KP: contraction length padded (kb <= KP); Y tile (KP / 32 slices of 128 lines x 128 bytes); the
+// Y tiles and the C tiles go through rings of their own (a Y stage is free once the tile's MMAs
+// complete, a C stage only after the drain and the store): NY Y stages, NC C stages.  At KP = 128
+// two 64 KB Y stages and three C stages fit where three whole stages would not.
 template <int KP> struct UtCfg {
-    static constexpr int NST = KP == 64 ? 3 : 2;
+    static constexpr int NY = KP == 64 ? 3 : 2;
+    static constexpr int NC = 3;
     static constexpr int TILE_Y = 2 * UT_BN * KP * 4;
-    static constexpr int STAGE = TILE_Y + UT_TILE_C;
+    static constexpr int SMEM = NY * TILE_Y + NC * UT_TILE_C;
 };
 
 // Y (kb x nt FP64: row k < kb1 of column c at Y[c * ldy + k], row k >= kb1 at Y2[c * ldy2 + k - kb1])
@@ -78,23 +81,26 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
     update_tc_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapY,
                      const float* __restrict__ V, long long ldv, UtArgs a, Status* st)
 {
-    constexpr int UT_NST = UtCfg<KP>::NST;
+    constexpr int NY = UtCfg<KP>::NY, NC = UtCfg<KP>::NC;
     constexpr int UT_TILE_Y = UtCfg<KP>::TILE_Y;
-    constexpr int UT_STAGE = UtCfg<KP>::STAGE;
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = status_error(st);
     __syncthreads();
     if (s_skip) return;  // block-uniform: warp 1's tensor-memory allocation is warp-collective
     extern __shared__ unsigned char smraw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[UT_NST], cdone[UT_NST], aready, accfull[2], accempty[2];
+    __shared__ __align__(8) uint64_t fullY[NY], freeY[NY], fullC[NC], cdone[NC], aready, accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 1) tmem_alloc(&tmem_base, UT_TMEM_COLS);
     if (tid == 0) {
-        for (int s = 0; s < UT_NST; ++s) {
-            mbar_init(&full[s], 1);
+        for (int s = 0; s < NY; ++s) {
+            mbar_init(&fullY[s], 1);
+            mbar_init(&freeY[s], 1);
+        }
+        for (int s = 0; s < NC; ++s) {
+            mbar_init(&fullC[s], 1);
             mbar_init(&cdone[s], UT_WARPS_W);
         }
         mbar_init(&aready, UT_WARPS_W);
@@ -112,7 +118,8 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
     const uint32_t tA = tmem + 256;
     const long long g0 = a.total * blockIdx.x / gridDim.x;
     const long long g1 = a.total * (blockIdx.x + 1) / gridDim.x;
-    auto stage_ptr = [&](int s) { return base + (size_t)s * UT_STAGE; };
+    auto ystage = [&](int s) { return base + (size_t)s * UT_TILE_Y; };
+    auto cstage = [&](int s) { return base + (size_t)NY * UT_TILE_Y + (size_t)s * UT_TILE_C; };
     auto fail = [&]() {
         s_fail = 1;
         set_error(st, RQRCP_ERR_TIMEOUT);
@@ -120,49 +127,58 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            int px[UT_NST], py[UT_NST];  // C coordinates of the tile held by each stage
+            int px[NC], py[NC];  // C coordinates of the tile held by each C stage
             long long t = 0;
             bool ok = true;
             for (long long g = g0; g < g1; ++g, ++t) {
-                const int s = (int)(t % UT_NST);
-                unsigned char* sp = stage_ptr(s);
-                if (t >= UT_NST) {
-                    // the stage's previous tile is finished: store it, and reuse the stage once the
+                const int sy = (int)(t % NY), sc = (int)(t % NC);
+                if (t >= NC) {
+                    // the C stage's previous tile is finished: store it, and reuse the stage once the
                     // store has read it
-                    if (!mbar_wait(&cdone[s], (unsigned)((t - UT_NST) / UT_NST) & 1u, &s_fail)) {
+                    if (!mbar_wait(&cdone[sc], (unsigned)((t - NC) / NC) & 1u, &s_fail)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    tma_store_2d(&mapC, px[s], py[s], sp + UT_TILE_Y);
+                    tma_store_2d(&mapC, px[sc], py[sc], cstage(sc));
                     bulk_commit();
                     bulk_wait_read();
                 }
+                // the Y stage is free once the MMAs of its previous tile have completed
+                if (t >= NY && !mbar_wait(&freeY[sy], (unsigned)((t - NY) / NY) & 1u, &s_fail)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
                 const long long band = g / a.ntiles, ct = g % a.ntiles;
-                px[s] = (int)(band * UT_BM);
-                py[s] = (int)(ct * UT_BN);
-                mbar_expect_tx(&full[s], UT_STAGE);
+                px[sc] = (int)(band * UT_BM);
+                py[sc] = (int)(ct * UT_BN);
+                mbar_expect_tx(&fullY[sy], UT_TILE_Y);
 #pragma unroll
                 for (int u = 0; u < KP / 32; ++u)
-                    tma_load_2d(sp + u * UT_KSUB, &mapY, 32 * u, (int)(ct * 2 * UT_BN), &full[s]);
-                tma_load_2d(sp + UT_TILE_Y, &mapC, px[s], py[s], &full[s]);
+                    tma_load_2d(ystage(sy) + u * UT_KSUB, &mapY, 32 * u, (int)(ct * 2 * UT_BN), &fullY[sy]);
+                mbar_expect_tx(&fullC[sc], UT_TILE_C);
+                tma_load_2d(cstage(sc), &mapC, px[sc], py[sc], &fullC[sc]);
             }
             if (ok) {
-                for (long long u = (t > UT_NST ? t - UT_NST : 0); u < t; ++u) {
-                    const int s = (int)(u % UT_NST);
-                    if (!mbar_wait(&cdone[s], (unsigned)(u / UT_NST) & 1u, &s_fail)) {
+                for (long long u = (t > NC ? t - NC : 0); u < t; ++u) {
+                    const int sc = (int)(u % NC);
+                    if (!mbar_wait(&cdone[sc], (unsigned)(u / NC) & 1u, &s_fail)) {
                         fail();
                         ok = false;
                         break;
                     }
-                    tma_store_2d(&mapC, px[s], py[s], stage_ptr(s) + UT_TILE_Y);
+                    tma_store_2d(&mapC, px[sc], py[sc], cstage(sc));
                     bulk_commit();
                 }
             }
             bulk_wait_all();
-            if (!ok)  // loads still in flight (tiles t - UT_NST .. t - 1) land before the block leaves
-                for (long long u = (t > UT_NST ? t - UT_NST : 0); u < t; ++u)
-                    mbar_wait(&full[u % UT_NST], (unsigned)(u / UT_NST) & 1u, nullptr);
+            if (!ok) {  // loads still in flight land before the block leaves (bounded)
+                for (long long u = (t > NY ? t - NY : 0); u < t; ++u)
+                    mbar_wait(&fullY[u % NY], (unsigned)(u / NY) & 1u, nullptr);
+                for (long long u = (t > NC ? t - NC : 0); u < t; ++u)
+                    mbar_wait(&fullC[u % NC], (unsigned)(u / NC) & 1u, nullptr);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -178,14 +194,14 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                     ++run;
                     prev_band = band;
                 }
-                const int s = (int)(t % UT_NST), b = (int)(t & 1);
-                if (!mbar_wait(&full[s], (unsigned)(t / UT_NST) & 1u, &s_fail) ||
+                const int sy = (int)(t % NY), b = (int)(t & 1);
+                if (!mbar_wait(&fullY[sy], (unsigned)(t / NY) & 1u, &s_fail) ||
                     (t >= 2 && !mbar_wait(&accempty[b], (unsigned)((t - 2) >> 1) & 1u, &s_fail))) {
                     fail();
                     break;
                 }
                 fence_after();
-                const unsigned char* yt = stage_ptr(s);
+                const unsigned char* yt = ystage(sy);
                 const uint32_t td = tmem + (uint32_t)(b * 2 * UT_BN);
                 // K = 128 (two blocks): the second block's k-steps first.  Its products are of the size
                 // of the trailing matrix after the first block's update, which can be far smaller than
@@ -199,6 +215,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                     const int kk = KP == 128 ? a.ksteps - 1 - kx : kx;
                     mma_tf32_ts(td, tA + 8 * kk, umma_desc(yt + (kk >> 2) * UT_KSUB + (kk & 3) * 32), idesc, 1);
                 }
+                mma_commit(&freeY[sy]);
                 mma_commit(&accfull[b]);
                 issued = t + 1;
             }
@@ -260,9 +277,9 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                 if (lane == 0) mbar_arrive(&aready);
                 prev_band = band;
             }
-            const int s = (int)(t % UT_NST), b = (int)(t & 1);
+            const int sc = (int)(t % NC), b = (int)(t & 1);
             bool okw = mbar_wait(&accfull[b], (unsigned)(t >> 1) & 1u, &s_fail);
-            okw = okw && mbar_wait(&full[s], (unsigned)(t / UT_NST) & 1u, &s_fail);  // C tile visible here
+            okw = okw && mbar_wait(&fullC[sc], (unsigned)(t / NC) & 1u, &s_fail);  // C tile visible here
             if (!__all_sync(0xffffffffu, okw)) {
                 ok = false;
                 break;
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[b]);
-            float* ctile = reinterpret_cast<float*>(stage_ptr(s) + UT_TILE_Y);
+            float* ctile = reinterpret_cast<float*>(cstage(sc));
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 float* x = ctile + (16 * h + u) * UT_BM + row;
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&cdone[s]);
+            if (lane == 0) mbar_arrive(&cdone[sc]);
         }
         if (!ok) fail();
     }
@@ -307,7 +324,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
 template <int KP>
 size_t ut_smem_bytes()
 {
-    return 1024 + (size_t)UtCfg<KP>::NST * UtCfg<KP>::STAGE;
+    return 1024 + (size_t)UtCfg<KP>::SMEM;
 }
 
 template <int KP>
