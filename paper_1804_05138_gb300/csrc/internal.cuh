@@ -312,10 +312,11 @@ cudaError_t launch_swaps(T* A, int64_t lda, int64_t m, int bb, const long long* 
                          const Status* st, cudaStream_t s);
 
 // Correction split of a paired block step (update.cu): Pc[(c0 + c) bb + r] = -(Gx Y0(:, cy0 + c))(r)
-// for c < nt, r < bb <= 64, Gx(r, q) = sum_sp P2[(sp bb + q) bb + r], Y0 column-major (ldy).  P2's
-// splits are summed into its first split in place.
-cudaError_t launch_wy_corr(const double* P2, int ns2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt,
-                           int64_t c0, double* Pc, const Status* st, cudaStream_t s);
+// for c < nt, r < bb <= 64, Gx(r, q) = P2[q bb + r], Y0 column-major (ldy).  launch_split_sum first
+// sums the ns2 splits of length len into the first, in place.
+cudaError_t launch_split_sum(double* P2, int ns2, int64_t len, const Status* st, cudaStream_t s);
+cudaError_t launch_wy_corr(const double* P2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt, int64_t c0,
+                           double* Pc, const Status* st, cudaStream_t s);
 
 // Status block reset (rank = k) and jpvt = 0..n-1.
 cudaError_t launch_init(Status* st, int64_t k, int32_t* jpvt, int64_t n, cudaStream_t s);

@@ -449,8 +449,11 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
             RQ_LAUNCH(K_TFORM, (double)b * b * b / 3.0, (double)ns1 * b * b * 8,
                       launch_tform(P, ns1, n - j, b, tau + j, Tm, st, s));
             // the correction -(V1^T V0low) Y0 as split ns1, then Y1 = T1^T (W1 + correction)
+            if (ns2 > 1)
+                RQ_LAUNCH(K_REDUCE_Y, (double)ns2 * b * bb, (double)(ns2 + 1) * b * bb * 8,
+                          launch_split_sum(P2, ns2, (int64_t)b * bb, st, s));
             RQ_LAUNCH(K_REDUCE_Y, 2.0 * b * bb * nt1, (double)bb * nt1 * 8 * 2,
-                      launch_wy_corr(P2, ns2, b, Y, bb, b, nt1, b, P + (size_t)ns1 * (n - j) * b, st, s));
+                      launch_wy_corr(P2, b, Y, bb, b, nt1, b, P + (size_t)ns1 * (n - j) * b, st, s));
             RQ_LAUNCH(K_REDUCE_Y, (double)b * b * nt1, ((double)ns1 + 2.0) * b * nt1 * 8,
                       launch_reduce_y(P, ns1 + 1, n - j, b, b, Tm, 1, Y1, nt1, st, s, 1));
         }

@@ -251,15 +251,17 @@ __global__ void split_sum_kernel(double* __restrict__ P2, int ns, int64_t len, c
 
 }  // namespace
 
-cudaError_t launch_wy_corr(const double* P2, int ns2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt,
-                           int64_t c0, double* Pc, const Status* st, cudaStream_t s)
+cudaError_t launch_split_sum(double* P2, int ns2, int64_t len, const Status* st, cudaStream_t s)
+{
+    split_sum_kernel<<<16, 256, 0, s>>>(P2, ns2, len, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wy_corr(const double* P2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt, int64_t c0,
+                           double* Pc, const Status* st, cudaStream_t s)
 {
     if (nt <= 0) return cudaSuccess;
     if (bb < 1 || bb > 64) return cudaErrorInvalidValue;
-    if (ns2 > 1) {
-        split_sum_kernel<<<16, 256, 0, s>>>(const_cast<double*>(P2), ns2, (int64_t)bb * bb, st);
-        if (cudaError_t e = cudaGetLastError()) return e;
-    }
     wy_corr_kernel<<<(unsigned)((nt + kCorrCols - 1) / kCorrCols), 256, 0, s>>>(P2, bb, Y0, ldy, cy0, nt, c0, Pc, st);
     return cudaGetLastError();
 }
