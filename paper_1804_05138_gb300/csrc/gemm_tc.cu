@@ -67,7 +67,8 @@ struct TcArgs {
     int M, Nb;               // rows of X used (<= Nb), MMA N (multiple of 16)
     long long N, K;          // columns of C, contraction length
     long long kchunk;        // K per split (multiple of TC_KC)
-    long long maskC;         // C columns c < maskC carry the reflector mask
+    long long maskC;         // C columns maskC0 <= c < maskC0 + maskC carry the reflector mask
+    long long maskC0;        // (relative to column maskC0)
     int nst;                 // pipeline stages (2..TC_MAXST)
     unsigned tmem_cols;
 };
@@ -311,12 +312,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     v[4 * pc + 2] = f.z;
                     v[4 * pc + 3] = f.w;
                 }
-                if (c < a.maskC && k0 < a.maskC) {
+                if (c - a.maskC0 >= 0 && c - a.maskC0 < a.maskC && k0 < a.maskC) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const long long qq = (long long)k0 + 8 * h + u;
-                        if (qq < c) v[u] = 0.f;
-                        else if (qq == c) v[u] = 1.f;
+                        if (qq < c - a.maskC0) v[u] = 0.f;
+                        else if (qq == c - a.maskC0) v[u] = 1.f;
                     }
                 }
                 uint32_t hi[8], lo[8];
@@ -529,12 +530,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     v[4 * pc + 2] = f.z;
                     v[4 * pc + 3] = f.w;
                 }
-                if (c < a.maskC && k0 < a.maskC) {
+                if (c - a.maskC0 >= 0 && c - a.maskC0 < a.maskC && k0 < a.maskC) {
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
                         const long long qq = (long long)k0 + 16 * half + u;
-                        if (qq < c) v[u] = 0.f;
-                        else if (qq == c) v[u] = 1.f;
+                        if (qq < c - a.maskC0) v[u] = 0.f;
+                        else if (qq == c - a.maskC0) v[u] = 1.f;
                     }
                 }
                 uint32_t hi[16], lo[16];
@@ -799,12 +800,13 @@ long long tc_kchunk(long long N, long long K, int& nsplit, int bf16, long long M
 
 cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
                               long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
-                              const Status* st, cudaStream_t s, int bf16)
+                              const Status* st, cudaStream_t s, int bf16, long long maskC0)
 {
     const bool bf = bf16 != 0;
     const int Nb = (int)(((M + 15) / 16) * 16);
     const int nst = tc_stages(Nb, bf);
-    if (nst < 2 || ((uintptr_t)xs % 16) != 0 || (bf && (maskX != 0 || maskC != 0))) return cudaErrorInvalidValue;
+    if (nst < 2 || ((uintptr_t)xs % 16) != 0 || (bf && (maskX != 0 || maskC != 0)) || maskC0 < 0)
+        return cudaErrorInvalidValue;
     CUtensorMap mapC, mapX;
     {
         long long gx = (K + 255) / 256;
@@ -838,6 +840,7 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
         a3.K = K;
         a3.kchunk = kchunk;
         a3.maskC = maskC;
+        a3.maskC0 = maskC0;
         a3.nst = nst3;
         a3.tmem_cols = 512;  // D0, D1 (2 Nb each), A0, A1 (128 each)
         const size_t smem3 = tc3_smem_bytes(Nb, nst3);
@@ -862,6 +865,7 @@ cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, lon
     a.K = K;
     a.kchunk = kchunk;
     a.maskC = maskC;
+    a.maskC0 = maskC0;
     a.nst = nst;
     unsigned cols = 32;
     const int need = bf ? 2 * Nb + 64 : 4 * Nb + 128;  // D0, D1, A0, A1

@@ -198,13 +198,14 @@ int gemm_tn_tile_rows(int64_t M);
 // 16-byte aligned with ldc % 4 == 0 (tc_gemm_supported); xs (16-byte aligned,
 // tc_xsplit_bytes(M, K)) receives the TF32 parts of X.  kchunk must come from tc_kchunk with
 // the same bf16 flag and M.  bf16: both operands rounded to BF16 (round to nearest even), products on
-// the kind::f16 tensor path with FP32 accumulation (the BF16 sketch; no reflector masks).
+// the kind::f16 tensor path with FP32 accumulation (the BF16 sketch; no reflector masks).  maskC0
+// moves C's masked columns to maskC0 .. maskC0 + maskC - 1 (the structure relative to maskC0).
 bool tc_gemm_supported(long long M, long long ldc, const void* C, int bf16 = 0);
 size_t tc_xsplit_bytes(long long M, long long K);
 long long tc_kchunk(long long N, long long K, int& nsplit, int bf16 = 0, long long M = 96);
 cudaError_t launch_gemm_tn_tc(const float* X, long long ldx, const float* C, long long ldc, long long M, long long N,
                               long long K, long long kchunk, double* P, long long maskX, long long maskC, float* xs,
-                              const Status* st, cudaStream_t s, int bf16 = 0);
+                              const Status* st, cudaStream_t s, int bf16 = 0, long long maskC0 = 0);
 // Tensor-core (tcgen05 kind::tf32, 3xTF32) form of launch_gemm_update<float> without colmap:
 // C(mr x nt) -= V(mr x kb) Y(kb x nt), kb <= 64, V unit-lower for rows r < maskV.  C must be
 // 16-byte aligned with ldc % 4 == 0 (tc_update_supported); ys (16-byte aligned,
@@ -313,8 +314,8 @@ cudaError_t launch_swaps(T* A, int64_t lda, int64_t m, int bb, const long long* 
 
 // Correction split of a paired block step (update.cu): Pc[(c0 + c) bb + r] = -(Gx Y0(:, cy0 + c))(r)
 // for c < nt, r < bb <= 64, Gx(r, q) = P2[q bb + r], Y0 column-major (ldy).  launch_split_sum first
-// sums the ns2 splits of length len into the first, in place.
-cudaError_t launch_split_sum(double* P2, int ns2, int64_t len, const Status* st, cudaStream_t s);
+// sums ns2 splits of length len, stride apart, into the first, in place.
+cudaError_t launch_split_sum(double* P2, int ns2, int64_t len, int64_t stride, const Status* st, cudaStream_t s);
 cudaError_t launch_wy_corr(const double* P2, int bb, const double* Y0, int64_t ldy, int64_t cy0, int64_t nt, int64_t c0,
                            double* Pc, const Status* st, cudaStream_t s);
 

@@ -105,7 +105,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, tp, P2, Y2, total;
+    size_t status, omega, B, Bc, P, Y, Tm, What, piv, cand, part, tmp, xs, cqr, tp, Y2, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
@@ -142,8 +142,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t b, int64_t p, size_t esz)
     L.cqr = take(esz == sizeof(float) ? cholqr_ws_bytes(m) : 0);
     // QR with tournament pivoting: the tree's choices, the root's reflectors and R_hat columns
     L.tp = take(tournament_ws_bytes(n, (int)l, b, (int)esz));
-    // FP32 form, paired block steps: the partials of V1^T V0 and block i+1's Y
-    L.P2 = take(esz == sizeof(float) ? (size_t)kMaxSplit * b * b * sizeof(double) : 0);
+    // FP32 form, paired block steps: block i+1's Y
     L.Y2 = take(esz == sizeof(float) ? (size_t)b * n * sizeof(double) : 0);
     L.total = off;
     return L;
@@ -419,7 +418,6 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
             continue;
         }
         float* xs = reinterpret_cast<float*>(w + L.xs);
-        double* P2 = reinterpret_cast<double*>(w + L.P2);
         double* Y1 = reinterpret_cast<double*>(w + L.Y2);
         // block i: its R12 rows (rows i..j-1 of the trailing columns), then Eq. (4)
         RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * bb * nt, 2.0 * bb * nt * es,
@@ -437,25 +435,27 @@ int factor_impl(int64_t m, int64_t n, T* A, int64_t lda, int64_t k, int64_t b, i
         RQ_LAUNCH(K_WY_UPDATE, 2.0 * bb * mr1 * b, 2.0 * mr1 * b * es + (double)mr1 * bb * es,
                   launch_gemm_update_tc((float*)(A + j * lda + j), lda, A0low, lda, Y, bb, mr1, b, bb, 0, xs, st, s));
         if (int e = panel(j, b)) return e;
-        // block i + 1's Gram over the trailing matrix before block i's update, and V1^T V0low
-        int ns1;
-        if (int e = gram(j, b, true, ns1)) return e;
+        // block i + 1's Gram over rows j..m-1 of columns i..n-1 before block i's update, in one pass:
+        // V1^T [V0low V1 C] (V1's reflector mask on the second 64 columns); partial column c holds
+        // V1^T V0low for c < bb, V1^T V1 for bb <= c < bb + b, and V1^T C beyond
         {
-            int ns2;
-            const int64_t kc2 = tc_kchunk(bb, mr1, ns2, 0, b);
-            RQ_LAUNCH(K_WY_GEMM, 2.0 * b * mr1 * bb, (double)mr1 * bb * es,
-                      launch_gemm_tn_tc((const float*)(A + j * lda + j), lda, A0low, lda, b, bb, mr1, kc2, P2, b, 0, xs,
-                                        st, s));
+            int ns1;
+            const int64_t nc1 = n - i;
+            const int64_t kc1 = tc_kchunk(nc1, mr1, ns1, 0, b);
+            RQ_LAUNCH(K_WY_GEMM, 2.0 * b * mr1 * (double)nc1, (double)mr1 * nc1 * es,
+                      launch_gemm_tn_tc((const float*)(A + j * lda + j), lda, A0low, lda, b, nc1, mr1, kc1, P, b, b, xs,
+                                        st, s, 0, bb));
             RQ_LAUNCH(K_TFORM, (double)b * b * b / 3.0, (double)ns1 * b * b * 8,
-                      launch_tform(P, ns1, n - j, b, tau + j, Tm, st, s));
-            // the correction -(V1^T V0low) Y0 as split ns1, then Y1 = T1^T (W1 + correction)
-            if (ns2 > 1)
-                RQ_LAUNCH(K_REDUCE_Y, (double)ns2 * b * bb, (double)(ns2 + 1) * b * bb * 8,
-                          launch_split_sum(P2, ns2, (int64_t)b * bb, st, s));
+                      launch_tform(P + (size_t)bb * b, ns1, nc1, b, tau + j, Tm, st, s));
+            // V1^T V0low summed into split 0, then the correction -(V1^T V0low) Y0 as split ns1, then
+            // Y1 = T1^T (W1 + correction)
+            if (ns1 > 1)
+                RQ_LAUNCH(K_REDUCE_Y, (double)ns1 * b * bb, (double)(ns1 + 1) * b * bb * 8,
+                          launch_split_sum(P, ns1, (int64_t)b * bb, nc1 * b, st, s));
             RQ_LAUNCH(K_REDUCE_Y, 2.0 * b * bb * nt1, (double)bb * nt1 * 8 * 2,
-                      launch_wy_corr(P2, b, Y, bb, b, nt1, b, P + (size_t)ns1 * (n - j) * b, st, s));
+                      launch_wy_corr(P, b, Y, bb, b, nt1, bb + b, P + (size_t)ns1 * nc1 * b, st, s));
             RQ_LAUNCH(K_REDUCE_Y, (double)b * b * nt1, ((double)ns1 + 2.0) * b * nt1 * 8,
-                      launch_reduce_y(P, ns1 + 1, n - j, b, b, Tm, 1, Y1, nt1, st, s, 1));
+                      launch_reduce_y(P, ns1 + 1, nc1, bb + b, b, Tm, 1, Y1, nt1, st, s, 1));
         }
         // the trailing matrix of block i + 1, rows j..m-1: C -= [V0low V1] [Y0(:, b:); Y1]
         RQ_LAUNCH(K_WY_UPDATE, 2.0 * (bb + b) * mr1 * nt1, 2.0 * mr1 * nt1 * es + (double)mr1 * (bb + b) * es,

@@ -237,23 +237,23 @@ __global__ void __launch_bounds__(256) wy_corr_kernel(const double* __restrict__
     }
 }
 
-// P2[e] = sum_sp P2[sp * len + e] for e < len: the splits summed into the first (each entry read
+// P2[e] = sum_sp P2[sp * stride + e] for e < len: the splits summed into the first (each entry read
 // before it is written, by the same thread).
-__global__ void split_sum_kernel(double* __restrict__ P2, int ns, int64_t len, const Status* st)
+__global__ void split_sum_kernel(double* __restrict__ P2, int ns, int64_t len, int64_t stride, const Status* st)
 {
     if (status_error(st)) return;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
         double g = 0.0;
-        for (int sp = 0; sp < ns; ++sp) g += P2[sp * len + e];
+        for (int sp = 0; sp < ns; ++sp) g += P2[sp * stride + e];
         P2[e] = g;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_split_sum(double* P2, int ns2, int64_t len, const Status* st, cudaStream_t s)
+cudaError_t launch_split_sum(double* P2, int ns2, int64_t len, int64_t stride, const Status* st, cudaStream_t s)
 {
-    split_sum_kernel<<<16, 256, 0, s>>>(P2, ns2, len, st);
+    split_sum_kernel<<<16, 256, 0, s>>>(P2, ns2, len, stride, st);
     return cudaGetLastError();
 }
 
