@@ -6,14 +6,16 @@
 //
 // A persistent kernel: block b of G owns the contiguous run [b T / G, (b+1) T / G) of the T tiles
 // (128 rows x 64 columns of C) in band-major order.  Per 128-row band the workers load V's band,
-// split it and store it to tensor memory as the MMA's A operand (hi parts in 64 columns, lo parts
-// in 64 more).  Per tile, a TMA producer warp loads the pre-split Y tile ([Y_hi; Y_lo] as a
-// 128-row K-major B operand, 128-byte swizzle) and the C tile (128 rows x 64 columns, column-major)
-// into a stage; one thread issues 2 ceil(kb / 8) MMAs (the A_lo products first) into one of two
-// accumulators (128 x 128: the Y_hi half, then the Y_lo half); sixteen worker warps read the
+// split it and store it to tensor memory as the MMA's A operand (hi parts in KP columns, lo parts
+// in KP more).  Per tile, a TMA producer warp loads the pre-split Y tile ([Y_hi; Y_lo] as a
+// 128-row K-major B operand, 128-byte swizzle) into the Y ring and the C tile (128 rows x 64
+// columns, column-major) into the C ring; one thread issues 2 ceil(kb / 8) MMAs (the A_lo products
+// first; at KP = 128 the later K first) into one of two accumulators (128 x 128: the Y_hi half,
+// then the Y_lo half), which frees the Y stage when they complete; sixteen worker warps read the
 // accumulator (tcgen05.ld), subtract it from the C tile in shared memory and hand the tile back
-// to the producer, which writes it with a TMA store.  Every wait is bounded; on timeout the block
-// records RQRCP_ERR_TIMEOUT, lets its copies land and frees its tensor memory.
+// to the producer, which writes it with a TMA store before reusing the C stage.  Every wait is
+// bounded; on timeout the block records RQRCP_ERR_TIMEOUT, lets its copies land and frees its
+// tensor memory.
 #include "tc_common.cuh"
 
 namespace rq {
